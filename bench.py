@@ -1,0 +1,319 @@
+"""Benchmark: contraction TFLOP/s and amplitudes/s of random-circuit amplitudes on GB300.
+
+Workload (default): a seeded 7x7 random circuit of depth 1+32+1 (sqrt(X), sqrt(Y), T
+single-qubit gates, CZs over 8 nearest-neighbour patterns; bond dimension 16 per edge),
+complex64, 6 open output sites -> 64 amplitudes per x1 batch (fast sampling, Sec. III.B),
+no cuts (largest intermediate 2^32 elements = 32 GiB), plain FP32 SIMT path.  One step =
+one x1 batch through the whole path: fold, scale, 48 contraction steps, FP64 sum.
+Counted work is Eq. 1 (F = 8 sqrt(v0 v1 v2) per contraction), 2.256e14 flop per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qfx|reference]
+                  [--workload full|small]
+
+Multi-GPU (torchrun): replicas -- each rank contracts its own x1 batches (no exchange on
+the data path); value is the sum over ranks, time the max over ranks ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import rqc_inputs as ri  # noqa: E402
+
+METRIC = "contraction TFLOP/s & amplitudes/s at rel err<=1e-5; % of tensor/HBM roofline"
+WORKLOADS = {
+    "full": dict(rows=7, cols=7, depth=32, n_open=6, seed=0),
+    "small": dict(rows=7, cols=7, depth=24, n_open=6, seed=0),   # profiling case (128 MiB boundary)
+}
+# DRAM traffic per launch of the dominant kernel, from one ncu capture of the same
+# kernel build; None until captured (see profiles/).
+TRAFFIC = {"full": None, "small": None}
+
+
+def workload_desc(w):
+    return (f"{w['rows']}x{w['cols']}x(1+{w['depth']}+1) RQC seed {w['seed']}, complex64, "
+            f"|x2|={w['n_open']} -> {1 << w['n_open']} amplitudes per x1 batch, no cuts, FP32 SIMT")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_median": statistics.median(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(seconds: float = 12.0):
+    """The oracle's contraction step (complex128 definition, oracle.primitives) on a
+    bounded sample of the dominant step of the workload: K = N = 256, 2^14 of its 2^24
+    columns, repeated for about `seconds`."""
+    from oracle import primitives
+    K = N = 256
+    cols = 1 << 14
+    S = ri.random_complex((K, N), seed=1).astype(np.complex128)
+    B = ri.random_complex((1, K, cols), seed=2).astype(np.complex128)
+    flops = 8.0 * K * N * cols
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        primitives.contract_step(S, B, 1, K, N, cols)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return flops * reps / dt / 1e12, reps, dt
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    times, tf = [], []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rate, reps, dt = cpu_oracle_sample(seconds=4.0)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            tf.append(rate)
+    value = float(np.mean(tf))
+    flops_step = 2.2558e14 if args.workload == "full" else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "l2": "host CPU run"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": "oracle.primitives.contract_step (numpy complex128 einsum, one "
+                                   "thread) on 2^14 of the 2^24 columns of the dominant step "
+                                   "(K=N=256), repeated ~4 s per step"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    if flops_step:
+        line["amplitudes_per_s"] = value * 1e12 / flops_step * (1 << w["n_open"])
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_qfx(args):
+    import torch
+    import torch.distributed as dist
+    world, rank, local = dist_env()
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1905_00444_gb300 as qfx
+
+    w = WORKLOADS[args.workload]
+    circ = ri.rqc(w["rows"], w["cols"], w["depth"], seed=w["seed"])
+    t0 = time.perf_counter()
+    plan = qfx.Plan(qfx.Circuit(circ), n_open=w["n_open"])
+    plan.upload()
+    plan_s = time.perf_counter() - t0
+    flops_step = plan.stats["flops_per_item"] * plan.n_slices
+    amps_step = 1 << w["n_open"]
+    nq = w["rows"] * w["cols"]
+    total = args.warmup + args.steps
+    x1_host = ri.random_bitstrings(nq, total * world, seed=1000)[rank * total:(rank + 1) * total]
+    x1_dev = torch.tensor(x1_host.view(np.int64), device=dev)
+    ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
+    out = torch.empty((1, amps_step), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        qfx.amplitudes(plan, x1_dev[i:i + 1], workspace=ws, out=out, stream=stream)
+    barrier()
+
+    # ---- device-timed region: inputs resident in HBM -------------------------------
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid is not None else str(local))
+    clocks.start()
+    qfx.profile_enable(True)
+    launches0 = qfx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for i in range(args.warmup, total):
+        qfx.amplitudes(plan, x1_dev[i:i + 1], workspace=ws, out=out, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = qfx.launch_count() - launches0
+    qfx.profile_enable(False)
+    recs = qfx.profile_collect()
+    clk = clocks.stop()
+    amax = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(amax, op=dist.ReduceOp.MAX)
+    elapsed = float(amax.item())
+
+    # ---- end to end through the public API with host buffers ----------------------
+    pin_x1 = torch.tensor(x1_host.view(np.int64)).pin_memory()
+    pin_out = torch.empty((1, amps_step), dtype=torch.complex128).pin_memory()
+    barrier()
+    e0 = time.perf_counter()
+    for i in range(args.warmup, total):
+        d = pin_x1[i:i + 1].to(dev, non_blocking=True)
+        qfx.amplitudes(plan, d, workspace=ws, out=out, stream=stream)
+        pin_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+    e_el = time.perf_counter() - e0
+    emax = torch.tensor([e_el], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(emax, op=dist.ReduceOp.MAX)
+    e_el = float(emax.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (largest contraction step) ---------------
+    big = plan.steps[plan.stats["largest_step"]]
+    dom = [r for r in recs if r["kind"] == 0 and r["flops"] == big["flops"]]
+    dom_ms = float(np.mean([r["ms"] for r in dom])) if dom else float("nan")
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12          # FP32 FMA pipes, TFLOP/s
+    achieved = big["flops"] / (dom_ms / 1e3) / 1e12
+    kern_total = sum(r["ms"] for r in recs)
+    share = {}
+    for r in recs:
+        key = {0: "contraction_step", 1: "fold", 4: "permute"}.get(r["kind"], str(r["kind"]))
+        share[key] = share.get(key, 0.0) + r["ms"]
+
+    value = flops_step * args.steps * world / elapsed / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(w), "grid": [w["rows"], w["cols"]],
+                   "depth": w["depth"], "n_open": w["n_open"], "n_slices": plan.n_slices,
+                   "flops_per_step": flops_step, "max_intermediate_bytes": plan.stats["max_elements"] * 8,
+                   "l2": "inputs larger than L2 (each big step reads and writes 32 GiB)",
+                   "plan_s": plan_s, "precision": "fp32_simt"},
+        "amplitudes_per_s": amps_step * args.steps * world / elapsed,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": TRAFFIC.get(args.workload),
+                     "kernel": f"cgemm_step variant {big['variant']} (P,K,N,Sd)="
+                               f"({big['P']},{big['K']},{big['N']},{big['Sd']})",
+                     "launches_timed": len(dom),
+                     "peak_note": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                                  "(FMA pipes; recipe unit counts)"},
+        "kernel_share": {k: v / kern_total for k, v in share.items()} if kern_total else {},
+        "e2e": {"value": flops_step * args.steps * world / e_el / 1e12, "unit": "TFLOP/s",
+                "amplitudes_per_s": amps_step * args.steps * world / e_el,
+                "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 16 * amps_step},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+    }
+    if world == 1 and not args.no_cpu:
+        rate, reps, dt = cpu_oracle_sample(seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle.primitives.contract_step (numpy complex128 einsum, one thread) on "
+                      f"2^14 of the 2^24 columns of the dominant step (K=N=256), {reps} reps in "
+                      f"{dt:.1f} s; host has {os.cpu_count()} cores",
+            "amplitudes_per_s": rate * 1e12 / flops_step * amps_step}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="qfx", choices=["qfx", "reference"])
+    ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_qfx(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

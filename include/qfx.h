@@ -1,0 +1,219 @@
+/*
+ * qfx.h -- C ABI of libqfx: tensor-network amplitudes of random quantum circuits on a
+ * 2D qubit grid, computed on one GB300 GPU (sm_103a).
+ *
+ * What the library computes (arXiv:1905.00444):
+ *   amp(x) = <x| C |0^n>, the quantity behind "Probability(circuit, s)" of the RCS
+ *   benchmark (Fig. 1), for batches of bitstrings x = x1 u x2 that share x1 (fast
+ *   sampling, Sec. III.B), as a sum over independent slices of the network (cuts,
+ *   Sec. III.A).  The circuit is folded in time into one tensor per grid site (Sec. III,
+ *   Fig. 3), each diagonal two-qubit gate becoming a bond of dimension 2 between the two
+ *   sites; the sites are then contracted one by one, each contraction a complex GEMM in
+ *   the TTGT form of Sec. III.E, with counted work F = 8 sqrt(v0 v1 v2) (Eq. 1).
+ *
+ * Conventions
+ *   - qubit q = r * cols + c; bit q of a uint64 bitstring is the value of qubit q (n <= 64).
+ *   - complex numbers are (re, im) pairs; complex64 = 2 x float, complex128 = 2 x double.
+ *   - Every call returns a qfx_status.  On failure, qfx_last_error() (thread-local) holds
+ *     a message.  No exception crosses the ABI and nothing aborts the process.
+ *   - Host objects (qfx_circuit, qfx_plan) are opaque, owned by the library, created by
+ *     *_create and freed by *_destroy.  They are immutable after creation (the plan's
+ *     device tables are uploaded once per device under a lock) and may be shared
+ *     between threads.
+ *   - All device buffers (inputs, outputs, workspace) are owned by the caller.  The
+ *     compute entry points allocate no device memory, so they can run on any stream.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL = legacy stream).
+ */
+#ifndef QFX_H
+#define QFX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QFX_OK = 0,
+  QFX_EINVAL = 1,       /* bad argument, bad circuit, bad plan option */
+  QFX_ENOMEM = 2,       /* caller's workspace smaller than one work item needs */
+  QFX_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  QFX_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+  QFX_EUNSUPPORTED = 5, /* valid request this build does not implement */
+  QFX_EPLAN = 6         /* no plan meets the memory cap */
+} qfx_status;
+
+typedef enum {
+  QFX_GATE_H = 0,
+  QFX_GATE_SQRT_X = 1,
+  QFX_GATE_SQRT_Y = 2,
+  QFX_GATE_T = 3,
+  QFX_GATE_CZ = 4,
+  QFX_GATE_U1 = 5,  /* any single-qubit 2x2 matrix */
+  QFX_GATE_U2 = 6   /* any diagonal two-qubit gate */
+} qfx_gate_kind;
+
+/* One gate.  `kind` is a label only: the library always uses `mat`.
+ *   single-qubit (q1 == -1): mat = 2x2 complex, row-major, (re, im) interleaved:
+ *                            mat[2*(2*row + col)] + i*mat[2*(2*row + col) + 1].
+ *   two-qubit (q1 >= 0):     a diagonal gate; mat = its 4 diagonal entries d[2*b0 + b1]
+ *                            (b0 = value of q0, b1 = value of q1), interleaved.
+ *                            q0 and q1 must be grid neighbours.
+ * Gates of one layer must act on disjoint qubits; layers run in increasing order. */
+typedef struct {
+  int32_t layer;
+  int32_t q0;
+  int32_t q1;
+  int32_t kind;
+  double mat[8];
+} qfx_gate;
+
+typedef struct qfx_circuit qfx_circuit;
+typedef struct qfx_plan qfx_plan;
+
+/* Sec. III (RQC class on a planar grid; Table I's "1+d+1" circuits).
+ * Validates and copies the gate list (a1): qubit ranges, two-qubit gates only between
+ * grid neighbours, disjoint qubits within a layer, layers >= 0, rows*cols <= 64.
+ * Errors: QFX_EINVAL with the offending gate index in qfx_last_error(). */
+qfx_status qfx_circuit_create(int32_t rows, int32_t cols, const qfx_gate* gates,
+                              int64_t n_gates, qfx_circuit** out);
+
+/* Same, from text: first line "grid R C", then one gate per line
+ * "layer KIND q0 [q1] v0 v1 ... v7" with every gate's 8 matrix values written out
+ * (KIND one of H SQRT_X SQRT_Y T CZ U1 U2; q1 present only for CZ and U2).
+ * '#' starts a comment.  Errors: QFX_EINVAL with the line number. */
+qfx_status qfx_circuit_from_text(const char* text, qfx_circuit** out);
+
+void qfx_circuit_destroy(qfx_circuit* c);
+
+typedef enum {
+  QFX_PREC_FP32_SIMT = 0,   /* complex FP32 on the FMA pipes, 4 real FMAs per complex MAC */
+  QFX_PREC_C3M_BF16X3 = 1,  /* 3M complex product on tcgen05, operands split into 3 BF16 terms */
+  QFX_PREC_C3M_TF32X3 = 2   /* 3M complex product on tcgen05, operands split into 2 TF32 terms */
+} qfx_precision;
+
+/* A cut (Sec. III.A): the bond between grid neighbours qa and qb is sliced into pieces
+ * of `size` consecutive bond values (size a power of two dividing the bond dimension;
+ * size 1 fixes the bond completely).  A bond's index reads the leg of its earliest
+ * two-qubit gate as the most significant bit. */
+typedef struct {
+  int32_t qa;
+  int32_t qb;
+  int32_t size;
+} qfx_cut;
+
+typedef struct {
+  uint64_t max_intermediate_bytes; /* cap on the largest intermediate tensor (complex64); 0 = none */
+  const int32_t* open_sites;       /* x2 qubits (Sec. III.B), or NULL to let the planner take
+                                      the last n_open sites of its contraction order */
+  int32_t n_open;                  /* number of x2 qubits (<= 24); output index bit i = open site i */
+  const qfx_cut* forced_cuts;      /* cuts always applied (before any the cap needs) */
+  int32_t n_forced_cuts;
+  int32_t precision;               /* qfx_precision */
+  int32_t plan_family;             /* 0 = line sweep (the only family of this build) */
+  int32_t reserved;
+} qfx_plan_opts;
+
+/* Sec. III.D (contraction order and cuts), Sec. III.A (slices), Sec. III.B (x2), Eq. 1.
+ * Host only: the plan sweeps the grid line by line (along the shorter grid dimension),
+ * absorbing one site per step so that every step is a strided batched complex GEMM
+ * C[nh][p][nl][s] = sum_k S[k][nh*NL+nl] * B[p][k][s] with no tensor transpose; then it
+ * adds cuts (greedily halving the bond that keeps the total work lowest) until the
+ * largest intermediate fits the cap.
+ * Errors: QFX_EINVAL (bad options), QFX_EPLAN (cap cannot be met). */
+qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts* opts, qfx_plan** out);
+void qfx_plan_destroy(qfx_plan* p);
+
+typedef struct {
+  int64_t n_slices;            /* product of the cut radices */
+  int32_t n_steps;             /* sites absorbed, = number of qubits (step 0 is free) */
+  int32_t n_open;
+  int32_t n_cuts;
+  int32_t n_sites;
+  double flops_per_item;       /* Eq. 1 flops of one (slice, x1) work item */
+  double bytes_per_item;       /* algorithmic bytes: each GEMM operand read once, output written once */
+  int64_t max_elements;        /* largest intermediate, complex64 elements */
+  uint64_t item_bytes;         /* workspace one work item needs */
+  uint64_t workspace_min;      /* workspace for one item plus the shared header */
+  int32_t largest_step;        /* index of the step with the most flops */
+  int32_t precision;
+} qfx_plan_stats;
+
+qfx_status qfx_plan_info(const qfx_plan* p, qfx_plan_stats* out);
+
+/* Workspace bytes for `n_concurrent` work items in flight at once. */
+uint64_t qfx_workspace_bytes(const qfx_plan* p, int64_t n_concurrent);
+
+typedef struct {
+  int32_t site;       /* qubit absorbed by this step */
+  int32_t variant;    /* kernel tile variant chosen for it */
+  int64_t P, K, N, NL, Sd;  /* shapes as in qfx_plan_create's formula; NH = N / NL */
+  double flops;       /* 8*P*K*N*Sd = 8 sqrt(v0 v1 v2), Eq. 1 */
+  double bytes;       /* 8*(P*K*Sd + K*N + P*N*Sd) */
+} qfx_step_info;
+
+qfx_status qfx_plan_step(const qfx_plan* p, int32_t i, qfx_step_info* out);
+qfx_status qfx_plan_cut(const qfx_plan* p, int32_t i, qfx_cut* out);
+/* The plan's x2 qubits, in output-bit order (out must hold n_open entries). */
+qfx_status qfx_plan_open_sites(const qfx_plan* p, int32_t* out);
+
+/* Uploads the plan's tables to the current device (done implicitly by the first compute
+ * call on a device, which is then synchronous; call this first before stream capture). */
+qfx_status qfx_plan_upload(const qfx_plan* p);
+
+/* Amplitudes (Sec. III.A-III.B; the sum over paths of Sec. III.A and III.C).
+ *   x1        device, [n_batch] uint64 bitstrings; the bits of the open sites are ignored.
+ *   slices    [slice_begin, slice_end) of the plan's n_slices; a sub-range gives that
+ *             range's contribution (sharding, or a fraction of paths).
+ *   workspace device, ws_bytes >= qfx_plan_stats.workspace_min, 256-byte aligned; more
+ *             workspace lets more (slice, x1) items run concurrently.
+ *   out       device complex128 [n_batch][2^n_open], overwritten with
+ *             2^(sum of per-site scale exponents) * sum over slices (in slice order, FP64).
+ * Asynchronous on `stream`.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA. */
+qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                          int64_t slice_begin, int64_t slice_end, void* workspace,
+                          size_t ws_bytes, double* out, void* stream);
+
+/* Waits for `stream` and reports any asynchronous CUDA error as QFX_ECUDA. */
+qfx_status qfx_sync(void* stream);
+
+/* One contraction step of the TTGT form (Sec. III.E), for tests and microbenchmarks:
+ * C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] * B[p][k][s], complex64, all device pointers,
+ * 16-byte aligned, no aliasing.  `variant` < 0 lets the library choose. */
+qfx_status qfx_contract_step(const void* S, const void* B, void* C, int64_t P, int64_t K,
+                             int64_t N, int64_t NL, int64_t Sd, int32_t precision,
+                             int32_t variant, void* stream);
+
+/* Tensor transpose (Sec. III.E): out = in with axes reordered; complex64, rank <= 10.
+ * shape[] is the input shape (C order); out axis a is input axis perm[a].
+ * Device pointers, no aliasing.  Errors: QFX_EINVAL for a bad permutation or rank. */
+qfx_status qfx_permute(const void* in, void* out, int32_t rank, const int64_t* shape,
+                       const int32_t* perm, void* stream);
+
+/* Kernel timing for measurement (not needed for computing): while enabled, each
+ * contraction-step launch is bracketed by CUDA events on its own stream. */
+typedef struct {
+  int32_t step;       /* plan step index, or -1 for qfx_contract_step */
+  int32_t variant;
+  int32_t kind;       /* 0 = contraction step, 1 = fold, 2 = scale, 3 = accumulate */
+  float ms;
+  double flops;
+  double bytes;
+} qfx_kernel_time;
+
+qfx_status qfx_profile_enable(int32_t on);
+/* Waits for the recorded events; copies up to `max` records; returns the count in *n
+ * and clears the record list. */
+qfx_status qfx_profile_collect(qfx_kernel_time* out, int32_t max, int32_t* n);
+
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t qfx_launch_count(void);
+
+const char* qfx_last_error(void);
+const char* qfx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QFX_H */

@@ -1,0 +1,165 @@
+// Internal structures of libqfx shared by the host planner and the CUDA kernels.
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/qfx.h"
+
+namespace qfx {
+
+constexpr int kMaxSites = 64;
+constexpr int kMaxOpen = 24;
+constexpr int kMaxCuts = 64;
+
+// ---------------------------------------------------------------------------
+// circuit
+// ---------------------------------------------------------------------------
+struct Gate {
+  int layer, q0, q1, kind;
+  double m[8];
+};
+
+}  // namespace qfx
+
+struct qfx_circuit {
+  int rows = 0, cols = 0;
+  std::vector<qfx::Gate> gates;   // sorted by layer (stable)
+};
+
+namespace qfx {
+
+// ---------------------------------------------------------------------------
+// time fold program (Sec. III: contraction in the time direction first)
+// ---------------------------------------------------------------------------
+enum EventKind : int32_t {
+  EV_GATE = 0,   // v <- G v, G = 2x2 matrix `mat`
+  EV_PROJ = 1,   // this site is q0 of a diagonal 2q gate: v <- |k><k| v, k = leg bit
+  EV_DIAG = 2    // this site is q1: v <- diag(D[k][0], D[k][1]) v, k = leg bit
+};
+
+struct FoldEvent {
+  int32_t kind;
+  int32_t slot;   // bond slot 0..3 (up, left, right, down) holding the leg
+  int32_t bit;    // bit of the bond value that is this leg
+  int32_t mat;    // index into the matrix table (4 complex doubles each)
+};
+
+// Site tensor layout: T[up][left][x][right][down] (row-major), so that k = (up, left)
+// and n = (x, right, down) in the step formula.
+struct FoldSite {
+  int32_t qubit;
+  int32_t ev_begin, ev_end;
+  int32_t edge[4];      // edge id per slot (up, left, right, down), -1 if absent
+  int32_t dim[5];       // local dims: up, left, x, right, down (after slicing)
+  int32_t x_open;       // 1 if the output leg stays open
+  int32_t pad;
+  int64_t size;         // product of dims
+  int64_t offset;       // element offset of this site in an item's site region
+};
+
+struct CutDev {
+  int32_t edge;
+  int32_t size;         // slice width in bond values
+  int64_t radix;        // number of pieces
+  int64_t suffix;       // product of the radices of later cuts
+};
+
+// ---------------------------------------------------------------------------
+// contraction steps
+// ---------------------------------------------------------------------------
+struct Step {
+  int32_t site;
+  int32_t variant;
+  int64_t P, K, N, NL, Sd;
+  double flops, bytes;
+};
+
+// Workspace layout:
+//   header: per concurrent item: maxabs[n_sites] (u32) + exps[n_sites] (i32), padded
+//   items : per concurrent item: buf0 (max_elements) | buf1 (max_elements) | sites
+struct Layout {
+  uint64_t header_per_item;   // bytes
+  uint64_t item_bytes;        // bytes, multiple of 256
+  uint64_t buf0, buf1, sites; // byte offsets inside one item block
+};
+
+struct DeviceTables {
+  void* base = nullptr;          // one cudaMalloc holding everything below
+  const FoldSite* sites = nullptr;
+  const FoldEvent* events = nullptr;
+  const double* mats = nullptr;  // [n_mats][8]
+  const CutDev* cuts = nullptr;
+  const int32_t* open_perm = nullptr;  // output bit i -> bit of the final tensor index
+};
+
+}  // namespace qfx
+
+struct qfx_plan {
+  int rows = 0, cols = 0, n = 0;
+  int precision = 0;
+  bool transposed = false;        // lines are grid rows instead of columns
+  std::vector<int> order;         // qubits in sweep order
+  std::vector<int> open_sites;    // user order (output bit i)
+  std::vector<int32_t> open_perm; // output bit i -> final tensor bit
+  std::vector<std::pair<int, int>> edges;  // (q_lo, q_hi)
+  std::vector<int> edge_legs;     // legs per edge
+  std::vector<qfx_cut> cuts;      // in slice-id digit order (first = most significant)
+  std::vector<qfx::CutDev> cut_dev;
+  int64_t n_slices = 1;
+  std::vector<qfx::FoldSite> sites;     // indexed by qubit
+  std::vector<qfx::FoldEvent> events;
+  std::vector<double> mats;
+  std::vector<qfx::Step> steps;   // steps[0] is the free first site
+  int64_t max_elements = 1;
+  int64_t site_total = 0;
+  double flops_per_item = 0, bytes_per_item = 0;
+  int largest_step = 0;
+  qfx::Layout layout{};
+  // device tables, one set per device
+  mutable std::mutex mu;
+  mutable std::vector<qfx::DeviceTables> dev;   // index = device ordinal
+};
+
+namespace qfx {
+
+// error reporting (thread-local message)
+qfx_status fail(qfx_status st, const std::string& msg);
+qfx_status cuda_fail(int err, const char* what);
+
+// kernels (implemented in .cu files); all return 0 or a cudaError_t value
+int launch_fold(const DeviceTables& t, int n_sites, int64_t max_site_size, int n_cuts,
+                const uint64_t* x1, int64_t n_batch, int64_t slice_begin, int64_t item0,
+                int items, char* hdr, uint64_t hdr_stride, char* itemsp, uint64_t item_bytes,
+                uint64_t sites_off, void* stream);
+int launch_scale(const DeviceTables& t, int n_sites, int64_t max_site_size, int items,
+                 char* hdr, uint64_t hdr_stride, char* itemsp, uint64_t item_bytes,
+                 uint64_t sites_off, void* stream);
+int launch_accumulate(const DeviceTables& t, int n_sites, int n_open, int64_t n_batch,
+                      int64_t item0, int items, const char* hdr, uint64_t hdr_stride,
+                      const char* itemsp, uint64_t item_bytes, uint64_t final_off, double* out,
+                      void* stream);
+int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
+                int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
+                int batch, int variant, int precision, void* stream);
+int pick_variant(int64_t N, int64_t Sd);
+int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
+                   const int32_t* perm, void* stream);
+
+// device tables of a plan (uploaded once per device)
+qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out);
+void free_tables(DeviceTables& t);
+
+// profiling hooks
+bool profile_on();
+void profile_begin(void* stream, int* slot);
+void profile_end(void* stream, int slot, int step, int variant, int kind, double flops,
+                 double bytes);
+
+void count_launch(int n = 1);
+
+}  // namespace qfx

@@ -1,0 +1,289 @@
+// Runtime of libqfx: error state, launch accounting, kernel timing, plan tables on the
+// device, and the executor behind qfx_amplitudes.
+//
+// Executor (Sec. III.A-III.B): the work is the list of items (slice, x1) for slices in
+// [slice_begin, slice_end) and the n_batch bitstrings, slice-major.  As many items as
+// the caller's workspace holds run together: fold + scale their site tensors, run every
+// contraction step once for all of them (the item index is the GEMM's batch index), and
+// add each item's result into out in FP64, in slice order.  No device memory is
+// allocated here; all scratch lives in the caller's workspace.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qfx_internal.h"
+
+namespace qfx {
+
+namespace {
+thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int step, variant, kind;
+  double flops, bytes;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+}  // namespace
+
+qfx_status fail(qfx_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+qfx_status cuda_fail(int err, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString((cudaError_t)err);
+  return QFX_ECUDA;
+}
+
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+bool profile_on() { return g_prof_on; }
+
+void profile_begin(void* stream, int* slot) {
+  *slot = -1;
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfRec r{};
+  r.a = take_event();
+  r.b = take_event();
+  cudaEventRecord(r.a, (cudaStream_t)stream);
+  g_prof.push_back(r);
+  *slot = (int)g_prof.size() - 1;
+}
+
+void profile_end(void* stream, int slot, int step, int variant, int kind, double flops,
+                 double bytes) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot >= (int)g_prof.size()) return;
+  ProfRec& r = g_prof[slot];
+  cudaEventRecord(r.b, (cudaStream_t)stream);
+  r.step = step;
+  r.variant = variant;
+  r.kind = kind;
+  r.flops = flops;
+  r.bytes = bytes;
+}
+
+void free_tables(DeviceTables& t) {
+  if (t.base) cudaFree(t.base);
+  t = DeviceTables{};
+}
+
+qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(p->mu);
+  if ((int)p->dev.size() <= dev) p->dev.resize(dev + 1);
+  DeviceTables& t = p->dev[dev];
+  if (!t.base) {
+    const size_t s_sites = align256(p->sites.size() * sizeof(FoldSite));
+    const size_t s_ev = align256(std::max<size_t>(1, p->events.size()) * sizeof(FoldEvent));
+    const size_t s_mats = align256(std::max<size_t>(1, p->mats.size()) * sizeof(double));
+    const size_t s_cuts = align256(std::max<size_t>(1, p->cut_dev.size()) * sizeof(CutDev));
+    const size_t s_perm = align256(std::max<size_t>(1, p->open_perm.size()) * sizeof(int32_t));
+    const size_t total = s_sites + s_ev + s_mats + s_cuts + s_perm;
+    std::vector<char> host(total, 0);
+    char* h = host.data();
+    std::memcpy(h, p->sites.data(), p->sites.size() * sizeof(FoldSite));
+    std::memcpy(h + s_sites, p->events.data(), p->events.size() * sizeof(FoldEvent));
+    std::memcpy(h + s_sites + s_ev, p->mats.data(), p->mats.size() * sizeof(double));
+    std::memcpy(h + s_sites + s_ev + s_mats, p->cut_dev.data(), p->cut_dev.size() * sizeof(CutDev));
+    std::memcpy(h + s_sites + s_ev + s_mats + s_cuts, p->open_perm.data(),
+                p->open_perm.size() * sizeof(int32_t));
+    void* d = nullptr;
+    e = cudaMalloc(&d, total);
+    if (e != cudaSuccess) return cuda_fail(e, "plan table upload (cudaMalloc)");
+    e = cudaMemcpy(d, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "plan table upload (cudaMemcpy)"); }
+    char* b = (char*)d;
+    t.base = d;
+    t.sites = (const FoldSite*)b;
+    t.events = (const FoldEvent*)(b + s_sites);
+    t.mats = (const double*)(b + s_sites + s_ev);
+    t.cuts = (const CutDev*)(b + s_sites + s_ev + s_mats);
+    t.open_perm = (const int32_t*)(b + s_sites + s_ev + s_mats + s_cuts);
+  }
+  *out = &t;
+  return QFX_OK;
+}
+
+}  // namespace qfx
+
+using namespace qfx;
+
+extern "C" qfx_status qfx_plan_upload(const qfx_plan* p) {
+  if (!p) return fail(QFX_EINVAL, "qfx_plan_upload: NULL plan");
+  const DeviceTables* t = nullptr;
+  return ensure_tables(p, &t);
+}
+
+extern "C" qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                     int64_t slice_begin, int64_t slice_end, void* workspace,
+                                     size_t ws_bytes, double* out, void* stream) {
+  if (!p || !x1 || !out || !workspace) return fail(QFX_EINVAL, "qfx_amplitudes: NULL argument");
+  if (n_batch < 1) return fail(QFX_EINVAL, "qfx_amplitudes: n_batch must be >= 1");
+  if (slice_begin < 0 || slice_end > p->n_slices || slice_begin >= slice_end)
+    return fail(QFX_EINVAL, "qfx_amplitudes: slice range outside [0, n_slices)");
+  if (((uintptr_t)workspace & 255) != 0) return fail(QFX_EINVAL, "qfx_amplitudes: workspace not 256-byte aligned");
+  if (((uintptr_t)out & 15) != 0) return fail(QFX_EINVAL, "qfx_amplitudes: out not 16-byte aligned");
+  if (p->precision != QFX_PREC_FP32_SIMT)
+    return fail(QFX_EUNSUPPORTED, "qfx_amplitudes: this plan's precision has no kernel here");
+  const Layout& L = p->layout;
+  const uint64_t hdr = L.header_per_item, ib = L.item_bytes;
+  int64_t G = (int64_t)(ws_bytes / (hdr + ib));
+  while (G > 0 && align256((uint64_t)G * hdr) + (uint64_t)G * ib > ws_bytes) --G;
+  if (G < 1) return fail(QFX_ENOMEM, "qfx_amplitudes: workspace smaller than qfx_plan_stats.workspace_min");
+  const int64_t n_items = (slice_end - slice_begin) * n_batch;
+  G = std::min<int64_t>({G, n_items, 65535});
+
+  const DeviceTables* tp = nullptr;
+  qfx_status s = ensure_tables(p, &tp);
+  if (s != QFX_OK) return s;
+  const DeviceTables& t = *tp;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n_open = (int)p->open_sites.size();
+  const int n_sites = p->n;
+  int64_t max_site = 1;
+  for (const auto& fs : p->sites) max_site = std::max(max_site, fs.size);
+  char* hdr_base = (char*)workspace;
+  char* items = hdr_base + align256((uint64_t)G * hdr);
+  const int nsteps = (int)p->steps.size();
+  const uint64_t site0 = L.sites + (uint64_t)p->sites[p->steps[0].site].offset * 8;
+  const uint64_t final_off = nsteps == 1 ? site0 : ((nsteps - 1) % 2 ? L.buf1 : L.buf0);
+
+  cudaError_t e = cudaMemsetAsync(out, 0, (size_t)(n_batch << n_open) * 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes: clearing out");
+  for (int64_t item0 = 0; item0 < n_items; item0 += G) {
+    const int g = (int)std::min<int64_t>(G, n_items - item0);
+    e = cudaMemsetAsync(hdr_base, 0, (size_t)g * hdr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes: clearing header");
+    int slot;
+    profile_begin(st, &slot);
+    int err = launch_fold(t, n_sites, max_site, (int)p->cut_dev.size(), x1, n_batch,
+                          slice_begin, item0, g, hdr_base, hdr, items, ib, L.sites, st);
+    profile_end(st, slot, -1, 0, 1, 0.0, 0.0);
+    if (err) return cuda_fail(err, "fold kernel");
+    err = launch_scale(t, n_sites, max_site, g, hdr_base, hdr, items, ib, L.sites, st);
+    if (err) return cuda_fail(err, "scale kernel");
+    for (int i = 1; i < nsteps; ++i) {
+      const Step& sp = p->steps[i];
+      const char* S = items + L.sites + (uint64_t)p->sites[sp.site].offset * 8;
+      const char* B = items + (i == 1 ? site0 : ((i - 1) % 2 ? L.buf1 : L.buf0));
+      char* C = items + (i % 2 ? L.buf1 : L.buf0);
+      profile_begin(st, &slot);
+      err = launch_step(S, (int64_t)(ib / 8), B, (int64_t)(ib / 8), C, (int64_t)(ib / 8), sp.P,
+                        sp.K, sp.N, sp.NL, sp.Sd, g, sp.variant, p->precision, st);
+      profile_end(st, slot, i, sp.variant, 0, sp.flops * g, sp.bytes * g);
+      if (err) return cuda_fail(err, "contraction step kernel");
+    }
+    err = launch_accumulate(t, n_sites, n_open, n_batch, item0, g, hdr_base, hdr, items, ib,
+                            final_off, out, st);
+    if (err) return cuda_fail(err, "accumulate kernel");
+  }
+  return QFX_OK;
+}
+
+extern "C" qfx_status qfx_sync(void* stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "qfx_sync");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "qfx_sync");
+  return QFX_OK;
+}
+
+extern "C" qfx_status qfx_contract_step(const void* S, const void* B, void* C, int64_t P,
+                                        int64_t K, int64_t N, int64_t NL, int64_t Sd,
+                                        int32_t precision, int32_t variant, void* stream) {
+  if (!S || !B || !C) return fail(QFX_EINVAL, "qfx_contract_step: NULL pointer");
+  if (P < 1 || K < 1 || N < 1 || NL < 1 || Sd < 1 || N % NL)
+    return fail(QFX_EINVAL, "qfx_contract_step: need positive sizes and NL | N");
+  if ((((uintptr_t)S) | ((uintptr_t)B) | ((uintptr_t)C)) & 15)
+    return fail(QFX_EINVAL, "qfx_contract_step: pointers must be 16-byte aligned");
+  if (precision != QFX_PREC_FP32_SIMT)
+    return fail(QFX_EUNSUPPORTED, "qfx_contract_step: precision has no kernel here");
+  if (variant >= 10) return fail(QFX_EINVAL, "qfx_contract_step: unknown variant");
+  if (variant >= 0 && variant < 5 && Sd % 2)
+    return fail(QFX_EINVAL, "qfx_contract_step: variants 0-4 need an even Sd");
+  int slot;
+  profile_begin(stream, &slot);
+  int v = variant < 0 ? pick_variant(N, Sd) : variant;
+  int err = launch_step(S, 0, B, 0, C, 0, P, K, N, NL, Sd, 1, v, precision, stream);
+  profile_end(stream, slot, -1, v, 0, 8.0 * P * K * N * Sd,
+              8.0 * ((double)P * K * Sd + (double)K * N + (double)P * N * Sd));
+  if (err) return cuda_fail(err, "qfx_contract_step");
+  return QFX_OK;
+}
+
+extern "C" qfx_status qfx_permute(const void* in, void* out, int32_t rank, const int64_t* shape,
+                                  const int32_t* perm, void* stream) {
+  if (!in || !out || !shape || !perm) return fail(QFX_EINVAL, "qfx_permute: NULL argument");
+  if (rank < 1 || rank > 10) return fail(QFX_EINVAL, "qfx_permute: rank must be 1..10");
+  int seen = 0;
+  for (int i = 0; i < rank; ++i) {
+    if (perm[i] < 0 || perm[i] >= rank || (seen >> perm[i]) & 1)
+      return fail(QFX_EINVAL, "qfx_permute: perm is not a permutation");
+    seen |= 1 << perm[i];
+    if (shape[i] < 0) return fail(QFX_EINVAL, "qfx_permute: negative extent");
+  }
+  int slot;
+  profile_begin(stream, &slot);
+  int err = launch_permute(in, out, rank, shape, perm, stream);
+  double el = 1;
+  for (int i = 0; i < rank; ++i) el *= (double)shape[i];
+  profile_end(stream, slot, -1, 0, 4, 0.0, 16.0 * el);
+  if (err) return cuda_fail(err, "qfx_permute");
+  return QFX_OK;
+}
+
+extern "C" qfx_status qfx_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return QFX_OK;
+}
+
+extern "C" qfx_status qfx_profile_collect(qfx_kernel_time* out, int32_t max, int32_t* n) {
+  if (!n) return fail(QFX_EINVAL, "qfx_profile_collect: NULL count");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  int32_t k = 0;
+  for (auto& r : g_prof) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_profile_collect");
+    if (out && k < max) out[k] = qfx_kernel_time{r.step, r.variant, r.kind, ms, r.flops, r.bytes};
+    ++k;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof.clear();
+  *n = k;
+  return QFX_OK;
+}
+
+extern "C" uint64_t qfx_launch_count(void) { return g_launches.load(); }
+extern "C" const char* qfx_last_error(void) { return g_err.c_str(); }
+extern "C" const char* qfx_version(void) { return "qfx 0.1 (sm_103a)"; }

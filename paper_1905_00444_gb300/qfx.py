@@ -1,0 +1,275 @@
+"""ctypes binding of libqfx (include/qfx.h).  Argument marshalling only: every step of
+the contraction runs in the library's CUDA kernels; PyTorch supplies device memory and
+streams.  If the library cannot be loaded this module raises on import -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from typing import Iterable, List, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqfx.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "qfx.h")
+
+QFX_OK, QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA, QFX_ETIMEOUT, QFX_EUNSUPPORTED, QFX_EPLAN = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EUNSUPPORTED", "EPLAN"]
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 2}
+
+
+class QfxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"qfx {name}: {msg}")
+
+
+class Gate(C.Structure):
+    _fields_ = [("layer", C.c_int32), ("q0", C.c_int32), ("q1", C.c_int32), ("kind", C.c_int32),
+                ("mat", C.c_double * 8)]
+
+
+class Cut(C.Structure):
+    _fields_ = [("qa", C.c_int32), ("qb", C.c_int32), ("size", C.c_int32)]
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("max_intermediate_bytes", C.c_uint64), ("open_sites", C.POINTER(C.c_int32)),
+                ("n_open", C.c_int32), ("forced_cuts", C.POINTER(Cut)),
+                ("n_forced_cuts", C.c_int32), ("precision", C.c_int32),
+                ("plan_family", C.c_int32), ("reserved", C.c_int32)]
+
+
+class PlanStats(C.Structure):
+    _fields_ = [("n_slices", C.c_int64), ("n_steps", C.c_int32), ("n_open", C.c_int32),
+                ("n_cuts", C.c_int32), ("n_sites", C.c_int32), ("flops_per_item", C.c_double),
+                ("bytes_per_item", C.c_double), ("max_elements", C.c_int64),
+                ("item_bytes", C.c_uint64), ("workspace_min", C.c_uint64),
+                ("largest_step", C.c_int32), ("precision", C.c_int32)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("site", C.c_int32), ("variant", C.c_int32), ("P", C.c_int64), ("K", C.c_int64),
+                ("N", C.c_int64), ("NL", C.c_int64), ("Sd", C.c_int64), ("flops", C.c_double),
+                ("bytes", C.c_double)]
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("step", C.c_int32), ("variant", C.c_int32), ("kind", C.c_int32),
+                ("ms", C.c_float), ("flops", C.c_double), ("bytes", C.c_double)]
+
+
+def _declare(lib):
+    vp, i32, i64, u64, st = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_int
+    sig = {
+        "qfx_circuit_create": (st, [i32, i32, C.POINTER(Gate), i64, C.POINTER(vp)]),
+        "qfx_circuit_from_text": (st, [C.c_char_p, C.POINTER(vp)]),
+        "qfx_circuit_destroy": (None, [vp]),
+        "qfx_plan_create": (st, [vp, C.POINTER(PlanOpts), C.POINTER(vp)]),
+        "qfx_plan_destroy": (None, [vp]),
+        "qfx_plan_info": (st, [vp, C.POINTER(PlanStats)]),
+        "qfx_workspace_bytes": (u64, [vp, i64]),
+        "qfx_plan_step": (st, [vp, i32, C.POINTER(StepInfo)]),
+        "qfx_plan_cut": (st, [vp, i32, C.POINTER(Cut)]),
+        "qfx_plan_open_sites": (st, [vp, C.POINTER(i32)]),
+        "qfx_plan_upload": (st, [vp]),
+        "qfx_amplitudes": (st, [vp, vp, i64, i64, i64, vp, C.c_size_t, vp, vp]),
+        "qfx_sync": (st, [vp]),
+        "qfx_contract_step": (st, [vp, vp, vp, i64, i64, i64, i64, i64, i32, i32, vp]),
+        "qfx_permute": (st, [vp, vp, i32, C.POINTER(i64), C.POINTER(i32), vp]),
+        "qfx_profile_enable": (st, [i32]),
+        "qfx_profile_collect": (st, [C.POINTER(KernelTime), i32, C.POINTER(i32)]),
+        "qfx_launch_count": (u64, []),
+        "qfx_last_error": (C.c_char_p, []),
+        "qfx_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libqfx.so is not built ({LIB_PATH}); run paper_1905_00444_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    _declare(lib)
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int):
+    if status != QFX_OK:
+        raise QfxError(status, lib.qfx_last_error().decode(errors="replace"))
+
+
+def header_symbols() -> List[str]:
+    """Every function declared in include/qfx.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(qfx_[a-z0-9_]+)\s*\(", text)))
+
+
+def version() -> str:
+    return lib.qfx_version().decode()
+
+
+def launch_count() -> int:
+    return int(lib.qfx_launch_count())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Circuit:
+    """Validated circuit owned by the library.  `src` has .rows, .cols and .gates, each
+    gate with .layer, .q0, .q1, .kind and .mat (2x2 complex, or 4 diagonal entries)."""
+
+    def __init__(self, src=None, *, text: Optional[str] = None):
+        h = C.c_void_p()
+        if text is not None:
+            _check(lib.qfx_circuit_from_text(text.encode(), C.byref(h)))
+            self.rows = self.cols = None
+        else:
+            arr = (Gate * max(1, len(src.gates)))()
+            for i, g in enumerate(src.gates):
+                arr[i].layer, arr[i].q0, arr[i].q1, arr[i].kind = g.layer, g.q0, g.q1, g.kind
+                flat = list(g.mat.reshape(-1))
+                for j, v in enumerate(flat):
+                    arr[i].mat[2 * j] = float(v.real)
+                    arr[i].mat[2 * j + 1] = float(v.imag)
+            _check(lib.qfx_circuit_create(src.rows, src.cols, arr, len(src.gates), C.byref(h)))
+            self.rows, self.cols = src.rows, src.cols
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib.qfx_circuit_destroy(self._h)
+            self._h = None
+
+
+class Plan:
+    """Contraction plan (order, x2 open sites, cuts, workspace layout)."""
+
+    def __init__(self, circuit: Circuit, *, open_sites: Optional[Sequence[int]] = None,
+                 n_open: int = 0, max_intermediate_bytes: int = 0,
+                 cuts: Iterable = (), precision: str = "fp32"):
+        opts = PlanOpts()
+        opts.max_intermediate_bytes = int(max_intermediate_bytes)
+        self._open_arr = None
+        if open_sites is not None:
+            self._open_arr = (C.c_int32 * max(1, len(open_sites)))(*open_sites)
+            opts.open_sites = C.cast(self._open_arr, C.POINTER(C.c_int32))
+            opts.n_open = len(open_sites)
+        else:
+            opts.n_open = n_open
+        cuts = list(cuts)
+        self._cut_arr = (Cut * max(1, len(cuts)))(*[Cut(a, b, s) for (a, b, s) in cuts])
+        opts.forced_cuts = C.cast(self._cut_arr, C.POINTER(Cut))
+        opts.n_forced_cuts = len(cuts)
+        opts.precision = PRECISIONS[precision]
+        h = C.c_void_p()
+        _check(lib.qfx_plan_create(circuit._h, C.byref(opts), C.byref(h)))
+        self._h = h
+        self._circuit = circuit
+        st = PlanStats()
+        _check(lib.qfx_plan_info(h, C.byref(st)))
+        self.stats = {f: getattr(st, f) for f, _ in PlanStats._fields_}
+        self.steps = []
+        for i in range(st.n_steps):
+            si = StepInfo()
+            _check(lib.qfx_plan_step(h, i, C.byref(si)))
+            self.steps.append({f: getattr(si, f) for f, _ in StepInfo._fields_})
+        self.cuts = []
+        for i in range(st.n_cuts):
+            c = Cut()
+            _check(lib.qfx_plan_cut(h, i, C.byref(c)))
+            self.cuts.append((c.qa, c.qb, c.size))
+        arr = (C.c_int32 * max(1, st.n_open))()
+        _check(lib.qfx_plan_open_sites(h, arr))
+        self.open_sites = [arr[i] for i in range(st.n_open)]
+
+    @property
+    def n_slices(self) -> int:
+        return self.stats["n_slices"]
+
+    def workspace_bytes(self, n_concurrent: int = 1) -> int:
+        return int(lib.qfx_workspace_bytes(self._h, n_concurrent))
+
+    def upload(self):
+        _check(lib.qfx_plan_upload(self._h))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib.qfx_plan_destroy(self._h)
+            self._h = None
+
+
+def amplitudes(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Optional[int] = None,
+               workspace=None, out=None, stream=None):
+    """Amplitudes [n_batch, 2^n_open] (torch complex128 on x1's device).
+
+    x1: torch int64/uint64 CUDA tensor of bitstrings.  workspace: torch uint8 CUDA tensor
+    (default: room for one work item)."""
+    import torch
+    if not x1.is_cuda:
+        raise ValueError("x1 must be a CUDA tensor")
+    n_batch = x1.numel()
+    if slice_end is None:
+        slice_end = plan.n_slices
+    if workspace is None:
+        workspace = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=x1.device)
+    if out is None:
+        out = torch.empty((n_batch, 1 << len(plan.open_sites)), dtype=torch.complex128,
+                          device=x1.device)
+    _check(lib.qfx_amplitudes(plan._h, x1.data_ptr(), n_batch, slice_begin, slice_end,
+                              workspace.data_ptr(), workspace.numel(), out.data_ptr(),
+                              _stream_ptr(stream)))
+    return out
+
+
+def sync(stream=None):
+    _check(lib.qfx_sync(_stream_ptr(stream)))
+
+
+def contract_step(S, B, P, K, N, NL, Sd, *, out=None, variant: int = -1, precision="fp32",
+                  stream=None):
+    """C[nh][p][nl][s] = sum_k S[k][nh*NL+nl] B[p][k][s] on complex64 CUDA tensors."""
+    import torch
+    if out is None:
+        out = torch.empty(P * N * Sd, dtype=torch.complex64, device=S.device)
+    _check(lib.qfx_contract_step(S.data_ptr(), B.data_ptr(), out.data_ptr(), P, K, N, NL, Sd,
+                                 PRECISIONS[precision], variant, _stream_ptr(stream)))
+    return out
+
+
+def permute(x, shape: Sequence[int], perm: Sequence[int], *, out=None, stream=None):
+    """out = x viewed with `shape`, axes reordered by `perm` (complex64 CUDA tensors)."""
+    import torch
+    if out is None:
+        out = torch.empty(x.numel(), dtype=torch.complex64, device=x.device)
+    r = len(shape)
+    sh = (C.c_int64 * r)(*shape)
+    pm = (C.c_int32 * r)(*perm)
+    _check(lib.qfx_permute(x.data_ptr(), out.data_ptr(), r, sh, pm, _stream_ptr(stream)))
+    return out
+
+
+def profile_enable(on: bool = True):
+    _check(lib.qfx_profile_enable(1 if on else 0))
+
+
+def profile_collect(max_records: int = 1 << 16):
+    arr = (KernelTime * max_records)()
+    n = C.c_int32()
+    _check(lib.qfx_profile_collect(arr, max_records, C.byref(n)))
+    return [{f: getattr(arr[i], f) for f, _ in KernelTime._fields_}
+            for i in range(min(n.value, max_records))]

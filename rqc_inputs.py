@@ -211,15 +211,12 @@ def random_complex(shape, seed: int, dtype=np.complex64) -> np.ndarray:
 
 
 def circuit_to_text(c: Circuit) -> str:
-    """The project's text format: header 'grid R C', then one gate per line:
-    'layer kind q0 [q1] [re im ...]'; fixed kinds carry no matrix."""
+    """The project's text format: header 'grid R C', then one gate per line,
+    'layer KIND q0 [q1] v0 .. v7', with the gate's 8 matrix values (re, im interleaved:
+    the 2x2 matrix row-major, or the 4 diagonal entries of a two-qubit gate)."""
     lines = [f"grid {c.rows} {c.cols}"]
     for g in c.gates:
-        if g.kind in (U1, U2):
-            vals = " ".join(f"{v.real:.17g} {v.imag:.17g}" for v in g.mat.reshape(-1))
-            qs = f"{g.q0} {g.q1}" if g.two_qubit else f"{g.q0}"
-            lines.append(f"{g.layer} {KIND_NAMES[g.kind]} {qs} {vals}")
-        else:
-            qs = f"{g.q0} {g.q1}" if g.two_qubit else f"{g.q0}"
-            lines.append(f"{g.layer} {KIND_NAMES[g.kind]} {qs}")
+        vals = " ".join(f"{v.real:.17g} {v.imag:.17g}" for v in np.asarray(g.mat).reshape(-1))
+        qs = f"{g.q0} {g.q1}" if g.two_qubit else f"{g.q0}"
+        lines.append(f"{g.layer} {KIND_NAMES[g.kind]} {qs} {vals}")
     return "\n".join(lines) + "\n"

@@ -1,0 +1,159 @@
+"""Host-side tests of libqfx through its C ABI: loading, exported symbols, circuit
+validation, the planner's shapes and flop counts (Eq. 1), cut handling, argument checks.
+No GPU work is launched here."""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+import rqc_inputs as ri
+from oracle import primitives
+
+qfx = pytest.importorskip("paper_1905_00444_gb300")
+q = qfx.qfx
+
+
+def test_library_exports_every_header_symbol():
+    syms = q.header_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(q.lib, s), f"libqfx.so does not export {s}"
+
+
+def test_version_and_no_launches_on_host():
+    assert "sm_103a" in qfx.version()
+    ri_c = ri.rqc(3, 3, 8, seed=0)
+    p = qfx.Plan(qfx.Circuit(ri_c), n_open=2)
+    assert p.stats["n_steps"] == 9
+    assert qfx.launch_count() == 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(q0=9), dict(q1=5, kind=ri.CZ),           # out of range / not neighbours (0-5 on 3x3)
+    dict(layer=-1), dict(kind=ri.CZ),             # kind/arity mismatch (1q gate labelled CZ)
+])
+def test_circuit_validation_rejects(bad):
+    c = ri.rqc(3, 3, 2, seed=0)
+    g = c.gates[0]
+    for k, v in bad.items():
+        setattr(g, k, v)
+    if g.q1 >= 0 and g.mat.size != 4:
+        g.mat = ri.DIAG_CZ.copy()
+    with pytest.raises(qfx.QfxError) as e:
+        qfx.Circuit(c)
+    assert e.value.status == q.QFX_EINVAL
+
+
+def test_layer_disjointness_checked():
+    c = ri.rqc(2, 2, 0)
+    c.gates.append(ri.Gate(0, 0, -1, ri.H, ri.MAT_H.copy()))   # qubit 0 twice in layer 0
+    with pytest.raises(qfx.QfxError):
+        qfx.Circuit(c)
+
+
+def test_text_format_roundtrip_plan_identical():
+    c = ri.rqc(3, 4, 16, seed=5)
+    a = qfx.Plan(qfx.Circuit(c), n_open=3)
+    b = qfx.Plan(qfx.Circuit(text=ri.circuit_to_text(c)), n_open=3)
+    assert a.stats == b.stats and a.steps == b.steps
+
+
+def test_text_format_errors_name_the_line():
+    with pytest.raises(qfx.QfxError, match="line 2"):
+        qfx.Circuit(text="grid 2 2\n0 H 0 1 0\n")
+    with pytest.raises(qfx.QfxError, match="unknown kind"):
+        qfx.Circuit(text="grid 2 2\n0 FOO 0 1 0 0 0 0 0 0 0\n")
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 16), (5, 5, 24), (6, 6, 24), (7, 7, 32), (8, 8, 32),
+                                   (3, 5, 8), (5, 3, 8), (2, 7, 16), (1, 6, 8)])
+def test_plan_steps_obey_eq1(shape):
+    rows, cols, d = shape
+    c = ri.rqc(rows, cols, d, seed=0)
+    p = qfx.Plan(qfx.Circuit(c), n_open=min(4, rows * cols))
+    total = 0.0
+    for s in p.steps[1:]:
+        P, K, N, Sd = s["P"], s["K"], s["N"], s["Sd"]
+        v0, v1, v2 = P * K * Sd, K * N, P * N * Sd        # input boundary, site, output
+        assert s["flops"] == pytest.approx(primitives.flops_eq1(v0, v1, v2), rel=1e-12)
+        assert s["N"] % s["NL"] == 0
+        total += s["flops"]
+    assert p.stats["flops_per_item"] == pytest.approx(total, rel=1e-12)
+    assert sorted(s["site"] for s in p.steps) == list(range(rows * cols))
+    # sweep runs along the shorter dimension
+    chi = 2 ** (d // 8)
+    L = min(rows, cols)
+    if rows > 1 and cols > 1 and d % 8 == 0:
+        assert p.stats["max_elements"] <= chi ** (L + 1) * 2 ** 4
+
+
+def test_plan_7x7x32_matches_hand_count():
+    # chi = 16, lines of 7: 25 interior kink steps of 8*16^10 flops each dominate
+    c = ri.rqc(7, 7, 32, seed=0)
+    p = qfx.Plan(qfx.Circuit(c), n_open=6)
+    assert p.stats["max_elements"] == 2 ** 32
+    big = [s for s in p.steps if s["flops"] == 8 * 16 ** 10]
+    assert len(big) == 25
+    for s in big:
+        assert (s["K"], s["N"], s["P"] * s["Sd"]) == (256, 256, 2 ** 24)
+    assert p.stats["flops_per_item"] == pytest.approx(2.2558e14, rel=1e-3)
+    assert p.open_sites == [13, 20, 27, 34, 41, 48]
+
+
+def test_forced_cut_slices_and_cap():
+    c = ri.rqc(4, 4, 16, seed=0)
+    full = qfx.Plan(qfx.Circuit(c), n_open=2)
+    cut = qfx.Plan(qfx.Circuit(c), n_open=2, cuts=[(5, 6, 1), (9, 13, 2)])
+    assert cut.n_slices == 4 * 2
+    assert cut.cuts == [(5, 6, 1), (9, 13, 2)]
+    cap = full.stats["max_elements"] * 8 // 4
+    capped = qfx.Plan(qfx.Circuit(c), n_open=2, max_intermediate_bytes=cap)
+    assert capped.stats["max_elements"] * 8 <= cap
+    assert capped.n_slices > 1
+
+
+@pytest.mark.parametrize("cuts", [[(0, 5, 1)], [(1, 2, 3)], [(1, 2, 8)], [(1, 2, 1), (2, 1, 1)]])
+def test_bad_cuts_rejected(cuts):
+    c = ri.rqc(4, 4, 16, seed=0)
+    with pytest.raises(qfx.QfxError):
+        qfx.Plan(qfx.Circuit(c), cuts=cuts)
+
+
+def test_impossible_cap_is_eplan():
+    c = ri.rqc(3, 3, 8, seed=0)
+    with pytest.raises(qfx.QfxError) as e:
+        qfx.Plan(qfx.Circuit(c), n_open=4, max_intermediate_bytes=8)
+    assert e.value.status == q.QFX_EPLAN
+
+
+def test_open_site_validation():
+    c = ri.rqc(3, 3, 8, seed=0)
+    with pytest.raises(qfx.QfxError):
+        qfx.Plan(qfx.Circuit(c), open_sites=[1, 1])
+    with pytest.raises(qfx.QfxError):
+        qfx.Plan(qfx.Circuit(c), open_sites=[9])
+    p = qfx.Plan(qfx.Circuit(c), open_sites=[4, 0, 8])
+    assert p.open_sites == [4, 0, 8]
+
+
+def test_amplitudes_argument_checks_before_any_launch():
+    c = ri.rqc(2, 2, 8, seed=0)
+    p = qfx.Plan(qfx.Circuit(c), n_open=1)
+    f = q.lib.qfx_amplitudes
+    assert f(p._h, None, 1, 0, 1, None, 0, None, None) == q.QFX_EINVAL
+    fake = C.c_void_p(1 << 20)
+    assert f(p._h, fake, 0, 0, 1, fake, 1 << 20, fake, None) == q.QFX_EINVAL      # n_batch
+    assert f(p._h, fake, 1, 0, 2, fake, 1 << 20, fake, None) == q.QFX_EINVAL      # slices
+    assert f(p._h, fake, 1, 0, 1, C.c_void_p((1 << 20) + 8), 1 << 20, fake, None) == q.QFX_EINVAL
+    assert f(p._h, fake, 1, 0, 1, fake, 16, fake, None) == q.QFX_ENOMEM
+    assert qfx.launch_count() == 0
+
+
+def test_permute_and_step_argument_checks():
+    fake = C.c_void_p(1 << 20)
+    sh = (C.c_int64 * 3)(2, 3, 4)
+    bad = (C.c_int32 * 3)(0, 0, 1)
+    assert q.lib.qfx_permute(fake, fake, 3, sh, bad, None) == q.QFX_EINVAL
+    assert q.lib.qfx_contract_step(fake, fake, fake, 1, 1, 3, 2, 1, 0, -1, None) == q.QFX_EINVAL
+    assert q.lib.qfx_contract_step(fake, fake, fake, 1, 1, 2, 2, 3, 0, 0, None) == q.QFX_EINVAL
