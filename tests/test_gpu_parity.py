@@ -108,9 +108,13 @@ def test_shapes_vs_statevector(qfx, shape):
 
 def test_identity_circuit_exact(qfx):
     c = ri.rqc(3, 4, 0)                        # H then H: amp = delta(x, 0)
-    plan, out = run(qfx, c, [0, 5], n_open=12)
+    plan, out = run(qfx, c, [0, 5], n_open=12)  # all sites open: x1 is ignored
     want = np.zeros((2, 1 << 12))
-    want[0, 0] = 1.0
+    want[:, 0] = 1.0
+    np.testing.assert_array_equal(out, want)
+    plan, out = run(qfx, c, [0, 5, 16], n_open=3)
+    want = np.zeros((3, 8))
+    want[0, 0] = 1.0                           # x1 = 5 and 16 have closed bits set
     np.testing.assert_array_equal(out, want)
 
 
