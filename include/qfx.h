@@ -175,6 +175,24 @@ qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int64_t n_batch
                           int64_t slice_begin, int64_t slice_end, void* workspace,
                           size_t ws_bytes, double* out, void* stream);
 
+/* Size of the scratch array compiled into the library for qfx_amplitudes_static. */
+#define QFX_STATIC_SCRATCH_BYTES (64ull << 20)
+
+/* qfx_amplitudes without a caller workspace, for callers that cannot allocate device
+ * memory (a host application whose memory manager owns the device, code that cannot
+ * afford cudaMalloc's implicit synchronisation, a plugin handed only its buffers).
+ * The paper has no counterpart: it is an interface convenience of this library.
+ *   Same arguments and results as qfx_amplitudes, minus the workspace: scratch is a
+ *   file-scope device array of QFX_STATIC_SCRATCH_BYTES (64 MiB) that every GPU loading
+ *   the library holds until exit.  The plan's tables plus qfx_workspace_bytes(p, 1) must
+ *   fit in it, else QFX_ENOMEM with both sizes in the message.
+ *   Allocates nothing.  The first call on a device looks up the array's device address
+ *   (make it before any stream capture).  All calls share the array: calls that overlap
+ *   on the GPU race, and each call rewrites what it reads. */
+qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                 int64_t slice_begin, int64_t slice_end, double* out,
+                                 void* stream);
+
 /* Waits for `stream` and reports any asynchronous CUDA error as QFX_ECUDA. */
 qfx_status qfx_sync(void* stream);
 

@@ -153,6 +153,17 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
 // device tables of a plan (uploaded once per device)
 qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out);
 void free_tables(DeviceTables& t);
+// host image of a plan's tables; offs[] = byte offsets of sites, events, mats, cuts, perm
+size_t pack_tables(const qfx_plan* p, std::vector<char>& host, size_t offs[5]);
+DeviceTables tables_at(void* base, const size_t offs[5]);
+
+// the executor behind qfx_amplitudes (argument checks, items in flight, run)
+qfx_status check_amplitudes_args(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                 int64_t slice_begin, int64_t slice_end, double* out);
+int64_t items_in_flight(const qfx_plan* p, size_t ws_bytes);
+qfx_status exec_amplitudes(const qfx_plan* p, const DeviceTables& t, const uint64_t* x1,
+                           int64_t n_batch, int64_t slice_begin, int64_t slice_end,
+                           void* workspace, int64_t G, double* out, void* stream);
 
 // profiling hooks
 bool profile_on();

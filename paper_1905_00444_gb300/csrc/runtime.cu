@@ -92,6 +92,40 @@ void free_tables(DeviceTables& t) {
   t = DeviceTables{};
 }
 
+size_t pack_tables(const qfx_plan* p, std::vector<char>& host, size_t offs[5]) {
+  const size_t s_sites = align256(p->sites.size() * sizeof(FoldSite));
+  const size_t s_ev = align256(std::max<size_t>(1, p->events.size()) * sizeof(FoldEvent));
+  const size_t s_mats = align256(std::max<size_t>(1, p->mats.size()) * sizeof(double));
+  const size_t s_cuts = align256(std::max<size_t>(1, p->cut_dev.size()) * sizeof(CutDev));
+  const size_t s_perm = align256(std::max<size_t>(1, p->open_perm.size()) * sizeof(int32_t));
+  offs[0] = 0;
+  offs[1] = s_sites;
+  offs[2] = offs[1] + s_ev;
+  offs[3] = offs[2] + s_mats;
+  offs[4] = offs[3] + s_cuts;
+  const size_t total = offs[4] + s_perm;
+  host.assign(total, 0);
+  char* h = host.data();
+  std::memcpy(h + offs[0], p->sites.data(), p->sites.size() * sizeof(FoldSite));
+  std::memcpy(h + offs[1], p->events.data(), p->events.size() * sizeof(FoldEvent));
+  std::memcpy(h + offs[2], p->mats.data(), p->mats.size() * sizeof(double));
+  std::memcpy(h + offs[3], p->cut_dev.data(), p->cut_dev.size() * sizeof(CutDev));
+  std::memcpy(h + offs[4], p->open_perm.data(), p->open_perm.size() * sizeof(int32_t));
+  return total;
+}
+
+DeviceTables tables_at(void* base, const size_t offs[5]) {
+  char* b = (char*)base;
+  DeviceTables t;
+  t.base = base;
+  t.sites = (const FoldSite*)(b + offs[0]);
+  t.events = (const FoldEvent*)(b + offs[1]);
+  t.mats = (const double*)(b + offs[2]);
+  t.cuts = (const CutDev*)(b + offs[3]);
+  t.open_perm = (const int32_t*)(b + offs[4]);
+  return t;
+}
+
 qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -100,70 +134,46 @@ qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out) {
   if ((int)p->dev.size() <= dev) p->dev.resize(dev + 1);
   DeviceTables& t = p->dev[dev];
   if (!t.base) {
-    const size_t s_sites = align256(p->sites.size() * sizeof(FoldSite));
-    const size_t s_ev = align256(std::max<size_t>(1, p->events.size()) * sizeof(FoldEvent));
-    const size_t s_mats = align256(std::max<size_t>(1, p->mats.size()) * sizeof(double));
-    const size_t s_cuts = align256(std::max<size_t>(1, p->cut_dev.size()) * sizeof(CutDev));
-    const size_t s_perm = align256(std::max<size_t>(1, p->open_perm.size()) * sizeof(int32_t));
-    const size_t total = s_sites + s_ev + s_mats + s_cuts + s_perm;
-    std::vector<char> host(total, 0);
-    char* h = host.data();
-    std::memcpy(h, p->sites.data(), p->sites.size() * sizeof(FoldSite));
-    std::memcpy(h + s_sites, p->events.data(), p->events.size() * sizeof(FoldEvent));
-    std::memcpy(h + s_sites + s_ev, p->mats.data(), p->mats.size() * sizeof(double));
-    std::memcpy(h + s_sites + s_ev + s_mats, p->cut_dev.data(), p->cut_dev.size() * sizeof(CutDev));
-    std::memcpy(h + s_sites + s_ev + s_mats + s_cuts, p->open_perm.data(),
-                p->open_perm.size() * sizeof(int32_t));
+    std::vector<char> host;
+    size_t offs[5];
+    const size_t total = pack_tables(p, host, offs);
     void* d = nullptr;
     e = cudaMalloc(&d, total);
     if (e != cudaSuccess) return cuda_fail(e, "plan table upload (cudaMalloc)");
     e = cudaMemcpy(d, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "plan table upload (cudaMemcpy)"); }
-    char* b = (char*)d;
-    t.base = d;
-    t.sites = (const FoldSite*)b;
-    t.events = (const FoldEvent*)(b + s_sites);
-    t.mats = (const double*)(b + s_sites + s_ev);
-    t.cuts = (const CutDev*)(b + s_sites + s_ev + s_mats);
-    t.open_perm = (const int32_t*)(b + s_sites + s_ev + s_mats + s_cuts);
+    t = tables_at(d, offs);
   }
   *out = &t;
   return QFX_OK;
 }
 
-}  // namespace qfx
-
-using namespace qfx;
-
-extern "C" qfx_status qfx_plan_upload(const qfx_plan* p) {
-  if (!p) return fail(QFX_EINVAL, "qfx_plan_upload: NULL plan");
-  const DeviceTables* t = nullptr;
-  return ensure_tables(p, &t);
-}
-
-extern "C" qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
-                                     int64_t slice_begin, int64_t slice_end, void* workspace,
-                                     size_t ws_bytes, double* out, void* stream) {
-  if (!p || !x1 || !out || !workspace) return fail(QFX_EINVAL, "qfx_amplitudes: NULL argument");
+qfx_status check_amplitudes_args(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                 int64_t slice_begin, int64_t slice_end, double* out) {
+  if (!p || !x1 || !out) return fail(QFX_EINVAL, "qfx_amplitudes: NULL argument");
   if (n_batch < 1) return fail(QFX_EINVAL, "qfx_amplitudes: n_batch must be >= 1");
   if (slice_begin < 0 || slice_end > p->n_slices || slice_begin >= slice_end)
     return fail(QFX_EINVAL, "qfx_amplitudes: slice range outside [0, n_slices)");
-  if (((uintptr_t)workspace & 255) != 0) return fail(QFX_EINVAL, "qfx_amplitudes: workspace not 256-byte aligned");
   if (((uintptr_t)out & 15) != 0) return fail(QFX_EINVAL, "qfx_amplitudes: out not 16-byte aligned");
   if (p->precision != QFX_PREC_FP32_SIMT)
     return fail(QFX_EUNSUPPORTED, "qfx_amplitudes: this plan's precision has no kernel here");
-  const Layout& L = p->layout;
-  const uint64_t hdr = L.header_per_item, ib = L.item_bytes;
+  return QFX_OK;
+}
+
+int64_t items_in_flight(const qfx_plan* p, size_t ws_bytes) {
+  const uint64_t hdr = p->layout.header_per_item, ib = p->layout.item_bytes;
   int64_t G = (int64_t)(ws_bytes / (hdr + ib));
   while (G > 0 && align256((uint64_t)G * hdr) + (uint64_t)G * ib > ws_bytes) --G;
-  if (G < 1) return fail(QFX_ENOMEM, "qfx_amplitudes: workspace smaller than qfx_plan_stats.workspace_min");
+  return G;
+}
+
+qfx_status exec_amplitudes(const qfx_plan* p, const DeviceTables& t, const uint64_t* x1,
+                           int64_t n_batch, int64_t slice_begin, int64_t slice_end,
+                           void* workspace, int64_t G, double* out, void* stream) {
+  const Layout& L = p->layout;
+  const uint64_t hdr = L.header_per_item, ib = L.item_bytes;
   const int64_t n_items = (slice_end - slice_begin) * n_batch;
   G = std::min<int64_t>({G, n_items, 65535});
-
-  const DeviceTables* tp = nullptr;
-  qfx_status s = ensure_tables(p, &tp);
-  if (s != QFX_OK) return s;
-  const DeviceTables& t = *tp;
   cudaStream_t st = (cudaStream_t)stream;
   const int n_open = (int)p->open_sites.size();
   const int n_sites = p->n;
@@ -205,6 +215,31 @@ extern "C" qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int6
     if (err) return cuda_fail(err, "accumulate kernel");
   }
   return QFX_OK;
+}
+
+}  // namespace qfx
+
+using namespace qfx;
+
+extern "C" qfx_status qfx_plan_upload(const qfx_plan* p) {
+  if (!p) return fail(QFX_EINVAL, "qfx_plan_upload: NULL plan");
+  const DeviceTables* t = nullptr;
+  return ensure_tables(p, &t);
+}
+
+extern "C" qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                     int64_t slice_begin, int64_t slice_end, void* workspace,
+                                     size_t ws_bytes, double* out, void* stream) {
+  qfx_status s = check_amplitudes_args(p, x1, n_batch, slice_begin, slice_end, out);
+  if (s != QFX_OK) return s;
+  if (!workspace) return fail(QFX_EINVAL, "qfx_amplitudes: NULL argument");
+  if (((uintptr_t)workspace & 255) != 0) return fail(QFX_EINVAL, "qfx_amplitudes: workspace not 256-byte aligned");
+  const int64_t G = items_in_flight(p, ws_bytes);
+  if (G < 1) return fail(QFX_ENOMEM, "qfx_amplitudes: workspace smaller than qfx_plan_stats.workspace_min");
+  const DeviceTables* tp = nullptr;
+  s = ensure_tables(p, &tp);
+  if (s != QFX_OK) return s;
+  return exec_amplitudes(p, *tp, x1, n_batch, slice_begin, slice_end, workspace, G, out, stream);
 }
 
 extern "C" qfx_status qfx_sync(void* stream) {

@@ -76,6 +76,7 @@ def _declare(lib):
         "qfx_plan_open_sites": (st, [vp, C.POINTER(i32)]),
         "qfx_plan_upload": (st, [vp]),
         "qfx_amplitudes": (st, [vp, vp, i64, i64, i64, vp, C.c_size_t, vp, vp]),
+        "qfx_amplitudes_static": (st, [vp, vp, i64, i64, i64, vp, vp]),
         "qfx_sync": (st, [vp]),
         "qfx_contract_step": (st, [vp, vp, vp, i64, i64, i64, i64, i64, i32, i32, vp]),
         "qfx_permute": (st, [vp, vp, i32, C.POINTER(i64), C.POINTER(i32), vp]),
@@ -233,6 +234,28 @@ def amplitudes(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Optional[int]
     _check(lib.qfx_amplitudes(plan._h, x1.data_ptr(), n_batch, slice_begin, slice_end,
                               workspace.data_ptr(), workspace.numel(), out.data_ptr(),
                               _stream_ptr(stream)))
+    return out
+
+
+STATIC_SCRATCH_BYTES = 64 << 20   # QFX_STATIC_SCRATCH_BYTES in include/qfx.h
+
+
+def amplitudes_static(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Optional[int] = None,
+                      out=None, stream=None):
+    """As amplitudes(), but the library's built-in 64 MiB scratch array replaces the
+    caller's workspace (for callers that cannot allocate device memory; the output
+    buffer is still the caller's).  Calls that overlap on the GPU race on that array."""
+    import torch
+    if not x1.is_cuda:
+        raise ValueError("x1 must be a CUDA tensor")
+    n_batch = x1.numel()
+    if slice_end is None:
+        slice_end = plan.n_slices
+    if out is None:
+        out = torch.empty((n_batch, 1 << len(plan.open_sites)), dtype=torch.complex128,
+                          device=x1.device)
+    _check(lib.qfx_amplitudes_static(plan._h, x1.data_ptr(), n_batch, slice_begin, slice_end,
+                                     out.data_ptr(), _stream_ptr(stream)))
     return out
 
 
