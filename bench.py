@@ -300,18 +300,47 @@ def run_qfx(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- kernel case
+def run_kstep(args):
+    """The dominant contraction step alone (K = N = 256 as in the 7x7x32 interior steps)
+    on 2^18 of its 2^24 columns: 2 GiB in, 2 GiB out (larger than L2), the small case
+    used for ncu captures of that kernel."""
+    import torch
+    import paper_1905_00444_gb300 as qfx
+    P, K, N, NL, Sd = 1, 256, 256, 256, 1 << 18
+    S = torch.from_numpy(ri.random_complex((K * N,), seed=1)).cuda()
+    B = torch.from_numpy(ri.random_complex((P * K * Sd,), seed=2)).cuda()
+    C = torch.empty(P * N * Sd, dtype=torch.complex64, device="cuda")
+    for _ in range(args.warmup):
+        qfx.contract_step(S, B, P, K, N, NL, Sd, out=C)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        qfx.contract_step(S, B, P, K, N, NL, Sd, out=C)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = 8.0 * P * K * N * Sd
+    print(json.dumps({"workload": "dominant step (P,K,N,Sd)=(1,256,256,2^18)", "ms": ms,
+                      "tflops": flops / ms / 1e9, "steps": args.steps}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="qfx", choices=["qfx", "reference"])
-    ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS) + ["kstep"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "kstep":
+        return run_kstep(args)
     return run_qfx(args)
 
 
