@@ -36,9 +36,10 @@ WORKLOADS = {
     "full": dict(rows=7, cols=7, depth=32, n_open=6, seed=0),
     "small": dict(rows=7, cols=7, depth=24, n_open=6, seed=0),   # profiling case (128 MiB boundary)
 }
-# DRAM traffic per launch of the dominant kernel, from one ncu capture of the same
-# kernel build; None until captured (see profiles/).
-TRAFFIC = {"full": None, "small": None}
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the
+# same kernel build on the small case (2^18 columns, 1.028e9 B) scaled by the columns of a
+# full launch (2^24): profiles/cgemm_step_simt_dominant_step_ncu_full.md.
+TRAFFIC = {"full": 1.028e9 * 64, "small": None}
 
 
 def workload_desc(w):
@@ -303,7 +304,7 @@ def run_qfx(args):
 # ----------------------------------------------------------------------------- kernel case
 def run_kstep(args):
     """The dominant contraction step alone (K = N = 256 as in the 7x7x32 interior steps)
-    on 2^18 of its 2^24 columns: 2 GiB in, 2 GiB out (larger than L2), the small case
+    on 2^18 of its 2^24 columns: 512 MiB in, 512 MiB out (larger than L2), the small case
     used for ncu captures of that kernel."""
     import torch
     import paper_1905_00444_gb300 as qfx
