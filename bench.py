@@ -287,6 +287,9 @@ def run_qfx(args):
         "clocks": clk,
         "gpu_launches": int(launches),
     }
+    if not args.no_modes:
+        line["precision_modes"] = {m: run_mode(qfx, torch, circ, w, m, x1_dev, args, dev, stream)
+                                   for m in ("bf16x3", "tf32x3", "bf16x3_fast")}
     if world == 1 and not args.no_cpu:
         rate, reps, dt = cpu_oracle_sample(seconds=args.cpu_seconds)
         line["cpu_baseline"] = {
@@ -301,6 +304,62 @@ def run_qfx(args):
     return 0
 
 
+# Tensor-pipe work per counted complex multiply-add (8 counted flops): 4 real products,
+# each the sum of 6 (BF16x3) or 3 (TF32x3) term products -> 48 or 24 flops of the mode's
+# type.  TF32 runs at half the BF16 rate (nominal ratio), so both modes cost 6x the
+# counted flops in BF16-equivalent tensor work.
+TENSOR_FACTOR = {"bf16x3": 48 / 8, "tf32x3": 24 / 8}
+TENSOR_PEAK_RATIO = {"bf16x3": 1.0, "tf32x3": 0.5}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+def run_mode(qfx, torch, circ, w, mode, x1_dev, args, dev, stream):
+    """The same workload with the contraction steps on tcgen05 in a split precision."""
+    fast = mode.endswith("_fast")
+    mode = mode.replace("_fast", "")
+    plan = qfx.Plan(qfx.Circuit(circ), n_open=w["n_open"], precision=mode, fast_accumulation=fast)
+    plan.upload()
+    ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
+    out = torch.empty((1, 1 << w["n_open"]), dtype=torch.complex128, device=dev)
+    for i in range(args.warmup):
+        qfx.amplitudes(plan, x1_dev[i:i + 1], workspace=ws, out=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    qfx.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.warmup, args.warmup + args.steps):
+        qfx.amplitudes(plan, x1_dev[i:i + 1], workspace=ws, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    qfx.sync()
+    qfx.profile_enable(False)
+    recs = qfx.profile_collect()
+    el = e0.elapsed_time(e1) / 1e3
+    flops = plan.stats["flops_per_item"] * plan.n_slices
+    big = plan.steps[plan.stats["largest_step"]]
+    dom = [r["ms"] for r in recs if r["kind"] == 0 and r["flops"] == big["flops"]]
+    dom_ms = float(np.mean(dom)) if dom else float("nan")
+    counted = big["flops"] / (dom_ms / 1e3) / 1e12
+    peaks, src = measured_peaks()
+    peak = peaks["bf16_tflops_sustained"] * TENSOR_PEAK_RATIO[mode]
+    achieved = counted * TENSOR_FACTOR[mode]
+    return {"value": flops * args.steps / el / 1e12, "unit": "TFLOP/s",
+            "amplitudes_per_s": (1 << w["n_open"]) * args.steps / el,
+            "ms_per_step": 1e3 * el / args.steps,
+            "largest_step_counted_tflops": counted,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": f"tensor-pipe flops = {TENSOR_FACTOR[mode]:g} x counted; peak = "
+                                 f"{src} bf16 sustained x {TENSOR_PEAK_RATIO[mode]}"}}
+
+
 # ----------------------------------------------------------------------------- kernel case
 def run_kstep(args):
     """The dominant contraction step alone (K = N = 256 as in the 7x7x32 interior steps)
@@ -312,18 +371,22 @@ def run_kstep(args):
     S = torch.from_numpy(ri.random_complex((K * N,), seed=1)).cuda()
     B = torch.from_numpy(ri.random_complex((P * K * Sd,), seed=2)).cuda()
     C = torch.empty(P * N * Sd, dtype=torch.complex64, device="cuda")
+    prec = args.precision.replace("_fast", "")
+    var = 12 if args.precision.endswith("_fast") else -1
+    scratch = torch.empty(max(1, qfx.qfx.step_scratch_bytes(K, N, prec)), dtype=torch.uint8,
+                          device="cuda")
     for _ in range(args.warmup):
-        qfx.contract_step(S, B, P, K, N, NL, Sd, out=C)
+        qfx.contract_step(S, B, P, K, N, NL, Sd, out=C, precision=prec, scratch=scratch, variant=var)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        qfx.contract_step(S, B, P, K, N, NL, Sd, out=C)
+        qfx.contract_step(S, B, P, K, N, NL, Sd, out=C, precision=prec, scratch=scratch, variant=var)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     flops = 8.0 * P * K * N * Sd
-    print(json.dumps({"workload": "dominant step (P,K,N,Sd)=(1,256,256,2^18)", "ms": ms,
+    print(json.dumps({"workload": "dominant step (P,K,N,Sd)=(1,256,256,2^18)", "precision": args.precision, "ms": ms,
                       "tflops": flops / ms / 1e9, "steps": args.steps}), flush=True)
     return 0
 
@@ -337,6 +400,9 @@ def main():
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS) + ["kstep"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "bf16x3_fast"],
+                    help="kernel case only; the amplitude run reports every mode")
+    ap.add_argument("--no-modes", action="store_true", help="skip the split-precision runs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

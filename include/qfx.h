@@ -112,8 +112,15 @@ typedef struct {
   int32_t n_forced_cuts;
   int32_t precision;               /* qfx_precision */
   int32_t plan_family;             /* 0 = line sweep (the only family of this build) */
-  int32_t reserved;
+  int32_t tc_flags;                /* tensor-core options, QFX_TC_* bits; 0 = default */
 } qfx_plan_opts;
+
+/* Tensor-core accumulation.  Default: each complex tile is 128 x 128 with four TMEM
+ * accumulators -- the hi x hi term products in "main" ones, all cross-term products in
+ * "small" ones -- so the large accumulators see two additions per k-step (the tensor
+ * core's FP32 accumulation loses a little at each addition).  QFX_TC_FAST_ACCUMULATION:
+ * 128 x 256 tiles with one accumulator pair (fewer shared-memory reads, larger error). */
+#define QFX_TC_FAST_ACCUMULATION 1
 
 /* Sec. III.D (contraction order and cuts), Sec. III.A (slices), Sec. III.B (x2), Eq. 1.
  * Host only: the plan sweeps the grid line by line (along the shorter grid dimension),
@@ -193,15 +200,28 @@ qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x1, int64_t 
                                  int64_t slice_begin, int64_t slice_end, double* out,
                                  void* stream);
 
-/* Waits for `stream` and reports any asynchronous CUDA error as QFX_ECUDA. */
+/* Waits for `stream` and reports any asynchronous CUDA error as QFX_ECUDA, and a
+ * tensor-core kernel that gave up a bounded wait (about 1 s) as QFX_ETIMEOUT. */
 qfx_status qfx_sync(void* stream);
 
 /* One contraction step of the TTGT form (Sec. III.E), for tests and microbenchmarks:
  * C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] * B[p][k][s], complex64, all device pointers,
- * 16-byte aligned, no aliasing.  `variant` < 0 lets the library choose. */
+ * 16-byte aligned, no aliasing.  `variant` < 0 lets the library choose (FP32 only).
+ * Tensor-core precisions run on tcgen05 when N % 16 == 0, N <= 256, K a multiple of the
+ * term's k step (16 for BF16x3, 8 for TF32x3) and P*Sd >= 128, otherwise on the FP32
+ * path; they need `scratch` of qfx_step_scratch_bytes(K, N, precision) bytes, 256-byte
+ * aligned (NULL is fine for FP32).  Variant 12 selects fast accumulation (see
+ * QFX_TC_FAST_ACCUMULATION) for a tensor-core step.  Test hook: variant 99 with a tensor-core step
+ * withholds the stream of S, so every CTA's bounded waits expire (about 1 s each, run
+ * it on at most a few hundred columns); qfx_sync then reports QFX_ETIMEOUT and the
+ * context stays usable.  Errors: QFX_EINVAL, QFX_ENOMEM (scratch), QFX_ECUDA. */
 qfx_status qfx_contract_step(const void* S, const void* B, void* C, int64_t P, int64_t K,
                              int64_t N, int64_t NL, int64_t Sd, int32_t precision,
-                             int32_t variant, void* stream);
+                             int32_t variant, void* scratch, size_t scratch_bytes,
+                             void* stream);
+
+/* Scratch bytes a tensor-core step with these K and N needs (0 for FP32). */
+uint64_t qfx_step_scratch_bytes(int64_t K, int64_t N, int32_t precision);
 
 /* Tensor transpose (Sec. III.E): out = in with axes reordered; complex64, rank <= 10.
  * shape[] is the input shape (C order); out axis a is input axis perm[a].

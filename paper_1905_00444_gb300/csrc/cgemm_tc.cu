@@ -1,0 +1,575 @@
+// One contraction step on the 5th-generation tensor cores (tcgen05, TMEM accumulators),
+// with complex FP32 operands split into lower-precision terms.
+//
+//   C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] * B[p][k][s]     (Sec. III.E, Eq. 1)
+//
+// The paper ran this product as complex FP32 CGEMM without tensor cores, because FP16
+// inputs lose too much precision (Sec. III.E).  Here each FP32 real operand x is split
+// into terms of a tensor-core type and the complex product is formed from real products
+// (4M: Re = Ar Sr - Ai Si, Im = Ar Si + Ai Sr), each real product being the sum of the
+// cross products of the terms whose magnitude is above FP32 rounding:
+//   BF16x3: x = h + m + l (successive round-to-nearest residuals), products
+//           hh, hm, mh, hl, lh, mm  (error ~2^-24 relative);
+//   TF32x3: x = b + s, products bb, bs, sb  (error ~2^-21 relative).
+// Accumulation is FP32 in TMEM.
+//
+// Tile: one CTA owns 128 columns j of the step (M = 128, the boundary tensor B is the A
+// operand, rows j) and all N <= 256 rows n (the site matrix S is the B operand), with
+// the real and imaginary accumulators in TMEM columns [0, N) and [256, 256 + N).
+// Roles (192 threads):
+//   warps 0-3  load B (FP32) straight from global, split it into term planes in shared
+//              memory (K-major, no-swizzle core-matrix layout), later run the epilogue;
+//   warp 4     allocates TMEM; lane 0 issues the tcgen05.mma instructions;
+//   warp 5     lane 0 streams the pre-split image of S (written once per step by
+//              split_site_kernel in the same layout) with one bulk copy per stage.
+// A 3-stage ring of shared-memory stages is guarded by mbarriers.  Every wait has a
+// deadline; on expiry the kernel records an error, drains its own copies and MMAs,
+// frees TMEM and returns (the host reports QFX_ETIMEOUT).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "qfx_internal.h"
+
+namespace qfx {
+
+__device__ unsigned int g_tc_status = 0;
+
+namespace {
+
+constexpr int kRows = 128;        // UMMA M
+constexpr int kPlaneA = kRows * 32;   // bytes of one A term plane per stage
+constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait
+
+template <int MODE>
+struct Mode;
+template <>
+struct Mode<QFX_PREC_C3M_BF16X3> {
+  static constexpr int TERMS = 3, KS = 16, NPROD = 6;
+  static constexpr uint32_t FMT = 1;   // BF16
+  __device__ static constexpr int ta(int i) { return i == 0 ? 1 : i == 1 ? 0 : i == 2 ? 2 : i == 3 ? 0 : i == 4 ? 1 : 0; }
+  __device__ static constexpr int tb(int i) { return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 0 : i == 3 ? 1 : i == 4 ? 0 : 0; }
+};
+template <>
+struct Mode<QFX_PREC_C3M_TF32X3> {
+  static constexpr int TERMS = 2, KS = 8, NPROD = 3;
+  static constexpr uint32_t FMT = 2;   // TF32
+  __device__ static constexpr int ta(int i) { return i == 0 ? 0 : i == 1 ? 1 : 0; }
+  __device__ static constexpr int tb(int i) { return i == 0 ? 1 : i == 1 ? 0 : 0; }
+};
+
+// ---- term splitting ------------------------------------------------------------
+__device__ __forceinline__ void split_bf16x3(float x, uint16_t t[3]) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(m);
+  const __nv_bfloat16 l = __float2bfloat16_rn(r2);
+  t[0] = __bfloat16_as_ushort(h);
+  t[1] = __bfloat16_as_ushort(m);
+  t[2] = __bfloat16_as_ushort(l);
+}
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32x2(float x, uint32_t t[2]) {
+  t[0] = to_tf32(x);
+  t[1] = to_tf32(x - __uint_as_float(t[0]));
+}
+
+// Writes the KS values of one row (component c of `v`) as TERMS planes of 32 bytes each.
+// Row r of a plane lives at (r/8)*256 + kc*128 + (r%8)*16 (8x16-byte core matrices;
+// kc = which 16-byte half of the row).
+template <int MODE>
+__device__ __forceinline__ void store_row_terms(char* plane0, int plane_bytes, int row,
+                                                const float* x) {
+  using M_ = Mode<MODE>;
+  const int base = (row >> 3) * 256 + (row & 7) * 16;
+  if constexpr (MODE == QFX_PREC_C3M_BF16X3) {
+    uint32_t w[3][8];
+#pragma unroll
+    for (int k = 0; k < 16; k += 2) {
+      uint16_t a[3], b[3];
+      split_bf16x3(x[k], a);
+      split_bf16x3(x[k + 1], b);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) w[t][k / 2] = (uint32_t)a[t] | ((uint32_t)b[t] << 16);
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      char* pl = plane0 + t * plane_bytes + base;
+      *reinterpret_cast<uint4*>(pl) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      *reinterpret_cast<uint4*>(pl + 128) = make_uint4(w[t][4], w[t][5], w[t][6], w[t][7]);
+    }
+  } else {
+    uint32_t w[2][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      uint32_t a[2];
+      split_tf32x2(x[k], a);
+      w[0][k] = a[0];
+      w[1][k] = a[1];
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      char* pl = plane0 + t * plane_bytes + base;
+      *reinterpret_cast<uint4*>(pl) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      *reinterpret_cast<uint4*>(pl + 128) = make_uint4(w[t][4], w[t][5], w[t][6], w[t][7]);
+    }
+  }
+  (void)sizeof(M_);
+}
+
+// ---- PTX helpers -----------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(bar),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait: false if the deadline passed or another role gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  const unsigned long long deadline = globaltimer() + kWaitNs;
+  while (!mbar_try(bar, parity)) {
+    if (*abort) return false;
+    if (globaltimer() > deadline) {
+      *abort = 1;
+      atomicOr(&g_tc_status, 1u);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  // K-major, no swizzle: LBO = 128 B (next core matrix along K), SBO = 256 B (next
+  // 8-row group); bits 46-48 = 0b001; base offset 0; layout type 0.
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(256 >> 4) << 32) | (1ull << 46);
+}
+template <int MODE>
+__device__ __forceinline__ uint32_t instr_desc(int n, bool neg_a) {
+  // D = F32 (bits 4-5 = 1), A/B format (bits 7-9, 10-12), negate A (bit 13),
+  // both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+  return (1u << 4) | (Mode<MODE>::FMT << 7) | (Mode<MODE>::FMT << 10) | ((neg_a ? 1u : 0u) << 13) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (MODE == QFX_PREC_C3M_BF16X3) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+  const float2* B; int64_t b_stride;
+  float2* C; int64_t c_stride;
+  const char* simage; int64_t img_stride;   // pre-split S, per item
+  int64_t P, K, N, NL, Sd, J;
+  int Nt;            // columns n per tile (<= 128 split accumulators, <= 256 single)
+  int NHt;           // tiles along n per 128-row tile
+  int64_t JT;        // 128-row tiles per item
+  int64_t tiles;     // total tiles (items x JT x NHt)
+  int withhold_s;    // test hook: never stream S, so the bounded waits expire
+};
+
+// Persistent CTA, one per SM.  TMEM columns: with SPLITACC the hh-term products go to
+// "main" accumulators (re [0,128), im [128,256)) and every cross-term product to "small"
+// ones (re [256,384), im [384,512)), so the large accumulator sees 2 additions per
+// k-stage instead of 2 x NPROD; without SPLITACC re = [0, Nt), im = [256, 256 + Nt).
+// Warps: 0-3 producers, 4-11 epilogue (two per TMEM lane quarter, each half the columns),
+// 12 TMEM owner + MMA issuer, 13 S stream.
+template <int MODE, bool SPLITACC>
+struct TcCfg {
+  using M_ = Mode<MODE>;
+  static constexpr int NT_MAX = SPLITACC ? 128 : 256;
+  static constexpr int STAGES = SPLITACC ? 4 : 3;
+  static constexpr int PLANES = 2 * M_::TERMS;
+  static constexpr int STAGE_A = PLANES * kPlaneA;
+  static constexpr int THREADS = 14 * 32;
+  static size_t smem(int nt) {
+    return (size_t)STAGES * (STAGE_A + PLANES * nt * 32) + (3 * STAGES + 3) * sizeof(uint64_t);
+  }
+};
+
+template <int MODE, bool SPLITACC>
+__global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_kernel(const TcArgs a) {
+  using M_ = Mode<MODE>;
+  using CF = TcCfg<MODE, SPLITACC>;
+  constexpr int TERMS = M_::TERMS, KS = M_::KS, STAGES = CF::STAGES;
+  extern __shared__ __align__(16) char smem[];
+  const int stageA = CF::STAGE_A;
+  const int planeS = a.Nt * 32;
+  const int stageS = CF::PLANES * planeS;
+  char* sA = smem;
+  char* sS = smem + STAGES * stageA;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sS + STAGES * stageS);
+  // bars: fullA[S], fullS[S], empty[S], acc_full, tmem_free, done
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t KT = a.K / KS;
+
+  auto fullA = [&](int s) { return smem_u32(&bars[s]); };
+  auto fullS = [&](int s) { return smem_u32(&bars[STAGES + s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[2 * STAGES + s]); };
+  const uint32_t acc_full = smem_u32(&bars[3 * STAGES]);
+  const uint32_t tmem_free = smem_u32(&bars[3 * STAGES + 1]);
+  const uint32_t done = smem_u32(&bars[3 * STAGES + 2]);
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(fullA(s), kRows);
+      mbar_init(fullS(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(tmem_free, 8);
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 12) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_slot;
+  volatile int* abort = &abort_flag;
+  const int64_t per_item = a.JT * a.NHt;
+
+  if (warp < 4) {
+    // ---- producers: split 128 rows of B per k-stage into term planes -------------------
+    int64_t q = 0;
+    for (int64_t t = blockIdx.x; t < a.tiles && !*abort; t += gridDim.x) {
+      const int64_t g = t / per_item, jt = (t % per_item) / a.NHt;
+      const int64_t jg = jt * kRows + tid;
+      const bool valid = jg < a.J;
+      const float2* Bg = a.B + g * a.b_stride;
+      const int64_t pofs = valid ? (jg / a.Sd) * a.K * a.Sd + (jg % a.Sd) : 0;
+      bool ok = true;
+      for (int64_t it = 0; it < KT; ++it, ++q) {
+        const int s = (int)(q % STAGES);
+        if (q >= STAGES && !mbar_wait(empty(s), (uint32_t)((q / STAGES - 1) & 1), abort)) { ok = false; break; }
+        float re[KS], im[KS];
+#pragma unroll
+        for (int kk = 0; kk < KS; ++kk) {
+          float2 v = make_float2(0.f, 0.f);
+          if (valid) v = __ldg(Bg + pofs + (it * KS + kk) * a.Sd);
+          re[kk] = v.x;
+          im[kk] = v.y;
+        }
+        char* st = sA + s * stageA;
+        store_row_terms<MODE>(st, kPlaneA, tid, re);
+        store_row_terms<MODE>(st + TERMS * kPlaneA, kPlaneA, tid, im);
+        fence_async_smem();
+        mbar_arrive(fullA(s));
+      }
+      if (!ok) break;
+    }
+  } else if (warp == 13) {
+    // ---- S image stream ------------------------------------------------------------
+    if (lane == 0) {
+      int64_t q = 0, issued = 0;
+      bool ok = !a.withhold_s;
+      for (int64_t t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
+        const int64_t g = t / per_item, nh = t % a.NHt;
+        const char* img = a.simage + g * a.img_stride;
+        for (int64_t it = 0; it < KT; ++it, ++q) {
+          const int s = (int)(q % STAGES);
+          if (q >= STAGES && !mbar_wait(empty(s), (uint32_t)((q / STAGES - 1) & 1), abort)) { ok = false; break; }
+          mbar_arrive_tx(fullS(s), (uint32_t)stageS);
+          bulk_copy(smem_u32(sS + s * stageS), img + (it * a.NHt + nh) * stageS, (uint32_t)stageS, fullS(s));
+          issued = q + 1;
+        }
+      }
+      // drain: every issued copy must land before the CTA exits
+      for (int64_t i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i) {
+        const int s = (int)(i % STAGES);
+        const unsigned long long deadline = globaltimer() + kWaitNs;
+        while (!mbar_try(fullS(s), (uint32_t)((i / STAGES) & 1)) && globaltimer() < deadline) {
+        }
+      }
+    }
+  } else if (warp == 12) {
+    // ---- MMA issue -----------------------------------------------------------------
+    if (lane == 0) {
+      int64_t q = 0, tc = 0;
+      bool ok = true;
+      const uint32_t idesc_p = instr_desc<MODE>(a.Nt, false), idesc_n = instr_desc<MODE>(a.Nt, true);
+      for (int64_t t = blockIdx.x; t < a.tiles && ok; t += gridDim.x, ++tc) {
+        if (tc > 0 && !mbar_wait(tmem_free, (uint32_t)((tc - 1) & 1), abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool started[4] = {false, false, false, false};
+        for (int64_t it = 0; it < KT; ++it, ++q) {
+          const int s = (int)(q % STAGES);
+          const uint32_t par = (uint32_t)((q / STAGES) & 1);
+          if (!mbar_wait(fullA(s), par, abort) || !mbar_wait(fullS(s), par, abort)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * stageA), b0 = smem_u32(sS + s * stageS);
+#pragma unroll
+          for (int rp = 0; rp < 4; ++rp) {
+            const int ca = (rp == 0 || rp == 2) ? 0 : 1;          // Ar, Ai, Ar, Ai
+            const int cb = (rp == 0 || rp == 3) ? 0 : 1;          // Sr, Si, Si, Sr
+            const int to_im = rp >= 2 ? 1 : 0;
+            const uint32_t idesc = rp == 1 ? idesc_n : idesc_p;   // - Ai Si
+#pragma unroll
+            for (int pi = 0; pi < M_::NPROD; ++pi) {
+              const bool main_term = M_::ta(pi) == 0 && M_::tb(pi) == 0;
+              const int acc = (SPLITACC && !main_term) ? 2 + to_im : to_im;
+              const uint32_t d = SPLITACC ? tmem + (uint32_t)(acc * 128) : tmem + (uint32_t)(to_im * 256);
+              const uint64_t ad = smem_desc(a0 + (ca * TERMS + M_::ta(pi)) * kPlaneA);
+              const uint64_t bd = smem_desc(b0 + (cb * TERMS + M_::tb(pi)) * planeS);
+              mma<MODE>(d, ad, bd, idesc, started[acc] ? 1u : 0u);
+              started[acc] = true;
+            }
+          }
+          mma_commit(empty(s));
+        }
+        if (ok) mma_commit(acc_full);
+      }
+      mma_commit(done);
+    }
+  } else {
+    // ---- epilogue (warps 4-11): TMEM -> C ----------------------------------------------
+    const int quarter = warp & 3, half = (warp - 4) >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    // 16-column chunks alternate between the two warps of a lane quarter
+    const int nchunks = a.Nt / 16;
+    const int my_last = ((nchunks - 1 - half) >= 0) ? (nchunks - 1 - ((nchunks - 1 - half) & 1)) : -1;
+    int64_t tc = 0;
+    for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x, ++tc) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)(tc & 1), abort) && !*abort);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t g = t / per_item, jt = (t % per_item) / a.NHt, nh = t % a.NHt;
+      const int64_t jg = jt * kRows + row;
+      const bool valid = jg < a.J;
+      float2* Cg = a.C + g * a.c_stride;
+      const int64_t p = valid ? jg / a.Sd : 0, sidx = valid ? jg % a.Sd : 0;
+      const int64_t jofs = p * a.NL * a.Sd + sidx;
+      const int64_t strideNH = a.P * a.NL * a.Sd;
+      if (my_last < 0) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tmem_free);
+      }
+      for (int ci = half; ci < nchunks; ci += 2) {
+        const int c0 = ci * 16;
+        float vr[16], vi[16];
+        if (SPLITACC) {
+          float sr[16], si[16];
+          tmem_ld16(tmem + lane_base + c0, vr);
+          tmem_ld16(tmem + lane_base + 128 + c0, vi);
+          tmem_ld16(tmem + lane_base + 256 + c0, sr);
+          tmem_ld16(tmem + lane_base + 384 + c0, si);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int i = 0; i < 16; ++i) { vr[i] += sr[i]; vi[i] += si[i]; }
+        } else {
+          tmem_ld16(tmem + lane_base + c0, vr);
+          tmem_ld16(tmem + lane_base + 256 + c0, vi);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+        if (ci == my_last) {
+          // last TMEM read of this tile by this warp: hand the columns back to the MMA
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tmem_free);
+        }
+        if (valid) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int64_t n = nh * a.Nt + c0 + i;
+            const int64_t nhh = n / a.NL, nl = n % a.NL;
+            Cg[nhh * strideNH + nl * a.Sd + jofs] = make_float2(vr[i], vi[i]);
+          }
+        }
+      }
+    }
+  }
+
+  if (warp == 12) mbar_wait(done, 0, abort);   // last MMAs finished before freeing TMEM
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 12) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// Pre-split of the site matrix S[k][n] into the per-stage shared-memory image:
+// [stage ks][n tile][component][term][row n within the tile][32 bytes].
+template <int MODE>
+__global__ void __launch_bounds__(128) split_site_kernel(const float2* __restrict__ S, int64_t s_stride,
+                                                          int K, int N, int Nt, char* image,
+                                                          int64_t img_stride) {
+  using M_ = Mode<MODE>;
+  constexpr int TERMS = M_::TERMS, KS = M_::KS;
+  const int n = blockIdx.x * 128 + threadIdx.x;
+  const int ks = blockIdx.y;
+  const int g = blockIdx.z;
+  if (n >= N) return;
+  const float2* Sg = S + (int64_t)g * s_stride;
+  float re[KS], im[KS];
+#pragma unroll
+  for (int kk = 0; kk < KS; ++kk) {
+    const int k = ks * KS + kk;
+    float2 v = make_float2(0.f, 0.f);
+    if (k < K) v = Sg[(int64_t)k * N + n];
+    re[kk] = v.x;
+    im[kk] = v.y;
+  }
+  const int planeS = Nt * 32;
+  const int nht = N / Nt, nh = n / Nt, r = n % Nt;
+  char* st = image + (int64_t)g * img_stride + ((int64_t)ks * nht + nh) * 2 * TERMS * planeS;
+  store_row_terms<MODE>(st, planeS, r, re);
+  store_row_terms<MODE>(st + TERMS * planeS, planeS, r, im);
+}
+
+int num_sms() {
+  static int n[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64) dev = 63;
+  if (!n[dev]) cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev);
+  return n[dev] > 0 ? n[dev] : 1;
+}
+
+template <int MODE, bool SPLITACC>
+int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
+                   int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
+                   int batch, char* scratch, int64_t scratch_stride, int withhold,
+                   cudaStream_t st) {
+  using M_ = Mode<MODE>;
+  using CF = TcCfg<MODE, SPLITACC>;
+  const int Nt = (int)(N < CF::NT_MAX ? N : CF::NT_MAX);   // N % 16 == 0, N <= 256
+  const int KT = (int)(K / M_::KS);
+  dim3 sg((unsigned)((N + 127) / 128), KT, batch);
+  split_site_kernel<MODE><<<sg, 128, 0, st>>>((const float2*)S, s_stride, (int)K, (int)N, Nt,
+                                              scratch, scratch_stride);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return (int)e;
+  TcArgs a{};
+  a.B = (const float2*)B; a.b_stride = b_stride;
+  a.C = (float2*)C; a.c_stride = c_stride;
+  a.simage = scratch; a.img_stride = scratch_stride;
+  a.P = P; a.K = K; a.N = N; a.NL = NL; a.Sd = Sd; a.J = P * Sd;
+  a.Nt = Nt;
+  a.NHt = (int)(N / Nt);
+  a.JT = (a.J + kRows - 1) / kRows;
+  a.tiles = (int64_t)batch * a.JT * a.NHt;
+  a.withhold_s = withhold;
+  auto kern = cgemm_tc_kernel<MODE, SPLITACC>;
+  static int attr_done[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_done[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::smem(CF::NT_MAX));
+    if (e != cudaSuccess) return (int)e;
+    attr_done[dev] = 1;
+  }
+  const int64_t grid = a.tiles < num_sms() ? a.tiles : num_sms();
+  kern<<<(unsigned)grid, CF::THREADS, CF::smem(Nt), st>>>(a);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags) {
+  // default tiles are 128 columns wide (N <= 128 or exactly two tiles); fast ones up to 256
+  const bool n_ok = N % 16 == 0 && ((flags & kTcFast) ? N <= 256 : (N <= 128 || N == 256));
+  if (precision == QFX_PREC_C3M_BF16X3) return n_ok && K % 16 == 0 && J >= kRows;
+  if (precision == QFX_PREC_C3M_TF32X3) return n_ok && K % 8 == 0 && J >= kRows;
+  return false;
+}
+
+uint64_t tc_scratch_bytes(int precision, int64_t K, int64_t N) {
+  if (precision == QFX_PREC_C3M_BF16X3) return (uint64_t)(K / 16) * 6 * (uint64_t)N * 32;
+  if (precision == QFX_PREC_C3M_TF32X3) return (uint64_t)(K / 8) * 4 * (uint64_t)N * 32;
+  return 0;
+}
+
+int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
+                   int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
+                   int batch, int precision, char* scratch, int64_t scratch_stride, void* stream,
+                   int flags) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fast = (flags & kTcFast) != 0;
+  const int withhold = (flags & kTcWithhold) ? 1 : 0;
+  if (precision == QFX_PREC_C3M_BF16X3)
+    return fast ? launch_tc_mode<QFX_PREC_C3M_BF16X3, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
+                                                             Sd, batch, scratch, scratch_stride, withhold, st)
+                : launch_tc_mode<QFX_PREC_C3M_BF16X3, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
+                                                            Sd, batch, scratch, scratch_stride, withhold, st);
+  if (precision == QFX_PREC_C3M_TF32X3)
+    return fast ? launch_tc_mode<QFX_PREC_C3M_TF32X3, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
+                                                             Sd, batch, scratch, scratch_stride, withhold, st)
+                : launch_tc_mode<QFX_PREC_C3M_TF32X3, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
+                                                            Sd, batch, scratch, scratch_stride, withhold, st);
+  return (int)cudaErrorInvalidValue;
+}
+
+int tc_take_status() {
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(v)) != cudaSuccess) return -1;
+  if (v) {
+    const unsigned int z = 0;
+    cudaMemcpyToSymbol(g_tc_status, &z, sizeof(z));
+  }
+  return (int)v;
+}
+
+}  // namespace qfx

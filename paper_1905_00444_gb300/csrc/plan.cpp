@@ -137,6 +137,8 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     std::unique_ptr<qfx_plan> guard(p);
     p->rows = c->rows; p->cols = c->cols; p->n = n;
     p->precision = o->precision;
+    if (o->tc_flags & ~QFX_TC_FAST_ACCUMULATION) return qfx::fail(QFX_EINVAL, "unknown tc_flags bits");
+    p->tc_flags = o->tc_flags;
     p->transposed = geo.transposed;
     for (int line = 0; line < geo.W; ++line)
       for (int pos = 0; pos < geo.L; ++pos) p->order.push_back(geo.qubit(line, pos));
@@ -269,7 +271,14 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
 
     // steps
     p->steps = sim.steps;
-    for (auto& st : p->steps) st.variant = qfx::pick_variant(st.N, st.Sd);
+    uint64_t simage = 0;
+    for (auto& st : p->steps) {
+      st.variant = qfx::pick_variant(st.N, st.Sd);
+      if (&st != &p->steps[0] && qfx::tc_eligible(p->precision, st.K, st.N, st.P * st.Sd, p->tc_flags)) {
+        st.variant = p->precision == QFX_PREC_C3M_BF16X3 ? qfx::kVariantTcBf16 : qfx::kVariantTcTf32;
+        simage = std::max(simage, qfx::tc_scratch_bytes(p->precision, st.K, st.N));
+      }
+    }
     p->max_elements = 1;
     p->flops_per_item = sim.flops;
     p->bytes_per_item = sim.bytes;
@@ -340,7 +349,8 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     L.buf0 = 0;
     L.buf1 = align256((uint64_t)p->max_elements * 8);
     L.sites = L.buf1 + align256((uint64_t)p->max_elements * 8);
-    L.item_bytes = L.sites + align256((uint64_t)p->site_total * 8);
+    L.simage = L.sites + align256((uint64_t)p->site_total * 8);
+    L.item_bytes = L.simage + align256(simage);
     p->dev.resize(0);
     *out = guard.release();
     return QFX_OK;

@@ -86,6 +86,7 @@ struct Layout {
   uint64_t header_per_item;   // bytes
   uint64_t item_bytes;        // bytes, multiple of 256
   uint64_t buf0, buf1, sites; // byte offsets inside one item block
+  uint64_t simage;            // pre-split site image for tensor-core steps (0 bytes if none)
 };
 
 struct DeviceTables {
@@ -102,6 +103,7 @@ struct DeviceTables {
 struct qfx_plan {
   int rows = 0, cols = 0, n = 0;
   int precision = 0;
+  int tc_flags = 0;
   bool transposed = false;        // lines are grid rows instead of columns
   std::vector<int> order;         // qubits in sweep order
   std::vector<int> open_sites;    // user order (output bit i)
@@ -147,6 +149,18 @@ int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride
                 int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
                 int batch, int variant, int precision, void* stream);
 int pick_variant(int64_t N, int64_t Sd);
+// tensor-core steps (variants 10 = BF16x3, 11 = TF32x3)
+constexpr int kVariantTcBf16 = 10, kVariantTcTf32 = 11;
+constexpr int kTcFast = 1;       // QFX_TC_FAST_ACCUMULATION
+constexpr int kTcWithhold = 2;   // test hook: S stream withheld
+bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags);
+uint64_t tc_scratch_bytes(int precision, int64_t K, int64_t N);
+int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
+                   int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
+                   int batch, int precision, char* scratch, int64_t scratch_stride, void* stream,
+                   int flags = 0);
+
+int tc_take_status();   // reads and clears the tensor-core kernels' timeout flag
 int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
                    const int32_t* perm, void* stream);
 

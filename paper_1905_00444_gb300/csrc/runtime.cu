@@ -155,8 +155,6 @@ qfx_status check_amplitudes_args(const qfx_plan* p, const uint64_t* x1, int64_t 
   if (slice_begin < 0 || slice_end > p->n_slices || slice_begin >= slice_end)
     return fail(QFX_EINVAL, "qfx_amplitudes: slice range outside [0, n_slices)");
   if (((uintptr_t)out & 15) != 0) return fail(QFX_EINVAL, "qfx_amplitudes: out not 16-byte aligned");
-  if (p->precision != QFX_PREC_FP32_SIMT)
-    return fail(QFX_EUNSUPPORTED, "qfx_amplitudes: this plan's precision has no kernel here");
   return QFX_OK;
 }
 
@@ -205,8 +203,13 @@ qfx_status exec_amplitudes(const qfx_plan* p, const DeviceTables& t, const uint6
       const char* B = items + (i == 1 ? site0 : ((i - 1) % 2 ? L.buf1 : L.buf0));
       char* C = items + (i % 2 ? L.buf1 : L.buf0);
       profile_begin(st, &slot);
-      err = launch_step(S, (int64_t)(ib / 8), B, (int64_t)(ib / 8), C, (int64_t)(ib / 8), sp.P,
-                        sp.K, sp.N, sp.NL, sp.Sd, g, sp.variant, p->precision, st);
+      if (sp.variant >= kVariantTcBf16)
+        err = launch_step_tc(S, (int64_t)(ib / 8), B, (int64_t)(ib / 8), C, (int64_t)(ib / 8), sp.P,
+                             sp.K, sp.N, sp.NL, sp.Sd, g, p->precision, items + L.simage,
+                             (int64_t)ib, st, p->tc_flags);
+      else
+        err = launch_step(S, (int64_t)(ib / 8), B, (int64_t)(ib / 8), C, (int64_t)(ib / 8), sp.P,
+                          sp.K, sp.N, sp.NL, sp.Sd, g, sp.variant, p->precision, st);
       profile_end(st, slot, i, sp.variant, 0, sp.flops * g, sp.bytes * g);
       if (err) return cuda_fail(err, "contraction step kernel");
     }
@@ -247,26 +250,50 @@ extern "C" qfx_status qfx_sync(void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "qfx_sync");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "qfx_sync");
+  const int tc = tc_take_status();
+  if (tc < 0) return fail(QFX_ECUDA, "qfx_sync: reading the tensor-core status word failed");
+  if (tc > 0) return fail(QFX_ETIMEOUT, "qfx_sync: a tensor-core contraction step gave up waiting (bounded wait expired)");
   return QFX_OK;
+}
+
+extern "C" uint64_t qfx_step_scratch_bytes(int64_t K, int64_t N, int32_t precision) {
+  return tc_scratch_bytes(precision, K, N);
 }
 
 extern "C" qfx_status qfx_contract_step(const void* S, const void* B, void* C, int64_t P,
                                         int64_t K, int64_t N, int64_t NL, int64_t Sd,
-                                        int32_t precision, int32_t variant, void* stream) {
+                                        int32_t precision, int32_t variant, void* scratch,
+                                        size_t scratch_bytes, void* stream) {
   if (!S || !B || !C) return fail(QFX_EINVAL, "qfx_contract_step: NULL pointer");
   if (P < 1 || K < 1 || N < 1 || NL < 1 || Sd < 1 || N % NL)
     return fail(QFX_EINVAL, "qfx_contract_step: need positive sizes and NL | N");
   if ((((uintptr_t)S) | ((uintptr_t)B) | ((uintptr_t)C)) & 15)
     return fail(QFX_EINVAL, "qfx_contract_step: pointers must be 16-byte aligned");
-  if (precision != QFX_PREC_FP32_SIMT)
-    return fail(QFX_EUNSUPPORTED, "qfx_contract_step: precision has no kernel here");
+  if (precision < QFX_PREC_FP32_SIMT || precision > QFX_PREC_C3M_TF32X3)
+    return fail(QFX_EINVAL, "qfx_contract_step: unknown precision");
+  const bool tc = precision != QFX_PREC_FP32_SIMT &&
+                  tc_eligible(precision, K, N, P * Sd, variant == 12 ? kTcFast : 0);
+  if (tc) {
+    if (!scratch || scratch_bytes < tc_scratch_bytes(precision, K, N) || ((uintptr_t)scratch & 255))
+      return fail(QFX_ENOMEM, "qfx_contract_step: tensor-core steps need qfx_step_scratch_bytes() of 256-byte aligned scratch");
+  }
+  int flags = 0;
+  if (variant == 99 && tc) { flags = kTcWithhold; variant = -1; }
+  if (variant == 12 && tc) { flags = kTcFast; variant = -1; }
   if (variant >= 10) return fail(QFX_EINVAL, "qfx_contract_step: unknown variant");
   if (variant >= 0 && variant < 5 && Sd % 2)
     return fail(QFX_EINVAL, "qfx_contract_step: variants 0-4 need an even Sd");
   int slot;
   profile_begin(stream, &slot);
   int v = variant < 0 ? pick_variant(N, Sd) : variant;
-  int err = launch_step(S, 0, B, 0, C, 0, P, K, N, NL, Sd, 1, v, precision, stream);
+  int err;
+  if (tc) {
+    v = precision == QFX_PREC_C3M_BF16X3 ? kVariantTcBf16 : kVariantTcTf32;
+    err = launch_step_tc(S, 0, B, 0, C, 0, P, K, N, NL, Sd, 1, precision, (char*)scratch, 0, stream,
+                         flags);
+  } else {
+    err = launch_step(S, 0, B, 0, C, 0, P, K, N, NL, Sd, 1, v, precision, stream);
+  }
   profile_end(stream, slot, -1, v, 0, 8.0 * P * K * N * Sd,
               8.0 * ((double)P * K * Sd + (double)K * N + (double)P * N * Sd));
   if (err) return cuda_fail(err, "qfx_contract_step");

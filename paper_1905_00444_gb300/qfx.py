@@ -39,7 +39,7 @@ class PlanOpts(C.Structure):
     _fields_ = [("max_intermediate_bytes", C.c_uint64), ("open_sites", C.POINTER(C.c_int32)),
                 ("n_open", C.c_int32), ("forced_cuts", C.POINTER(Cut)),
                 ("n_forced_cuts", C.c_int32), ("precision", C.c_int32),
-                ("plan_family", C.c_int32), ("reserved", C.c_int32)]
+                ("plan_family", C.c_int32), ("tc_flags", C.c_int32)]
 
 
 class PlanStats(C.Structure):
@@ -78,7 +78,8 @@ def _declare(lib):
         "qfx_amplitudes": (st, [vp, vp, i64, i64, i64, vp, C.c_size_t, vp, vp]),
         "qfx_amplitudes_static": (st, [vp, vp, i64, i64, i64, vp, vp]),
         "qfx_sync": (st, [vp]),
-        "qfx_contract_step": (st, [vp, vp, vp, i64, i64, i64, i64, i64, i32, i32, vp]),
+        "qfx_contract_step": (st, [vp, vp, vp, i64, i64, i64, i64, i64, i32, i32, vp, C.c_size_t, vp]),
+        "qfx_step_scratch_bytes": (u64, [i64, i64, i32]),
         "qfx_permute": (st, [vp, vp, i32, C.POINTER(i64), C.POINTER(i32), vp]),
         "qfx_profile_enable": (st, [i32]),
         "qfx_profile_collect": (st, [C.POINTER(KernelTime), i32, C.POINTER(i32)]),
@@ -162,7 +163,7 @@ class Plan:
 
     def __init__(self, circuit: Circuit, *, open_sites: Optional[Sequence[int]] = None,
                  n_open: int = 0, max_intermediate_bytes: int = 0,
-                 cuts: Iterable = (), precision: str = "fp32"):
+                 cuts: Iterable = (), precision: str = "fp32", fast_accumulation: bool = False):
         opts = PlanOpts()
         opts.max_intermediate_bytes = int(max_intermediate_bytes)
         self._open_arr = None
@@ -177,6 +178,7 @@ class Plan:
         opts.forced_cuts = C.cast(self._cut_arr, C.POINTER(Cut))
         opts.n_forced_cuts = len(cuts)
         opts.precision = PRECISIONS[precision]
+        opts.tc_flags = 1 if fast_accumulation else 0
         h = C.c_void_p()
         _check(lib.qfx_plan_create(circuit._h, C.byref(opts), C.byref(h)))
         self._h = h
@@ -263,14 +265,22 @@ def sync(stream=None):
     _check(lib.qfx_sync(_stream_ptr(stream)))
 
 
+def step_scratch_bytes(K: int, N: int, precision: str = "fp32") -> int:
+    return int(lib.qfx_step_scratch_bytes(K, N, PRECISIONS[precision]))
+
+
 def contract_step(S, B, P, K, N, NL, Sd, *, out=None, variant: int = -1, precision="fp32",
-                  stream=None):
+                  scratch=None, stream=None):
     """C[nh][p][nl][s] = sum_k S[k][nh*NL+nl] B[p][k][s] on complex64 CUDA tensors."""
     import torch
     if out is None:
         out = torch.empty(P * N * Sd, dtype=torch.complex64, device=S.device)
+    need = step_scratch_bytes(K, N, precision)
+    if scratch is None and need:
+        scratch = torch.empty(need, dtype=torch.uint8, device=S.device)
+    sp, sb = (scratch.data_ptr(), scratch.numel()) if scratch is not None else (None, 0)
     _check(lib.qfx_contract_step(S.data_ptr(), B.data_ptr(), out.data_ptr(), P, K, N, NL, Sd,
-                                 PRECISIONS[precision], variant, _stream_ptr(stream)))
+                                 PRECISIONS[precision], variant, sp, sb, _stream_ptr(stream)))
     return out
 
 

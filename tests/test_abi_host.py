@@ -155,5 +155,25 @@ def test_permute_and_step_argument_checks():
     sh = (C.c_int64 * 3)(2, 3, 4)
     bad = (C.c_int32 * 3)(0, 0, 1)
     assert q.lib.qfx_permute(fake, fake, 3, sh, bad, None) == q.QFX_EINVAL
-    assert q.lib.qfx_contract_step(fake, fake, fake, 1, 1, 3, 2, 1, 0, -1, None) == q.QFX_EINVAL
-    assert q.lib.qfx_contract_step(fake, fake, fake, 1, 1, 2, 2, 3, 0, 0, None) == q.QFX_EINVAL
+    assert q.lib.qfx_contract_step(fake, fake, fake, 1, 1, 3, 2, 1, 0, -1, None, 0, None) == q.QFX_EINVAL
+    assert q.lib.qfx_contract_step(fake, fake, fake, 1, 1, 2, 2, 3, 0, 0, None, 0, None) == q.QFX_EINVAL
+    # tensor-core precision without scratch
+    assert q.lib.qfx_contract_step(fake, fake, fake, 1, 256, 256, 256, 256, 1, -1, None, 0,
+                                   None) == q.QFX_ENOMEM
+    assert q.lib.qfx_step_scratch_bytes(256, 256, 1) == 16 * 6 * 256 * 32
+    assert q.lib.qfx_step_scratch_bytes(256, 256, 2) == 32 * 4 * 256 * 32
+    assert q.lib.qfx_step_scratch_bytes(256, 256, 0) == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_tensor_core_plan_variants(prec):
+    c = ri.rqc(7, 7, 32, seed=0)
+    p = qfx.Plan(qfx.Circuit(c), n_open=6, precision=prec)
+    tc = [s for s in p.steps if s["variant"] >= 10]
+    big = [s for s in p.steps if s["flops"] == 8 * 16 ** 10]
+    assert all(s["variant"] == (10 if prec == "bf16x3" else 11) for s in big)
+    share = sum(s["flops"] for s in tc) / p.stats["flops_per_item"]
+    assert share > 0.97
+    # the site image region makes the tensor-core item larger than the FP32 one
+    p32 = qfx.Plan(qfx.Circuit(c), n_open=6)
+    assert p.stats["item_bytes"] > p32.stats["item_bytes"]
