@@ -200,6 +200,24 @@ qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x1, int64_t 
                                  int64_t slice_begin, int64_t slice_end, double* out,
                                  void* stream);
 
+/* Adjoint (not in the paper; the multilinear structure of Sec. III's network makes it
+ * exact): gradients of a real loss L(amp) with respect to every gate's 8 matrix values.
+ *   grad_out   device complex128 [n_batch][2^n_open]: dL/dRe(amp) + i dL/dIm(amp) for the
+ *              amplitudes qfx_amplitudes returns for the same arguments (PyTorch's
+ *              convention; for L = sum |amp|^2 it is 2 amp).
+ *   grad_gates device complex128 [n_gates][4], overwritten: for gate g of the caller's
+ *              list, dL/dRe + i dL/dIm of its mat entries (2x2 row-major, or the 4
+ *              diagonal entries of a two-qubit gate), summed over batch and slices.
+ *   workspace  device, >= qfx_backward_workspace_bytes(p), 256-byte aligned.
+ * Runs the contraction in FP32 on the FMA path, keeping the boundary at each line start
+ * and recomputing one line at a time.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA,
+ * QFX_EUNSUPPORTED (more than 64 events on one site's time line). */
+qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                   int64_t slice_begin, int64_t slice_end, const double* grad_out,
+                                   double* grad_gates, void* workspace, size_t ws_bytes,
+                                   void* stream);
+uint64_t qfx_backward_workspace_bytes(const qfx_plan* p);
+
 /* Waits for `stream` and reports any asynchronous CUDA error as QFX_ECUDA, and a
  * tensor-core kernel that gave up a bounded wait (about 1 s) as QFX_ETIMEOUT. */
 qfx_status qfx_sync(void* stream);

@@ -19,7 +19,8 @@ LIB = os.path.join(HERE, "libqfx.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["circuit.cpp", "plan.cpp", "runtime.cu", "fold.cu", "cgemm_simt.cu", "permute.cu",
-           "static_scratch.cu", "cgemm_tc.cu"]
+           "static_scratch.cu", "cgemm_tc.cu",
+           "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

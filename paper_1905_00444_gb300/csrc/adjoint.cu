@@ -1,0 +1,532 @@
+// Adjoint of the amplitude contraction: Wirtinger gradients of a real loss with respect
+// to every gate tensor (PyTorch convention: grad = dL/dRe + i dL/dIm = 2 dL/dconj).
+//
+// The amplitude is multilinear in the site tensors and each gate sits in one site's time
+// fold (two sites for a two-qubit gate), so reverse mode is exact:
+//   forward   L_{i+1}[nh][p][nl][s] = sum_k S_i[k][nh*NL+nl] L_i[p][k][s]      (Sec. III.E)
+//   reverse   R_i[p][k][s]          = sum_n conj(S_i[k][n]) R_{i+1}[nh][p][nl][s]
+//             Gbar_{S_i}[k][n]      = sum_{p,s} conj(L_i[p][k][s]) R_{i+1}[nh][p][nl][s]
+//   seed      R_n = upstream gradient of the amplitudes (scaled by 2^-m)
+//   fold      T[idx] = <x| O_M .. O_1 |0>:  dT/dG[a][b] = w_j[a] u_{j-1}[b] with
+//             u_{j-1} = O_{j-1}..O_1|0>, w_j = <x|O_M..O_{j+1}; grad G = sum Gbar_T conj(dT/dG).
+// Checkpointing: the forward sweep keeps the boundary at the start of every line; the
+// reverse sweep recomputes one line's boundaries from its checkpoint, then walks it
+// backwards.  Memory: (lines + line length + 2) boundary tensors instead of one per site.
+// Scaling: sites were scaled by 2^-e_s and the amplitude by 2^E (E = sum e_s), so the
+// gradient of site s is 2^(E - e_s + m) times what the reverse sweep computes; that
+// factor is applied in FP64 when the per-event partials are reduced.
+// All partial sums are reduced in a fixed order, so results are deterministic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "qfx_internal.h"
+
+namespace qfx {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kMaxEvents = 64;     // events per site the fold adjoint supports
+constexpr int64_t kJChunk = 4096;  // columns per partial in the site-gradient GEMM
+
+uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {   // a * conj(b)
+  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// ---- seed: R_n[f(o)] = gbar[o] * 2^-m ------------------------------------------------
+__global__ void __launch_bounds__(kT) seed_kernel(const double* __restrict__ gout, const int32_t* __restrict__ open_perm,
+                                                  int n_open, float2* R, int* m_out) {
+  __shared__ double red[kT];
+  const int64_t per = int64_t(1) << n_open;
+  double mx = 0.0;
+  for (int64_t o = threadIdx.x; o < per; o += kT) mx = fmax(mx, fmax(fabs(gout[2 * o]), fabs(gout[2 * o + 1])));
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = kT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  int m = 0;
+  if (red[0] > 0.0) frexp(red[0], &m);
+  if (threadIdx.x == 0) *m_out = m;
+  for (int64_t o = threadIdx.x; o < per; o += kT) {
+    int64_t f = 0;
+    for (int i = 0; i < n_open; ++i) f |= ((o >> i) & 1) << open_perm[i];
+    R[f] = make_float2((float)ldexp(gout[2 * o], -m), (float)ldexp(gout[2 * o + 1], -m));
+  }
+}
+
+// ---- reverse step: Rout[p][k][s] = sum_n conj(S[k][n]) Rin[n/NL][p][n%NL][s] ------------
+__global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S, const float2* __restrict__ Rin,
+                                                   float2* __restrict__ Rout, int64_t P, int64_t K,
+                                                   int64_t N, int64_t NL, int64_t Sd) {
+  constexpr int BM = 64, BJ = 64, BR = 16;
+  __shared__ float2 As[BR][BM + 1];
+  __shared__ float2 Bs[BR][BJ + 1];
+  const int64_t J = P * Sd, KT_ = (K + BM - 1) / BM;
+  const int64_t kt = blockIdx.x % KT_, jt = blockIdx.x / KT_;
+  const int64_t k0 = kt * BM, j0 = jt * BJ;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t strideNH = P * NL * Sd;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int64_t n0 = 0; n0 < N; n0 += BR) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = threadIdx.x + i * kT;
+      const int r = e / BM, c = e % BM;
+      const int64_t k = k0 + c, n = n0 + r;
+      float2 v = make_float2(0.f, 0.f);
+      if (k < K && n < N) { v = S[k * N + n]; v.y = -v.y; }
+      As[r][c] = v;
+      const int64_t j = j0 + c;
+      float2 b = make_float2(0.f, 0.f);
+      if (j < J && n < N) b = Rin[(n / NL) * strideNH + (j / Sd) * NL * Sd + (n % NL) * Sd + j % Sd];
+      Bs[r][c] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { a[i] = As[r][ty * 4 + i]; b[i] = Bs[r][tx * 4 + i]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t k = k0 + ty * 4 + i, jj = j0 + tx * 4 + j;
+      if (k < K && jj < J) Rout[(jj / Sd) * K * Sd + k * Sd + jj % Sd] = acc[i][j];
+    }
+}
+
+// ---- site gradient, split over columns: part[c][k][n] = sum_{j in c} conj(L(k,j)) R(n,j) ----
+__global__ void __launch_bounds__(kT) grads_kernel(const float2* __restrict__ Lin, const float2* __restrict__ Rin,
+                                                   float2* __restrict__ part, int64_t P, int64_t K,
+                                                   int64_t N, int64_t NL, int64_t Sd) {
+  constexpr int BM = 64, BN = 64, BJ = 16;
+  __shared__ float2 As[BJ][BM + 1];
+  __shared__ float2 Bs[BJ][BN + 1];
+  const int64_t J = P * Sd;
+  const int64_t k0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t jb = (int64_t)blockIdx.z * kJChunk, je = min(J, jb + kJChunk);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t strideNH = P * NL * Sd;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int64_t j0 = jb; j0 < je; j0 += BJ) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = threadIdx.x + i * kT;
+      const int jj = e % BJ, c = e / BJ;
+      const int64_t j = j0 + jj;
+      const int64_t k = k0 + c, n = n0 + c;
+      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+      if (j < je && k < K) { a = Lin[(j / Sd) * K * Sd + k * Sd + j % Sd]; a.y = -a.y; }
+      if (j < je && n < N) b = Rin[(n / NL) * strideNH + (j / Sd) * NL * Sd + (n % NL) * Sd + j % Sd];
+      As[jj][c] = a;
+      Bs[jj][c] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < BJ; ++r) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { a[i] = As[r][ty * 4 + i]; b[i] = Bs[r][tx * 4 + i]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+  float2* out = part + (int64_t)blockIdx.z * K * N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t k = k0 + ty * 4 + i, n = n0 + tx * 4 + j;
+      if (k < K && n < N) out[k * N + n] = acc[i][j];
+    }
+}
+
+__global__ void __launch_bounds__(kT) reduce_chunks_kernel(const float2* __restrict__ part, int64_t chunks,
+                                                           int64_t KN, float2* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (t >= KN) return;
+  float re = 0.f, im = 0.f;
+  for (int64_t c = 0; c < chunks; ++c) {
+    const float2 v = part[c * KN + t];
+    re += v.x;
+    im += v.y;
+  }
+  out[t] = make_float2(re, im);
+}
+
+// ---- fold adjoint: per-block partial gradients of every event's matrix ----------------
+__global__ void __launch_bounds__(kT) fold_backward_kernel(
+    const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events, const double* __restrict__ mats,
+    const CutDev* __restrict__ cuts, int n_cuts, const uint64_t* __restrict__ x1, int64_t b, int64_t sid,
+    const float2* __restrict__ sgrad, double* __restrict__ bpart, const int64_t* __restrict__ part_off) {
+  __shared__ double wpart[kT / 32][kMaxEvents][8];
+  const FoldSite st = sites[blockIdx.y];
+  const int nev = st.ev_end - st.ev_begin;
+  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if ((int64_t)blockIdx.x * kT >= st.size) return;   // block-uniform
+  const bool active = i < st.size;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t off[4] = {0, 0, 0, 0};
+  for (int c = 0; c < n_cuts; ++c) {
+    const CutDev cd = cuts[c];
+    const int64_t digit = (sid / cd.suffix) % cd.radix;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (st.edge[s] == cd.edge) off[s] = digit * cd.size;
+  }
+  int64_t r = active ? i : 0;
+  const int64_t vd = r % st.dim[4]; r /= st.dim[4];
+  const int64_t vr = r % st.dim[3]; r /= st.dim[3];
+  const int64_t vx = r % st.dim[2]; r /= st.dim[2];
+  const int64_t vl = r % st.dim[1]; r /= st.dim[1];
+  const int64_t vu = r;
+  const uint64_t val0 = (uint64_t)(vu + off[0]), val1 = (uint64_t)(vl + off[1]);
+  const uint64_t val2 = (uint64_t)(vr + off[2]), val3 = (uint64_t)(vd + off[3]);
+  const int xv = st.x_open ? (int)vx : (int)((x1[b] >> st.qubit) & 1ull);
+  // forward: states u_j before each event
+  double2 u0[kMaxEvents + 1], u1[kMaxEvents + 1];
+  u0[0] = make_double2(1.0, 0.0);
+  u1[0] = make_double2(0.0, 0.0);
+  for (int j = 0; j < nev; ++j) {
+    const FoldEvent ev = events[st.ev_begin + j];
+    const double* m = mats + 8 * (int64_t)ev.mat;
+    double2 a = u0[j], c = u1[j];
+    if (ev.kind == EV_GATE) {
+      const double2 n0 = make_double2(m[0] * a.x - m[1] * a.y + m[2] * c.x - m[3] * c.y,
+                                      m[0] * a.y + m[1] * a.x + m[2] * c.y + m[3] * c.x);
+      const double2 n1 = make_double2(m[4] * a.x - m[5] * a.y + m[6] * c.x - m[7] * c.y,
+                                      m[4] * a.y + m[5] * a.x + m[6] * c.y + m[7] * c.x);
+      a = n0;
+      c = n1;
+    } else {
+      const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
+      const int k = (int)((bv >> ev.bit) & 1ull);
+      if (ev.kind == EV_PROJ) {
+        if (k) a = make_double2(0.0, 0.0);
+        else   c = make_double2(0.0, 0.0);
+      } else {
+        a = cmul(a, make_double2(m[4 * k + 0], m[4 * k + 1]));
+        c = cmul(c, make_double2(m[4 * k + 2], m[4 * k + 3]));
+      }
+    }
+    u0[j + 1] = a;
+    u1[j + 1] = c;
+  }
+  double2 g = make_double2(0.0, 0.0);
+  if (active) {
+    const float2 gf = sgrad[st.offset + i];
+    g = make_double2(gf.x, gf.y);
+  }
+  // backward: row vector w = <x| O_M .. O_{j+1}
+  double2 w0 = make_double2(xv == 0 ? 1.0 : 0.0, 0.0), w1 = make_double2(xv == 1 ? 1.0 : 0.0, 0.0);
+  for (int j = nev - 1; j >= 0; --j) {
+    const FoldEvent ev = events[st.ev_begin + j];
+    const double* m = mats + 8 * (int64_t)ev.mat;
+    const double2 a = u0[j], c = u1[j];
+    double2 d[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                    make_double2(0.0, 0.0)};
+    int k = 0;
+    if (ev.kind != EV_GATE) {
+      const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
+      k = (int)((bv >> ev.bit) & 1ull);
+    }
+    if (ev.kind == EV_GATE) {
+      d[0] = cmulc(g, cmul(w0, a));   // dG[0][0] = w0 u0
+      d[1] = cmulc(g, cmul(w0, c));   // dG[0][1] = w0 u1
+      d[2] = cmulc(g, cmul(w1, a));   // dG[1][0] = w1 u0
+      d[3] = cmulc(g, cmul(w1, c));   // dG[1][1] = w1 u1
+    } else if (ev.kind == EV_DIAG) {
+      d[2 * k + 0] = cmulc(g, cmul(w0, a));
+      d[2 * k + 1] = cmulc(g, cmul(w1, c));
+    }
+    // warp sums, one slot per warp (no atomics)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      double re = d[t].x, im = d[t].y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) {
+        wpart[warp][j][2 * t] = re;
+        wpart[warp][j][2 * t + 1] = im;
+      }
+    }
+    // w <- w O_j
+    if (ev.kind == EV_GATE) {
+      const double2 g00 = make_double2(m[0], m[1]), g01 = make_double2(m[2], m[3]);
+      const double2 g10 = make_double2(m[4], m[5]), g11 = make_double2(m[6], m[7]);
+      const double2 n0 = make_double2(cmul(w0, g00).x + cmul(w1, g10).x, cmul(w0, g00).y + cmul(w1, g10).y);
+      const double2 n1 = make_double2(cmul(w0, g01).x + cmul(w1, g11).x, cmul(w0, g01).y + cmul(w1, g11).y);
+      w0 = n0;
+      w1 = n1;
+    } else if (ev.kind == EV_PROJ) {
+      if (k) w0 = make_double2(0.0, 0.0);
+      else   w1 = make_double2(0.0, 0.0);
+    } else {
+      w0 = cmul(w0, make_double2(m[4 * k + 0], m[4 * k + 1]));
+      w1 = cmul(w1, make_double2(m[4 * k + 2], m[4 * k + 3]));
+    }
+  }
+  __syncthreads();
+  double* outp = bpart + part_off[blockIdx.y] + (int64_t)blockIdx.x * nev * 8;
+  for (int t = threadIdx.x; t < nev * 8; t += kT) {
+    const int j = t / 8, e = t % 8;
+    double s = 0.0;
+    for (int w = 0; w < kT / 32; ++w) s += wpart[w][j][e];
+    outp[j * 8 + e] = s;
+  }
+}
+
+// one thread per (event, entry): sum the site's blocks, apply 2^(E - e_s + m)
+__global__ void __launch_bounds__(kT) event_reduce_kernel(const FoldSite* __restrict__ sites, int n_sites,
+                                                          const double* __restrict__ bpart,
+                                                          const int64_t* __restrict__ part_off,
+                                                          const int* __restrict__ hdr_exps, const int* m_ptr,
+                                                          int n_events, double* __restrict__ evgrad) {
+  const int t = blockIdx.x * kT + threadIdx.x;
+  if (t >= n_events * 8) return;
+  const int e = t / 8, entry = t % 8;
+  int s = 0;
+  for (int q = 0; q < n_sites; ++q)
+    if (e >= sites[q].ev_begin && e < sites[q].ev_end) s = q;
+  const FoldSite st = sites[s];
+  const int nev = st.ev_end - st.ev_begin, j = e - st.ev_begin;
+  const int64_t nblk = (st.size + kT - 1) / kT;
+  double sum = 0.0;
+  for (int64_t bk = 0; bk < nblk; ++bk) sum += bpart[part_off[s] + bk * nev * 8 + j * 8 + entry];
+  int E = 0;
+  for (int q = 0; q < n_sites; ++q) E += hdr_exps[q];
+  evgrad[t] = ldexp(sum, E - hdr_exps[s] + *m_ptr);
+}
+
+// one thread per (gate, entry): add the gate's events into the output (item order)
+__global__ void __launch_bounds__(kT) gate_accum_kernel(const int32_t* __restrict__ gate_ev, int n_gates,
+                                                        const double* __restrict__ evgrad, double* grad) {
+  const int t = blockIdx.x * kT + threadIdx.x;
+  if (t >= n_gates * 8) return;
+  const int gte = t / 8, entry = t % 8;
+  double s = 0.0;
+  for (int q = 0; q < 2; ++q) {
+    const int e = gate_ev[2 * gte + q];
+    if (e >= 0) s += evgrad[e * 8 + entry];
+  }
+  grad[t] += s;
+}
+
+struct BwdLayout {
+  uint64_t hdr, sites, sgrad, ckpt, lb, rr, gpart, bpart, evgrad, partoff, total;
+};
+
+BwdLayout bwd_layout(const qfx_plan* p) {
+  BwdLayout L{};
+  const uint64_t B = a256((uint64_t)p->max_elements * 8);
+  uint64_t o = 0;
+  L.hdr = o; o += a256((uint64_t)p->n * 8 + 16);
+  L.sites = o; o += a256((uint64_t)p->site_total * 8);
+  L.sgrad = o; o += a256((uint64_t)p->site_total * 8);
+  L.ckpt = o; o += (uint64_t)p->lines * B;
+  L.lb = o; o += (uint64_t)p->line_len * B;
+  L.rr = o; o += 2 * B;
+  uint64_t gp = 0;
+  for (size_t i = 1; i < p->steps.size(); ++i) {
+    const Step& s = p->steps[i];
+    const uint64_t chunks = (uint64_t)((s.P * s.Sd + kJChunk - 1) / kJChunk);
+    gp = std::max(gp, chunks * (uint64_t)s.K * (uint64_t)s.N * 8);
+  }
+  L.gpart = o; o += a256(gp);
+  uint64_t bp = 0;
+  for (const auto& fs : p->sites) bp += (uint64_t)((fs.size + kT - 1) / kT) * (fs.ev_end - fs.ev_begin) * 8;
+  L.bpart = o; o += a256(bp * 8);
+  L.evgrad = o; o += a256((uint64_t)p->events.size() * 8 * 8);
+  L.partoff = o; o += a256((uint64_t)p->n * 8);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+}  // namespace qfx
+
+using namespace qfx;
+
+extern "C" uint64_t qfx_backward_workspace_bytes(const qfx_plan* p) {
+  if (!p) return 0;
+  return bwd_layout(p).total;
+}
+
+extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                              int64_t slice_begin, int64_t slice_end,
+                                              const double* grad_out, double* grad_gates,
+                                              void* workspace, size_t ws_bytes, void* stream) {
+  qfx_status s = check_amplitudes_args(p, x1, n_batch, slice_begin, slice_end, grad_out);
+  if (s != QFX_OK) return s;
+  if (!grad_gates || !workspace) return fail(QFX_EINVAL, "qfx_amplitudes_backward: NULL argument");
+  if (((uintptr_t)workspace & 255) || ((uintptr_t)grad_gates & 15))
+    return fail(QFX_EINVAL, "qfx_amplitudes_backward: misaligned workspace or grad_gates");
+  for (const auto& fs : p->sites)
+    if (fs.ev_end - fs.ev_begin > kMaxEvents)
+      return fail(QFX_EUNSUPPORTED, "qfx_amplitudes_backward: a site has more than 64 time-line events");
+  const BwdLayout Lw = bwd_layout(p);
+  if (ws_bytes < Lw.total) return fail(QFX_ENOMEM, "qfx_amplitudes_backward: workspace smaller than qfx_backward_workspace_bytes()");
+  const DeviceTables* tp = nullptr;
+  s = ensure_tables(p, &tp);
+  if (s != QFX_OK) return s;
+  const DeviceTables& t = *tp;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  const uint64_t B = a256((uint64_t)p->max_elements * 8);
+  const int n = p->n, L = p->line_len, W = p->lines;
+  const int n_open = (int)p->open_sites.size();
+  const int64_t per = int64_t(1) << n_open;
+  int64_t max_site = 1;
+  for (const auto& fs : p->sites) max_site = std::max(max_site, fs.size);
+
+  // per-site offsets of the fold-adjoint partials (host -> workspace, once per call)
+  std::vector<int64_t> partoff(n);
+  {
+    int64_t o = 0;
+    for (int q = 0; q < n; ++q) {
+      partoff[q] = o;
+      const auto& fs = p->sites[q];
+      o += ((fs.size + kT - 1) / kT) * (fs.ev_end - fs.ev_begin) * 8;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(ws + Lw.partoff, partoff.data(), n * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: partial offsets");
+  e = cudaMemsetAsync(grad_gates, 0, (size_t)p->n_gates * 8 * sizeof(double), st);
+  if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: clearing grad_gates");
+
+  char* hdr = ws + Lw.hdr;
+  int* exps = (int*)hdr + n;
+  int* m_ptr = (int*)(hdr + (uint64_t)n * 8);
+  char* sites = ws + Lw.sites;
+  float2* sgrad = (float2*)(ws + Lw.sgrad);
+  auto ckpt = [&](int w) { return ws + Lw.ckpt + (uint64_t)w * B; };
+  auto lb = [&](int j) { return ws + Lw.lb + (uint64_t)j * B; };
+  auto rr = [&](int j) { return ws + Lw.rr + (uint64_t)j * B; };
+  auto site_ptr = [&](int q) { return sites + (uint64_t)p->sites[q].offset * 8; };
+  const int64_t n_items = (slice_end - slice_begin) * n_batch;
+  auto step_fwd = [&](int i, const char* in, char* out) -> int {
+    const Step& sp = p->steps[i];
+    const int v = pick_variant(sp.N, sp.Sd);
+    return launch_step(site_ptr(sp.site), 0, in, 0, out, 0, sp.P, sp.K, sp.N, sp.NL, sp.Sd, 1, v,
+                       QFX_PREC_FP32_SIMT, st);
+  };
+
+  for (int64_t item = 0; item < n_items; ++item) {
+    const int64_t b = item % n_batch, sid = slice_begin + item / n_batch;
+    e = cudaMemsetAsync(hdr, 0, (size_t)n * 8 + 16, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: header");
+    int err = launch_fold(t, n, max_site, (int)p->cut_dev.size(), x1, n_batch, slice_begin, item, 1,
+                          hdr, 0, sites, 0, 0, st);
+    if (!err) err = launch_scale(t, n, max_site, 1, hdr, 0, sites, 0, 0, st);
+    if (err) return cuda_fail(err, "qfx_amplitudes_backward: fold");
+    // forward sweep, keeping the boundary at the start of every line
+    const char* cur = site_ptr(p->steps[0].site);
+    int pp = 0;
+    for (int i = 1; i < n - 1; ++i) {
+      char* out = ((i + 1) % L == 0) ? ckpt((i + 1) / L) : rr(pp);
+      if (out == rr(pp)) pp ^= 1;
+      err = step_fwd(i, cur, out);
+      if (err) return cuda_fail(err, "qfx_amplitudes_backward: forward step");
+      cur = out;
+    }
+    // seed from this batch row's upstream gradient
+    float2* Rcur = (float2*)rr(0);
+    int rsel = 0;
+    seed_kernel<<<1, kT, 0, st>>>(grad_out + 2 * b * per, t.open_perm, n_open, Rcur, m_ptr);
+    count_launch();
+    // reverse, line by line
+    for (int w = W - 1; w >= 0; --w) {
+      const int i0 = w * L;
+      // recompute this line's inputs: input of step i0 + j is lb(j) (j >= 1) or ckpt(w)
+      auto line_in = [&](int j) -> const char* {
+        if (j == 0) return w == 0 ? nullptr : ckpt(w);
+        if (w == 0 && j == 1) return site_ptr(p->steps[0].site);
+        return lb(j);
+      };
+      for (int j = 1; j < L && i0 + j < n; ++j) {
+        if (w == 0 && j == 1) continue;           // L_1 is site 0 itself
+        err = step_fwd(i0 + j - 1, line_in(j - 1), lb(j));
+        if (err) return cuda_fail(err, "qfx_amplitudes_backward: recompute step");
+      }
+      for (int j = std::min(L, n - i0) - 1; j >= 0; --j) {
+        const int i = i0 + j;
+        const Step& sp = p->steps[i];
+        float2* gdst = sgrad + p->sites[sp.site].offset;
+        if (i == 0) {
+          e = cudaMemcpyAsync(gdst, Rcur, (size_t)sp.N * 8, cudaMemcpyDeviceToDevice, st);
+          if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: site 0 gradient");
+          continue;
+        }
+        const float2* Lin = (const float2*)line_in(j);
+        const int64_t J = sp.P * sp.Sd, chunks = (J + kJChunk - 1) / kJChunk;
+        dim3 gg((unsigned)((sp.K + 63) / 64), (unsigned)((sp.N + 63) / 64), (unsigned)chunks);
+        float2* part = (float2*)(ws + Lw.gpart);
+        grads_kernel<<<gg, kT, 0, st>>>(Lin, Rcur, part, sp.P, sp.K, sp.N, sp.NL, sp.Sd);
+        const int64_t KN = sp.K * sp.N;
+        reduce_chunks_kernel<<<(unsigned)((KN + kT - 1) / kT), kT, 0, st>>>(part, chunks, KN, gdst);
+        float2* Rnext = (float2*)rr(rsel ^ 1);
+        const int64_t blocks = ((sp.K + 63) / 64) * ((J + 63) / 64);
+        rstep_kernel<<<(unsigned)blocks, kT, 0, st>>>((const float2*)site_ptr(sp.site), Rcur, Rnext, sp.P,
+                                                      sp.K, sp.N, sp.NL, sp.Sd);
+        count_launch(3);
+        rsel ^= 1;
+        Rcur = Rnext;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: reverse step");
+      }
+    }
+    // back through every site's time fold
+    dim3 fg((unsigned)((max_site + kT - 1) / kT), n);
+    fold_backward_kernel<<<fg, kT, 0, st>>>(t.sites, t.events, t.mats, t.cuts, (int)p->cut_dev.size(), x1, b,
+                                            sid, sgrad, (double*)(ws + Lw.bpart),
+                                            (const int64_t*)(ws + Lw.partoff));
+    const int nev = (int)p->events.size();
+    event_reduce_kernel<<<(nev * 8 + kT - 1) / kT, kT, 0, st>>>(t.sites, n, (const double*)(ws + Lw.bpart),
+                                                               (const int64_t*)(ws + Lw.partoff), exps,
+                                                               m_ptr, nev, (double*)(ws + Lw.evgrad));
+    gate_accum_kernel<<<(p->n_gates * 8 + kT - 1) / kT, kT, 0, st>>>(t.gate_ev, p->n_gates,
+                                                                     (const double*)(ws + Lw.evgrad), grad_gates);
+    count_launch(3);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: fold adjoint");
+  }
+  return QFX_OK;
+}

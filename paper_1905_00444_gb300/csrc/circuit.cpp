@@ -51,7 +51,7 @@ qfx_status build(int32_t rows, int32_t cols, const qfx_gate* gates, int64_t n_ga
     if (two != kind_two) { delete c; return qfx::fail(QFX_EINVAL, where + "kind does not match arity"); }
     for (double v : g.mat)
       if (!std::isfinite(v)) { delete c; return qfx::fail(QFX_EINVAL, where + "non-finite matrix entry"); }
-    qfx::Gate q{g.layer, g.q0, g.q1, g.kind, {}};
+    qfx::Gate q{g.layer, g.q0, g.q1, g.kind, {}, (int)i};
     std::memcpy(q.m, g.mat, sizeof(q.m));
     c->gates.push_back(q);
   }

@@ -136,6 +136,9 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     auto p = new qfx_plan;
     std::unique_ptr<qfx_plan> guard(p);
     p->rows = c->rows; p->cols = c->cols; p->n = n;
+    p->n_gates = (int)c->gates.size();
+    p->lines = geo.W;
+    p->line_len = geo.L;
     p->precision = o->precision;
     if (o->tc_flags & ~QFX_TC_FAST_ACCUMULATION) return qfx::fail(QFX_EINVAL, "unknown tc_flags bits");
     p->tc_flags = o->tc_flags;
@@ -322,6 +325,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
         const auto& g = c->gates[gi];
         if (g.q0 != q && g.q1 != q) continue;
         qfx::FoldEvent ev{};
+        ev.gate = g.index;
         ev.mat = (int32_t)(p->mats.size() / 8);
         p->mats.insert(p->mats.end(), g.m, g.m + 8);
         if (g.q1 < 0) {
@@ -342,6 +346,12 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       p->sites[q] = fs;
     }
     p->site_total = offset;
+    p->gate_ev.assign(2 * c->gates.size(), -1);
+    for (size_t e = 0; e < p->events.size(); ++e) {
+      const int g = p->events[e].gate;
+      if (p->gate_ev[2 * g] < 0) p->gate_ev[2 * g] = (int32_t)e;
+      else p->gate_ev[2 * g + 1] = (int32_t)e;
+    }
 
     // workspace layout
     qfx::Layout& L = p->layout;

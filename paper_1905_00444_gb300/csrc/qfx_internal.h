@@ -22,6 +22,7 @@ constexpr int kMaxCuts = 64;
 struct Gate {
   int layer, q0, q1, kind;
   double m[8];
+  int index;   // position in the caller's gate list
 };
 
 }  // namespace qfx
@@ -47,6 +48,7 @@ struct FoldEvent {
   int32_t slot;   // bond slot 0..3 (up, left, right, down) holding the leg
   int32_t bit;    // bit of the bond value that is this leg
   int32_t mat;    // index into the matrix table (4 complex doubles each)
+  int32_t gate;   // the gate's index in the caller's list (gradients are reported there)
 };
 
 // Site tensor layout: T[up][left][x][right][down] (row-major), so that k = (up, left)
@@ -96,18 +98,22 @@ struct DeviceTables {
   const double* mats = nullptr;  // [n_mats][8]
   const CutDev* cuts = nullptr;
   const int32_t* open_perm = nullptr;  // output bit i -> bit of the final tensor index
+  const int32_t* gate_ev = nullptr;    // per caller gate: its (up to 2) fold events, -1 if none
 };
 
 }  // namespace qfx
 
 struct qfx_plan {
   int rows = 0, cols = 0, n = 0;
+  int n_gates = 0;
+  int lines = 0, line_len = 0;    // sweep geometry: steps [w*line_len, (w+1)*line_len) form line w
   int precision = 0;
   int tc_flags = 0;
   bool transposed = false;        // lines are grid rows instead of columns
   std::vector<int> order;         // qubits in sweep order
   std::vector<int> open_sites;    // user order (output bit i)
   std::vector<int32_t> open_perm; // output bit i -> final tensor bit
+  std::vector<int32_t> gate_ev;   // 2 per caller gate
   std::vector<std::pair<int, int>> edges;  // (q_lo, q_hi)
   std::vector<int> edge_legs;     // legs per edge
   std::vector<qfx_cut> cuts;      // in slice-id digit order (first = most significant)
@@ -168,12 +174,13 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
 qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out);
 void free_tables(DeviceTables& t);
 // host image of a plan's tables; offs[] = byte offsets of sites, events, mats, cuts, perm
-size_t pack_tables(const qfx_plan* p, std::vector<char>& host, size_t offs[5]);
-DeviceTables tables_at(void* base, const size_t offs[5]);
+constexpr int kTableRegions = 6;
+size_t pack_tables(const qfx_plan* p, std::vector<char>& host, size_t offs[kTableRegions]);
+DeviceTables tables_at(void* base, const size_t offs[kTableRegions]);
 
 // the executor behind qfx_amplitudes (argument checks, items in flight, run)
 qfx_status check_amplitudes_args(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
-                                 int64_t slice_begin, int64_t slice_end, double* out);
+                                 int64_t slice_begin, int64_t slice_end, const void* out);
 int64_t items_in_flight(const qfx_plan* p, size_t ws_bytes);
 qfx_status exec_amplitudes(const qfx_plan* p, const DeviceTables& t, const uint64_t* x1,
                            int64_t n_batch, int64_t slice_begin, int64_t slice_end,

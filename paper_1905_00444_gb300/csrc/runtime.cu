@@ -92,29 +92,24 @@ void free_tables(DeviceTables& t) {
   t = DeviceTables{};
 }
 
-size_t pack_tables(const qfx_plan* p, std::vector<char>& host, size_t offs[5]) {
-  const size_t s_sites = align256(p->sites.size() * sizeof(FoldSite));
-  const size_t s_ev = align256(std::max<size_t>(1, p->events.size()) * sizeof(FoldEvent));
-  const size_t s_mats = align256(std::max<size_t>(1, p->mats.size()) * sizeof(double));
-  const size_t s_cuts = align256(std::max<size_t>(1, p->cut_dev.size()) * sizeof(CutDev));
-  const size_t s_perm = align256(std::max<size_t>(1, p->open_perm.size()) * sizeof(int32_t));
-  offs[0] = 0;
-  offs[1] = s_sites;
-  offs[2] = offs[1] + s_ev;
-  offs[3] = offs[2] + s_mats;
-  offs[4] = offs[3] + s_cuts;
-  const size_t total = offs[4] + s_perm;
+size_t pack_tables(const qfx_plan* p, std::vector<char>& host, size_t offs[kTableRegions]) {
+  const void* src[kTableRegions] = {p->sites.data(), p->events.data(), p->mats.data(),
+                                    p->cut_dev.data(), p->open_perm.data(), p->gate_ev.data()};
+  const size_t len[kTableRegions] = {p->sites.size() * sizeof(FoldSite), p->events.size() * sizeof(FoldEvent),
+                                     p->mats.size() * sizeof(double), p->cut_dev.size() * sizeof(CutDev),
+                                     p->open_perm.size() * sizeof(int32_t), p->gate_ev.size() * sizeof(int32_t)};
+  size_t total = 0;
+  for (int r = 0; r < kTableRegions; ++r) {
+    offs[r] = total;
+    total += align256(std::max<size_t>(1, len[r]));
+  }
   host.assign(total, 0);
-  char* h = host.data();
-  std::memcpy(h + offs[0], p->sites.data(), p->sites.size() * sizeof(FoldSite));
-  std::memcpy(h + offs[1], p->events.data(), p->events.size() * sizeof(FoldEvent));
-  std::memcpy(h + offs[2], p->mats.data(), p->mats.size() * sizeof(double));
-  std::memcpy(h + offs[3], p->cut_dev.data(), p->cut_dev.size() * sizeof(CutDev));
-  std::memcpy(h + offs[4], p->open_perm.data(), p->open_perm.size() * sizeof(int32_t));
+  for (int r = 0; r < kTableRegions; ++r)
+    if (len[r]) std::memcpy(host.data() + offs[r], src[r], len[r]);
   return total;
 }
 
-DeviceTables tables_at(void* base, const size_t offs[5]) {
+DeviceTables tables_at(void* base, const size_t offs[kTableRegions]) {
   char* b = (char*)base;
   DeviceTables t;
   t.base = base;
@@ -123,6 +118,7 @@ DeviceTables tables_at(void* base, const size_t offs[5]) {
   t.mats = (const double*)(b + offs[2]);
   t.cuts = (const CutDev*)(b + offs[3]);
   t.open_perm = (const int32_t*)(b + offs[4]);
+  t.gate_ev = (const int32_t*)(b + offs[5]);
   return t;
 }
 
@@ -135,7 +131,7 @@ qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out) {
   DeviceTables& t = p->dev[dev];
   if (!t.base) {
     std::vector<char> host;
-    size_t offs[5];
+    size_t offs[kTableRegions];
     const size_t total = pack_tables(p, host, offs);
     void* d = nullptr;
     e = cudaMalloc(&d, total);
@@ -149,7 +145,7 @@ qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out) {
 }
 
 qfx_status check_amplitudes_args(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
-                                 int64_t slice_begin, int64_t slice_end, double* out) {
+                                 int64_t slice_begin, int64_t slice_end, const void* out) {
   if (!p || !x1 || !out) return fail(QFX_EINVAL, "qfx_amplitudes: NULL argument");
   if (n_batch < 1) return fail(QFX_EINVAL, "qfx_amplitudes: n_batch must be >= 1");
   if (slice_begin < 0 || slice_end > p->n_slices || slice_begin >= slice_end)

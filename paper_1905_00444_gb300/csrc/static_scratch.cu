@@ -59,7 +59,7 @@ extern "C" qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x
   qfx_status s = qfx::check_amplitudes_args(p, x1, n_batch, slice_begin, slice_end, out);
   if (s != QFX_OK) return s;
   std::vector<char> host;
-  size_t offs[5];
+  size_t offs[qfx::kTableRegions];
   const uint64_t tables = align256(qfx::pack_tables(p, host, offs));
   const uint64_t need = tables + qfx_workspace_bytes(p, 1);
   if (need > (uint64_t)QFX_STATIC_SCRATCH_BYTES)

@@ -77,6 +77,8 @@ def _declare(lib):
         "qfx_plan_upload": (st, [vp]),
         "qfx_amplitudes": (st, [vp, vp, i64, i64, i64, vp, C.c_size_t, vp, vp]),
         "qfx_amplitudes_static": (st, [vp, vp, i64, i64, i64, vp, vp]),
+        "qfx_amplitudes_backward": (st, [vp, vp, i64, i64, i64, vp, vp, vp, C.c_size_t, vp]),
+        "qfx_backward_workspace_bytes": (u64, [vp]),
         "qfx_sync": (st, [vp]),
         "qfx_contract_step": (st, [vp, vp, vp, i64, i64, i64, i64, i64, i32, i32, vp, C.c_size_t, vp]),
         "qfx_step_scratch_bytes": (u64, [i64, i64, i32]),
@@ -140,6 +142,8 @@ class Circuit:
         if text is not None:
             _check(lib.qfx_circuit_from_text(text.encode(), C.byref(h)))
             self.rows = self.cols = None
+            self.n_gates = sum(1 for ln in text.splitlines()
+                               if ln.split("#")[0].strip() and not ln.strip().startswith("grid"))
         else:
             arr = (Gate * max(1, len(src.gates)))()
             for i, g in enumerate(src.gates):
@@ -150,6 +154,7 @@ class Circuit:
                     arr[i].mat[2 * j + 1] = float(v.imag)
             _check(lib.qfx_circuit_create(src.rows, src.cols, arr, len(src.gates), C.byref(h)))
             self.rows, self.cols = src.rows, src.cols
+            self.n_gates = len(src.gates)
         self._h = h
 
     def __del__(self):
@@ -183,6 +188,7 @@ class Plan:
         _check(lib.qfx_plan_create(circuit._h, C.byref(opts), C.byref(h)))
         self._h = h
         self._circuit = circuit
+        self.stats_n_gates = circuit.n_gates
         st = PlanStats()
         _check(lib.qfx_plan_info(h, C.byref(st)))
         self.stats = {f: getattr(st, f) for f, _ in PlanStats._fields_}
@@ -236,6 +242,24 @@ def amplitudes(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Optional[int]
     _check(lib.qfx_amplitudes(plan._h, x1.data_ptr(), n_batch, slice_begin, slice_end,
                               workspace.data_ptr(), workspace.numel(), out.data_ptr(),
                               _stream_ptr(stream)))
+    return out
+
+
+def amplitudes_backward(plan: Plan, x1, grad_out, *, slice_begin: int = 0,
+                        slice_end: Optional[int] = None, workspace=None, stream=None):
+    """Gradients [n_gates, 4] (complex128) of a real loss with respect to every gate's
+    matrix entries, given grad_out = dL/dRe(amp) + i dL/dIm(amp) [n_batch, 2^n_open]."""
+    import torch
+    if slice_end is None:
+        slice_end = plan.n_slices
+    if workspace is None:
+        workspace = torch.empty(int(lib.qfx_backward_workspace_bytes(plan._h)), dtype=torch.uint8,
+                                device=x1.device)
+    grad_out = grad_out.to(torch.complex128).contiguous()
+    out = torch.empty((plan.stats_n_gates, 4), dtype=torch.complex128, device=x1.device)
+    _check(lib.qfx_amplitudes_backward(plan._h, x1.data_ptr(), x1.numel(), slice_begin, slice_end,
+                                       grad_out.data_ptr(), out.data_ptr(), workspace.data_ptr(),
+                                       workspace.numel(), _stream_ptr(stream)))
     return out
 
 
