@@ -200,6 +200,39 @@ qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x1, int64_t 
                                  int64_t slice_begin, int64_t slice_end, double* out,
                                  void* stream);
 
+/* Batched execution (Sec. III.A: slices are independent paths; Sec. III.B: x1 batches).
+ * Many work items -- every (slice, x1) of every listed item, of any mix of plans and
+ * shapes -- run in ONE persistent kernel: a device task queue of fold chunks, scale
+ * chunks, contraction-step tiles (FP32 tiles, each step's plan-chosen variant) and FP64
+ * accumulations, with per-segment completion counters as dependencies and bounded waits.
+ * Each batch item's `out` rows get the same values qfx_amplitudes would produce. */
+typedef struct {
+  const qfx_plan* plan;
+  const uint64_t* x1;      /* device [n_batch] */
+  int64_t n_batch;
+  int64_t slice_begin, slice_end;
+  double* out;             /* device complex128 [n_batch][2^n_open], overwritten */
+} qfx_batch_item;
+
+typedef struct qfx_batch qfx_batch;
+
+/* Workspace that lets `slots` work items be in flight at once (an upper bound). */
+uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32_t n_items, int64_t slots);
+
+/* Builds the schedule and uploads it into `workspace` (synchronously on `stream`; also
+ * uploads plan tables).  The workspace, items' x1 and out buffers must stay valid while
+ * the batch is used.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA. */
+qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_items, void* workspace,
+                             size_t ws_bytes, qfx_batch** out, void* stream);
+
+/* Clears the queue counters and launches the persistent kernel: asynchronous, no
+ * allocation and no host synchronisation, so it can be captured in a CUDA graph.  A
+ * dependency wait that expires (5 s) is reported by qfx_sync as QFX_ETIMEOUT. */
+qfx_status qfx_batch_run(const qfx_batch* b, void* stream);
+
+qfx_status qfx_batch_info(const qfx_batch* b, int64_t* n_work, int64_t* n_tasks, int64_t* slots);
+void qfx_batch_destroy(qfx_batch* b);
+
 /* Adjoint (not in the paper; the multilinear structure of Sec. III's network makes it
  * exact): gradients of a real loss L(amp) with respect to every gate's 8 matrix values.
  *   grad_out   device complex128 [n_batch][2^n_open]: dL/dRe(amp) + i dL/dIm(amp) for the

@@ -9,7 +9,7 @@ from .build import build as _build
 _build()
 
 from .qfx import (  # noqa: E402,F401
-    Circuit, Plan, QfxError, amplitudes, amplitudes_backward, amplitudes_static, contract_step, header_symbols, launch_count, lib,
+    Batch, Circuit, Plan, QfxError, amplitudes, amplitudes_backward, amplitudes_static, contract_step, header_symbols, launch_count, lib,
     permute, profile_collect, profile_enable, sync, version,
 )
 from .sharding import partition_slices, reduce_partials  # noqa: E402,F401

@@ -15,19 +15,13 @@
 // FP64 when the slice contributions are added (Sec. III.A: sum over paths).
 #include <cuda_runtime.h>
 
+#include "fold_element.cuh"
 #include "qfx_internal.h"
 
 namespace qfx {
 namespace {
 
 constexpr int kThreads = 256;
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) {
-  return make_double2(a.x + b.x, a.y + b.y);
-}
 
 __global__ void __launch_bounds__(kThreads) fold_kernel(
     const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events,
@@ -44,48 +38,7 @@ __global__ void __launch_bounds__(kThreads) fold_kernel(
     const int64_t item = item0 + g;
     const int64_t b = item % n_batch;
     const int64_t sid = slice_begin + item / n_batch;
-    int64_t off[4] = {0, 0, 0, 0};
-    for (int c = 0; c < n_cuts; ++c) {
-      const CutDev cd = cuts[c];
-      const int64_t digit = (sid / cd.suffix) % cd.radix;
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (st.edge[s] == cd.edge) off[s] = digit * cd.size;
-    }
-    int64_t r = i;
-    const int64_t vd = r % st.dim[4]; r /= st.dim[4];
-    const int64_t vr = r % st.dim[3]; r /= st.dim[3];
-    const int64_t vx = r % st.dim[2]; r /= st.dim[2];
-    const int64_t vl = r % st.dim[1]; r /= st.dim[1];
-    const int64_t vu = r;
-    const uint64_t val0 = (uint64_t)(vu + off[0]), val1 = (uint64_t)(vl + off[1]);
-    const uint64_t val2 = (uint64_t)(vr + off[2]), val3 = (uint64_t)(vd + off[3]);
-    const int xv = st.x_open ? (int)vx : (int)((x1[b] >> st.qubit) & 1ull);
-    double2 v0 = make_double2(1.0, 0.0), v1 = make_double2(0.0, 0.0);
-    for (int e = st.ev_begin; e < st.ev_end; ++e) {
-      const FoldEvent ev = events[e];
-      const double* m = mats + 8 * (int64_t)ev.mat;
-      if (ev.kind == EV_GATE) {
-        const double2 g00 = make_double2(m[0], m[1]), g01 = make_double2(m[2], m[3]);
-        const double2 g10 = make_double2(m[4], m[5]), g11 = make_double2(m[6], m[7]);
-        const double2 n0 = cadd(cmul(g00, v0), cmul(g01, v1));
-        const double2 n1 = cadd(cmul(g10, v0), cmul(g11, v1));
-        v0 = n0;
-        v1 = n1;
-      } else {
-        const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
-        const int k = (int)((bv >> ev.bit) & 1ull);
-        if (ev.kind == EV_PROJ) {
-          if (k) v0 = make_double2(0.0, 0.0);
-          else   v1 = make_double2(0.0, 0.0);
-        } else {
-          v0 = cmul(v0, make_double2(m[4 * k + 0], m[4 * k + 1]));
-          v1 = cmul(v1, make_double2(m[4 * k + 2], m[4 * k + 3]));
-        }
-      }
-    }
-    const double2 res = xv ? v1 : v0;
-    const float2 out = make_float2((float)res.x, (float)res.y);
+    const float2 out = foldk::fold_element(st, events, mats, cuts, n_cuts, x1[b], sid, i);
     float2* T = reinterpret_cast<float2*>(items + (uint64_t)g * item_bytes + sites_off) + st.offset;
     T[i] = out;
     mx = fmaxf(fabsf(out.x), fabsf(out.y));

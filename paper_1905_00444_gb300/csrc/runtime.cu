@@ -249,6 +249,9 @@ extern "C" qfx_status qfx_sync(void* stream) {
   const int tc = tc_take_status();
   if (tc < 0) return fail(QFX_ECUDA, "qfx_sync: reading the tensor-core status word failed");
   if (tc > 0) return fail(QFX_ETIMEOUT, "qfx_sync: a tensor-core contraction step gave up waiting (bounded wait expired)");
+  const int bt = batch_take_status();
+  if (bt < 0) return fail(QFX_ECUDA, "qfx_sync: reading the batch status word failed");
+  if (bt > 0) return fail(QFX_ETIMEOUT, "qfx_sync: the batch scheduler gave up a dependency wait (bounded wait expired)");
   return QFX_OK;
 }
 

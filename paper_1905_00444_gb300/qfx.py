@@ -56,6 +56,11 @@ class StepInfo(C.Structure):
                 ("bytes", C.c_double)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("x1", C.c_void_p), ("n_batch", C.c_int64),
+                ("slice_begin", C.c_int64), ("slice_end", C.c_int64), ("out", C.c_void_p)]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("step", C.c_int32), ("variant", C.c_int32), ("kind", C.c_int32),
                 ("ms", C.c_float), ("flops", C.c_double), ("bytes", C.c_double)]
@@ -79,6 +84,11 @@ def _declare(lib):
         "qfx_amplitudes_static": (st, [vp, vp, i64, i64, i64, vp, vp]),
         "qfx_amplitudes_backward": (st, [vp, vp, i64, i64, i64, vp, vp, vp, C.c_size_t, vp]),
         "qfx_backward_workspace_bytes": (u64, [vp]),
+        "qfx_batch_workspace_bytes": (u64, [C.POINTER(BatchItem), i32, i64]),
+        "qfx_batch_prepare": (st, [C.POINTER(BatchItem), i32, vp, C.c_size_t, C.POINTER(vp), vp]),
+        "qfx_batch_run": (st, [vp, vp]),
+        "qfx_batch_info": (st, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
+        "qfx_batch_destroy": (None, [vp]),
         "qfx_sync": (st, [vp]),
         "qfx_contract_step": (st, [vp, vp, vp, i64, i64, i64, i64, i64, i32, i32, vp, C.c_size_t, vp]),
         "qfx_step_scratch_bytes": (u64, [i64, i64, i32]),
@@ -261,6 +271,47 @@ def amplitudes_backward(plan: Plan, x1, grad_out, *, slice_begin: int = 0,
                                        grad_out.data_ptr(), out.data_ptr(), workspace.data_ptr(),
                                        workspace.numel(), _stream_ptr(stream)))
     return out
+
+
+class Batch:
+    """Many (plan, x1 batch, slice range) items in one persistent launch.
+
+    items: list of (plan, x1 tensor, slice_begin, slice_end); outputs are allocated here
+    (complex128 [n_batch, 2^n_open] each) and refreshed by every run()."""
+
+    def __init__(self, items, *, slots: int = 8, workspace=None, stream=None):
+        import torch
+        self._keep = []
+        arr = (BatchItem * len(items))()
+        self.outs = []
+        for i, (plan, x1, sb, se) in enumerate(items):
+            out = torch.empty((x1.numel(), 1 << len(plan.open_sites)), dtype=torch.complex128,
+                              device=x1.device)
+            self.outs.append(out)
+            self._keep += [plan, x1, out]
+            arr[i] = BatchItem(plan._h.value, x1.data_ptr(), x1.numel(), sb,
+                               plan.n_slices if se is None else se, out.data_ptr())
+        self._arr = arr
+        if workspace is None:
+            nbytes = int(lib.qfx_batch_workspace_bytes(arr, len(items), slots))
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=items[0][1].device)
+        self.workspace = workspace
+        h = C.c_void_p()
+        _check(lib.qfx_batch_prepare(arr, len(items), workspace.data_ptr(), workspace.numel(),
+                                     C.byref(h), _stream_ptr(stream)))
+        self._h = h
+        nw, nt, sl = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib.qfx_batch_info(h, C.byref(nw), C.byref(nt), C.byref(sl)))
+        self.n_work, self.n_tasks, self.slots = nw.value, nt.value, sl.value
+
+    def run(self, stream=None):
+        _check(lib.qfx_batch_run(self._h, _stream_ptr(stream)))
+        return self.outs
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib.qfx_batch_destroy(self._h)
+            self._h = None
 
 
 STATIC_SCRATCH_BYTES = 64 << 20   # QFX_STATIC_SCRATCH_BYTES in include/qfx.h

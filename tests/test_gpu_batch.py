@@ -1,0 +1,100 @@
+"""Batched persistent scheduler (qfx_batch_*): many work items of uneven shapes in one
+launch must reproduce the per-item results exactly (same tile bodies, same FP64 order),
+match the oracle, not depend on the number of slots, and replay from a CUDA graph."""
+import numpy as np
+import pytest
+
+import rqc_inputs as ri
+from oracle import network
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def mixed_items(qfx):
+    specs = [  # (rows, cols, depth, seed, n_open, cuts, n_x1)
+        (4, 4, 16, 0, 5, [], 3),
+        (5, 5, 24, 1, 4, [(6, 7, 4)], 2),
+        (6, 6, 24, 2, 3, [(14, 15, 2)], 2),
+        (3, 5, 16, 3, 6, [], 4),
+        (2, 2, 3, 4, 2, [], 1),
+    ]
+    items, circuits = [], []
+    for rows, cols, d, seed, no, cuts, nx in specs:
+        c = ri.rqc(rows, cols, d, seed=seed)
+        plan = qfx.Plan(qfx.Circuit(c), n_open=no, cuts=cuts)
+        x1 = torch.tensor(ri.random_bitstrings(rows * cols, nx, seed=seed + 50).view(np.int64),
+                          device="cuda")
+        items.append((plan, x1, 0, None))
+        circuits.append(c)
+    return items, circuits
+
+
+def per_item(qfx, items):
+    outs = []
+    for plan, x1, sb, se in items:
+        ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device="cuda")
+        outs.append(qfx.amplitudes(plan, x1, slice_begin=sb,
+                                   slice_end=plan.n_slices if se is None else se,
+                                   workspace=ws).cpu().numpy())
+    qfx.sync()
+    return outs
+
+
+@pytest.mark.parametrize("slots", [1, 3, 16])
+def test_mixed_batch_matches_per_item(qfx, slots):
+    items, circuits = mixed_items(qfx)
+    want = per_item(qfx, items)
+    b = qfx.Batch(items, slots=slots)
+    outs = b.run()
+    qfx.sync()
+    assert b.n_work == sum(x1.numel() * plan.n_slices for plan, x1, _, _ in items)
+    for o, w in zip(outs, want):
+        np.testing.assert_array_equal(o.cpu().numpy(), w)
+    # and one item against the oracle
+    plan, x1, _, _ = items[2]
+    for r, x in enumerate(x1.cpu().numpy().view(np.uint64)):
+        ref = network.amplitudes_open(circuits[2], int(x), plan.open_sites)
+        got = outs[2][r].cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_batch_replays_from_cuda_graph(qfx):
+    items, _ = mixed_items(qfx)
+    want = per_item(qfx, items)
+    b = qfx.Batch(items, slots=4)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(stream=s)            # warm-up outside capture
+    torch.cuda.synchronize()
+    for o in b.outs:
+        o.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(stream=s)
+    for _ in range(2):
+        for o in b.outs:
+            o.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        qfx.sync()
+        for o, w in zip(b.outs, want):
+            np.testing.assert_array_equal(o.cpu().numpy(), w)
+
+
+def test_sampled_paths_of_a_capped_plan(qfx):
+    """Path subsampling (Sec. III.C): a seeded sample of slices of a 7x7x(1+24+1) plan cut
+    down to a 4 MiB per-item cap, each slice a separate batch item."""
+    c = ri.rqc(7, 7, 24, seed=5)
+    plan = qfx.Plan(qfx.Circuit(c), n_open=4, max_intermediate_bytes=4 << 20)
+    assert plan.n_slices >= 64
+    rng = np.random.default_rng(3)
+    sample = sorted(set(int(v) for v in rng.integers(0, plan.n_slices, size=64)))
+    x1 = torch.tensor(ri.random_bitstrings(49, 1, seed=8).view(np.int64), device="cuda")
+    items = [(plan, x1, s, s + 1) for s in sample]
+    want = per_item(qfx, items)
+    b = qfx.Batch(items, slots=8)
+    outs = b.run()
+    qfx.sync()
+    for o, w in zip(outs, want):
+        np.testing.assert_array_equal(o.cpu().numpy(), w)
