@@ -360,6 +360,101 @@ def run_mode(qfx, torch, circ, w, mode, x1_dev, args, dev, stream):
                                  f"{src} bf16 sustained x {TENSOR_PEAK_RATIO[mode]}"}}
 
 
+# ----------------------------------------------------------------------------- batch case
+BATCH_MIX_SMALL = [  # many tiny items: launch overhead dominates per-item execution
+    (4, 4, 16, 1 << 30, 2048, "x1"),
+    (4, 5, 16, 1 << 30, 1024, "x1"),
+    (5, 5, 24, 1 << 30, 1024, "x1"),
+]
+BATCH_MIX = [  # (rows, cols, depth, per-item cap bytes, items, kind)
+    (6, 6, 24, 1 << 30, 256, "x1"),       # bond dim 2^3, whole item per x1
+    (7, 7, 24, 1 << 30, 128, "x1"),       # 2^3
+    (8, 8, 24, 256 << 20, 96, "slice"),   # 2^3, seeded sample of slices (path subsampling)
+    (7, 7, 32, 1 << 30, 32, "slice"),     # 2^4
+]
+
+
+def run_batch(args):
+    """512 work items of uneven shapes from mixed grids, |x2| = 8 (256 amplitudes per
+    item): one persistent launch replayed from a CUDA graph vs one qfx_amplitudes call
+    per item (each its own fold, step and accumulate launches)."""
+    import torch
+    import paper_1905_00444_gb300 as qfx
+    dev = torch.device("cuda", 0)
+    items, flops = [], 0.0
+    rng = np.random.default_rng(7)
+    cache = os.path.join("/tmp", "qfx_autotune_batch.json")
+    mix = BATCH_MIX_SMALL if args.workload == "batch_small" else BATCH_MIX
+    n_open = 4 if args.workload == "batch_small" else 8
+    for (r, c, d, cap, count, kind) in mix:
+        circ = qfx.Circuit(ri.rqc(r, c, d, seed=r * 10 + d))
+        plan = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap)
+        if not args.no_autotune:
+            qfx.autotune(plan, cache)
+            plan = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap, autotune_cache=cache)
+        if kind == "x1":
+            xs = ri.random_bitstrings(r * c, count, seed=r + d)
+            for x in xs:
+                items.append((plan, torch.tensor(np.array([x], dtype=np.uint64).view(np.int64), device=dev), 0, 1))
+        else:
+            x1 = torch.tensor(ri.random_bitstrings(r * c, 1, seed=r + d).view(np.int64), device=dev)
+            for sl in sorted(set(int(v) for v in rng.integers(0, plan.n_slices, size=count))):
+                items.append((plan, x1, sl, sl + 1))
+        flops += plan.stats["flops_per_item"] * count
+    batch = qfx.Batch(items, slots=16)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            batch.run(stream=stream)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        batch.run(stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):      # replay() launches on the current stream
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    qfx.sync()
+    t_graph = e0.elapsed_time(e1) / 1e3 / args.steps
+    ref = [o.clone() for o in batch.outs]
+    # per-item launches on one shared workspace
+    ws = torch.empty(max(p.workspace_bytes(1) for p, _, _, _ in items), dtype=torch.uint8, device=dev)
+    outs = [torch.empty_like(o) for o in ref]
+    for (plan, x1, sb, se), o in zip(items, outs):
+        qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws, out=o)
+    torch.cuda.synchronize(dev)
+    l1 = qfx.launch_count()
+    e0.record()
+    for _ in range(args.steps):
+        for (plan, x1, sb, se), o in zip(items, outs):
+            qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws, out=o)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_items = e0.elapsed_time(e1) / 1e3 / args.steps
+    per_item_launches = (qfx.launch_count() - l1) // args.steps
+    same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    desc = ("batch of 512 work items: 256 x 6x6x(1+24+1), 128 x 7x7x(1+24+1) x1 batches; "
+            "96 sampled slices of 8x8x(1+24+1) (256 MiB cap), 32 of 7x7x(1+32+1) (1 GiB cap); "
+            "|x2| = 8; FP32 SIMT tiles") if args.workload == "batch" else (
+            "batch of 4096 small work items: 2048 x 4x4x(1+16+1), 1024 x 4x5x(1+16+1), "
+            "1024 x 5x5x(1+24+1) x1 batches; |x2| = 4; FP32 SIMT tiles")
+    print(json.dumps({
+        "workload": desc,
+        "metric": "contraction TFLOP/s", "unit": "TFLOP/s",
+        "graph_persistent": {"value": flops / t_graph / 1e12, "ms_per_batch": 1e3 * t_graph,
+                             "items_per_s": len(items) / t_graph, "kernel_launches": 1,
+                             "tasks": batch.n_tasks, "slots": batch.slots},
+        "per_item_launches": {"value": flops / t_items / 1e12, "ms_per_batch": 1e3 * t_items,
+                              "items_per_s": len(items) / t_items, "kernel_launches": per_item_launches},
+        "identical_results": bool(same), "flops_per_batch": flops, "n_items": len(items),
+        "autotuned": not args.no_autotune}), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- kernel case
 def run_kstep(args):
     """The dominant contraction step alone (K = N = 256 as in the 7x7x32 interior steps)
@@ -397,17 +492,21 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="qfx", choices=["qfx", "reference"])
-    ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS) + ["kstep"])
+    ap.add_argument("--workload", default="full",
+                    choices=sorted(WORKLOADS) + ["kstep", "batch", "batch_small"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "bf16x3_fast"],
                     help="kernel case only; the amplitude run reports every mode")
     ap.add_argument("--no-modes", action="store_true", help="skip the split-precision runs")
+    ap.add_argument("--no-autotune", action="store_true", help="batch case: planner's default tiles")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "kstep":
         return run_kstep(args)
+    if args.workload in ("batch", "batch_small"):
+        return run_batch(args)
     return run_qfx(args)
 
 

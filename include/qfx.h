@@ -113,6 +113,7 @@ typedef struct {
   int32_t precision;               /* qfx_precision */
   int32_t plan_family;             /* 0 = line sweep (the only family of this build) */
   int32_t tc_flags;                /* tensor-core options, QFX_TC_* bits; 0 = default */
+  const char* autotune_cache;      /* JSON file written by qfx_autotune, or NULL */
 } qfx_plan_opts;
 
 /* Tensor-core accumulation.  Default: each complex tile is 128 x 128 with four TMEM
@@ -250,6 +251,14 @@ qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t* x1, int64_
                                    double* grad_gates, void* workspace, size_t ws_bytes,
                                    void* stream);
 uint64_t qfx_backward_workspace_bytes(const qfx_plan* p);
+
+/* Autotuner: times every compatible FP32 tile variant of each distinct step shape of `p`
+ * (on `workspace`, shrinking the problem to fit it) and records the fastest per shape
+ * (N, K, NL, Sd) in the JSON file `cache_path` (existing entries are kept and not
+ * re-timed).  Plans created with opts.autotune_cache use the recorded variants.
+ * Synchronises `stream`.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA. */
+qfx_status qfx_autotune(const qfx_plan* p, const char* cache_path, void* workspace,
+                        size_t ws_bytes, void* stream);
 
 /* Waits for `stream` and reports any asynchronous CUDA error as QFX_ECUDA, and a
  * tensor-core kernel that gave up a bounded wait (about 1 s) as QFX_ETIMEOUT. */

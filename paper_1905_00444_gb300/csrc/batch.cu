@@ -113,22 +113,33 @@ __global__ void __launch_bounds__(kT, 1) batch_kernel(const BatchArgs a) {
   __shared__ int s_seg, s_go;
   __shared__ float s_max[kT / 32];
   const int tid = threadIdx.x;
+  // thread 0 keeps the next task index in flight and the last segment it found: task
+  // indices handed to one CTA only grow, so the next segment is found by galloping
+  // forward from the previous one (a few dependent loads instead of a full search).
+  long long next_t = 0;
+  int last = 0;
+  if (tid == 0) next_t = (long long)atomicAdd(a.head, 1ull);
   for (;;) {
     if (tid == 0) {
       s_go = 0;
-      const long long t = (long long)atomicAdd(a.head, 1ull);
+      const long long t = next_t;
       if (t < a.n_tasks && !*(volatile int32_t*)a.abort) {
-        int lo = 0, hi = a.n_segs - 1;
+        next_t = (long long)atomicAdd(a.head, 1ull);
+        int lo = last, step = 1;
+        while (lo + step < a.n_segs && a.segs[lo + step].first_task <= t) { lo += step; step <<= 1; }
+        int hi = min(a.n_segs - 1, lo + step);
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
           if (a.segs[mid].first_task <= t) lo = mid; else hi = mid - 1;
         }
+        last = lo;
         s_task = t;
         s_seg = lo;
         s_go = 1;
         const SegDev sg = a.segs[lo];
         for (int d = 0; d < 2 && s_go; ++d) {
           if (sg.dep[d] < 0) continue;
+          if (ld_acquire(a.done + sg.dep[d]) >= sg.need[d]) continue;
           const unsigned long long deadline = gtimer() + kDepWaitNs;
           while (ld_acquire(a.done + sg.dep[d]) < sg.need[d]) {
             if (*(volatile int32_t*)a.abort) { s_go = 0; break; }
@@ -138,6 +149,7 @@ __global__ void __launch_bounds__(kT, 1) batch_kernel(const BatchArgs a) {
               s_go = 0;
               break;
             }
+            __nanosleep(64);
           }
         }
       }

@@ -147,8 +147,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
   return ok != 0;
 }
-// Bounded wait: false if the deadline passed or another role gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// Bounded wait: false if the deadline passed or another role gave up.  Roles off the
+// critical path pass sleep_ns > 0 so that their polling does not take issue slots from
+// the producers.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          unsigned sleep_ns = 0) {
+  if (mbar_try(bar, parity)) return true;
   const unsigned long long deadline = globaltimer() + kWaitNs;
   while (!mbar_try(bar, parity)) {
     if (*abort) return false;
@@ -157,6 +161,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
       atomicOr(&g_tc_status, 1u);
       return false;
     }
+    if (sleep_ns) __nanosleep(sleep_ns);
   }
   return true;
 }
@@ -289,32 +294,41 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
 
   if (warp < 4) {
     // ---- producers: split 128 rows of B per k-stage into term planes -------------------
-    int64_t q = 0;
-    for (int64_t t = blockIdx.x; t < a.tiles && !*abort; t += gridDim.x) {
-      const int64_t g = t / per_item, jt = (t % per_item) / a.NHt;
+    // The loads of the next (tile, stage) are issued before the current one is split, so
+    // their latency overlaps the split and the wait for a free stage.
+    int64_t t = blockIdx.x, it = 0, q = 0;
+    auto row_ptr = [&](int64_t tt, int64_t& pofs) -> const float2* {
+      const int64_t g = tt / per_item, jt = (tt % per_item) / a.NHt;
       const int64_t jg = jt * kRows + tid;
-      const bool valid = jg < a.J;
-      const float2* Bg = a.B + g * a.b_stride;
-      const int64_t pofs = valid ? (jg / a.Sd) * a.K * a.Sd + (jg % a.Sd) : 0;
-      bool ok = true;
-      for (int64_t it = 0; it < KT; ++it, ++q) {
-        const int s = (int)(q % STAGES);
-        if (q >= STAGES && !mbar_wait(empty(s), (uint32_t)((q / STAGES - 1) & 1), abort)) { ok = false; break; }
-        float re[KS], im[KS];
+      pofs = jg < a.J ? (jg / a.Sd) * a.K * a.Sd + (jg % a.Sd) : -1;
+      return a.B + g * a.b_stride;
+    };
+    float2 nxt[KS];
+    auto fetch = [&](int64_t tt, int64_t ii) {
+      int64_t pofs;
+      const float2* Bg = row_ptr(tt, pofs);
 #pragma unroll
-        for (int kk = 0; kk < KS; ++kk) {
-          float2 v = make_float2(0.f, 0.f);
-          if (valid) v = __ldg(Bg + pofs + (it * KS + kk) * a.Sd);
-          re[kk] = v.x;
-          im[kk] = v.y;
-        }
-        char* st = sA + s * stageA;
-        store_row_terms<MODE>(st, kPlaneA, tid, re);
-        store_row_terms<MODE>(st + TERMS * kPlaneA, kPlaneA, tid, im);
-        fence_async_smem();
-        mbar_arrive(fullA(s));
-      }
-      if (!ok) break;
+      for (int kk = 0; kk < KS; ++kk)
+        nxt[kk] = pofs >= 0 ? __ldg(Bg + pofs + (ii * KS + kk) * a.Sd) : make_float2(0.f, 0.f);
+    };
+    if (t < a.tiles) fetch(t, 0);
+    while (t < a.tiles && !*abort) {
+      float re[KS], im[KS];
+#pragma unroll
+      for (int kk = 0; kk < KS; ++kk) { re[kk] = nxt[kk].x; im[kk] = nxt[kk].y; }
+      int64_t nt = t, ni = it + 1;
+      if (ni == KT) { nt = t + gridDim.x; ni = 0; }
+      if (nt < a.tiles) fetch(nt, ni);
+      const int s = (int)(q % STAGES);
+      if (q >= STAGES && !mbar_wait(empty(s), (uint32_t)((q / STAGES - 1) & 1), abort)) break;
+      char* st = sA + s * stageA;
+      store_row_terms<MODE>(st, kPlaneA, tid, re);
+      store_row_terms<MODE>(st + TERMS * kPlaneA, kPlaneA, tid, im);
+      fence_async_smem();
+      mbar_arrive(fullA(s));
+      ++q;
+      t = nt;
+      it = ni;
     }
   } else if (warp == 13) {
     // ---- S image stream ------------------------------------------------------------
@@ -326,7 +340,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
         const char* img = a.simage + g * a.img_stride;
         for (int64_t it = 0; it < KT; ++it, ++q) {
           const int s = (int)(q % STAGES);
-          if (q >= STAGES && !mbar_wait(empty(s), (uint32_t)((q / STAGES - 1) & 1), abort)) { ok = false; break; }
+          if (q >= STAGES && !mbar_wait(empty(s), (uint32_t)((q / STAGES - 1) & 1), abort, 32)) { ok = false; break; }
           mbar_arrive_tx(fullS(s), (uint32_t)stageS);
           bulk_copy(smem_u32(sS + s * stageS), img + (it * a.NHt + nh) * stageS, (uint32_t)stageS, fullS(s));
           issued = q + 1;
@@ -389,7 +403,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
     const int my_last = ((nchunks - 1 - half) >= 0) ? (nchunks - 1 - ((nchunks - 1 - half) & 1)) : -1;
     int64_t tc = 0;
     for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x, ++tc) {
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)(tc & 1), abort) && !*abort);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)(tc & 1), abort, 256) && !*abort);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int64_t g = t / per_item, jt = (t % per_item) / a.NHt, nh = t % a.NHt;
@@ -439,7 +453,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
     }
   }
 
-  if (warp == 12) mbar_wait(done, 0, abort);   // last MMAs finished before freeing TMEM
+  if (warp == 12) mbar_wait(done, 0, abort, 256);   // last MMAs finished before freeing TMEM
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 12) {

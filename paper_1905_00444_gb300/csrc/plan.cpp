@@ -282,6 +282,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
         simage = std::max(simage, qfx::tc_scratch_bytes(p->precision, st.K, st.N));
       }
     }
+    if (o->autotune_cache) qfx::apply_autotune_cache(p, o->autotune_cache);
     p->max_elements = 1;
     p->flops_per_item = sim.flops;
     p->bytes_per_item = sim.bytes;

@@ -171,6 +171,8 @@ int batch_take_status();  // reads and clears the batch scheduler's timeout flag
 int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
                    const int32_t* perm, void* stream);
 
+void apply_autotune_cache(qfx_plan* p, const char* path);
+
 // device tables of a plan (uploaded once per device)
 qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out);
 void free_tables(DeviceTables& t);

@@ -39,7 +39,8 @@ class PlanOpts(C.Structure):
     _fields_ = [("max_intermediate_bytes", C.c_uint64), ("open_sites", C.POINTER(C.c_int32)),
                 ("n_open", C.c_int32), ("forced_cuts", C.POINTER(Cut)),
                 ("n_forced_cuts", C.c_int32), ("precision", C.c_int32),
-                ("plan_family", C.c_int32), ("tc_flags", C.c_int32)]
+                ("plan_family", C.c_int32), ("tc_flags", C.c_int32),
+                ("autotune_cache", C.c_char_p)]
 
 
 class PlanStats(C.Structure):
@@ -95,6 +96,7 @@ def _declare(lib):
         "qfx_permute": (st, [vp, vp, i32, C.POINTER(i64), C.POINTER(i32), vp]),
         "qfx_profile_enable": (st, [i32]),
         "qfx_profile_collect": (st, [C.POINTER(KernelTime), i32, C.POINTER(i32)]),
+        "qfx_autotune": (st, [vp, C.c_char_p, vp, C.c_size_t, vp]),
         "qfx_launch_count": (u64, []),
         "qfx_last_error": (C.c_char_p, []),
         "qfx_version": (C.c_char_p, []),
@@ -178,7 +180,8 @@ class Plan:
 
     def __init__(self, circuit: Circuit, *, open_sites: Optional[Sequence[int]] = None,
                  n_open: int = 0, max_intermediate_bytes: int = 0,
-                 cuts: Iterable = (), precision: str = "fp32", fast_accumulation: bool = False):
+                 cuts: Iterable = (), precision: str = "fp32", fast_accumulation: bool = False,
+                 autotune_cache: Optional[str] = None):
         opts = PlanOpts()
         opts.max_intermediate_bytes = int(max_intermediate_bytes)
         self._open_arr = None
@@ -194,6 +197,7 @@ class Plan:
         opts.n_forced_cuts = len(cuts)
         opts.precision = PRECISIONS[precision]
         opts.tc_flags = 1 if fast_accumulation else 0
+        opts.autotune_cache = autotune_cache.encode() if autotune_cache else None
         h = C.c_void_p()
         _check(lib.qfx_plan_create(circuit._h, C.byref(opts), C.byref(h)))
         self._h = h
@@ -312,6 +316,16 @@ class Batch:
         if getattr(self, "_h", None):
             lib.qfx_batch_destroy(self._h)
             self._h = None
+
+
+def autotune(plan: Plan, cache_path: str, *, workspace=None, stream=None):
+    """Times the FP32 tile variants of the plan's step shapes; writes/extends the cache."""
+    import torch
+    if workspace is None:
+        workspace = torch.empty(min(plan.workspace_bytes(1), 4 << 30), dtype=torch.uint8,
+                                device="cuda")
+    _check(lib.qfx_autotune(plan._h, cache_path.encode(), workspace.data_ptr(), workspace.numel(),
+                            _stream_ptr(stream)))
 
 
 STATIC_SCRATCH_BYTES = 64 << 20   # QFX_STATIC_SCRATCH_BYTES in include/qfx.h

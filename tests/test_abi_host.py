@@ -177,3 +177,21 @@ def test_tensor_core_plan_variants(prec):
     # the site image region makes the tensor-core item larger than the FP32 one
     p32 = qfx.Plan(qfx.Circuit(c), n_open=6)
     assert p.stats["item_bytes"] > p32.stats["item_bytes"]
+
+
+def test_autotune_cache_is_applied(tmp_path):
+    c = ri.rqc(4, 4, 16, seed=0)
+    base = qfx.Plan(qfx.Circuit(c), n_open=3)
+    s = next(st for st in base.steps[1:] if st["Sd"] % 2 == 0 and st["N"] >= 16)
+    other = 2 if s["variant"] != 2 else 1
+    cache = tmp_path / "tune.json"
+    cache.write_text('{"qfx_autotune": 1, "entries": [\n'
+                     f'  {{"N": {s["N"]}, "K": {s["K"]}, "NL": {s["NL"]}, "Sd": {s["Sd"]}, '
+                     f'"variant": {other}, "ms": 0.5}}\n]}}\n')
+    tuned = qfx.Plan(qfx.Circuit(c), n_open=3, autotune_cache=str(cache))
+    for a, b in zip(base.steps, tuned.steps):
+        same = (a["N"], a["K"], a["NL"], a["Sd"]) == (s["N"], s["K"], s["NL"], s["Sd"])
+        assert b["variant"] == (other if same else a["variant"])
+    # a missing or unreadable cache leaves the defaults
+    p2 = qfx.Plan(qfx.Circuit(c), n_open=3, autotune_cache=str(tmp_path / "missing.json"))
+    assert [st["variant"] for st in p2.steps] == [st["variant"] for st in base.steps]
