@@ -455,6 +455,90 @@ def run_batch(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- adjoint case
+def run_adjoint(args):
+    """6x6x(1+24+1) circuit with parametrised single-qubit gates, 128 bitstrings
+    (|x2| = 7), L = sum |amp|^2: forward amplitudes and the adjoint's gradients for every
+    gate tensor, timed separately with CUDA events."""
+    import torch
+    import paper_1905_00444_gb300 as qfx
+    circ = ri.rqc(6, 6, 24, seed=0, parametrised=True)
+    plan = qfx.Plan(qfx.Circuit(circ), n_open=7)
+    x1 = torch.tensor(ri.random_bitstrings(36, 1, seed=9).view(np.int64), device="cuda")
+    ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device="cuda")
+    bws = torch.empty(int(qfx.lib.qfx_backward_workspace_bytes(plan._h)), dtype=torch.uint8,
+                      device="cuda")
+    out = torch.empty((1, 128), dtype=torch.complex128, device="cuda")
+    for _ in range(args.warmup):
+        amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
+        g = qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f_ms, b_ms = [], []
+    for _ in range(args.steps):
+        ev[0].record()
+        amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
+        ev[1].record()
+        g = qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
+        ev[2].record()
+        torch.cuda.synchronize()
+        f_ms.append(ev[0].elapsed_time(ev[1]))
+        b_ms.append(ev[1].elapsed_time(ev[2]))
+    qfx.sync()
+    flops = plan.stats["flops_per_item"]
+    print(json.dumps({
+        "workload": "adjoint: 6x6x(1+24+1) parametrised RQC, 128 bitstrings (|x2|=7), "
+                    "L = sum |amp|^2, gradients of all %d gate tensors" % len(circ.gates),
+        "forward_ms": float(np.median(f_ms)), "backward_ms": float(np.median(b_ms)),
+        "forward_tflops": flops / (np.median(f_ms) / 1e3) / 1e12,
+        "backward_model_flops": 4 * flops,
+        "backward_tflops": 4 * flops / (np.median(b_ms) / 1e3) / 1e12,
+        "note": "backward work model: forward recomputed twice (checkpoints, then line by line), "
+                "plus a reverse step and a site-gradient GEMM per step, each of the forward "
+                "step's flops", "grad_norm": float(torch.linalg.vector_norm(g).item())}), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- permute case
+PERMUTES = [  # (shape, perm): bond-tensor transposes of the kind region plans need
+    ((16,) * 7, (6, 5, 4, 3, 2, 1, 0)),           # full reversal: tiled transpose path
+    ((256, 256, 256, 16), (0, 2, 1, 3)),          # inner axis kept: row-copy path
+    ((4096, 65536), (1, 0)),                      # matrix transpose
+    ((16, 16, 16, 16, 16, 16, 16), (0, 1, 3, 2, 4, 6, 5)),
+]
+
+
+def run_permute(args):
+    """qfx_permute on 2^28-element complex64 tensors (2 GiB in, 2 GiB out): achieved HBM
+    bandwidth (16 B per element) against the measured copy bandwidth."""
+    import torch
+    import paper_1905_00444_gb300 as qfx
+    peaks, src = measured_peaks()
+    out = []
+    for shape, perm in PERMUTES:
+        n = int(np.prod(shape))
+        x = torch.randn(n, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            qfx.permute(x, shape, perm, out=y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            qfx.permute(x, shape, perm, out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        gbs = 16.0 * n / (ms / 1e3) / 1e9
+        out.append({"shape": list(shape), "perm": list(perm), "ms": ms, "GB/s": gbs,
+                    "frac": gbs / peaks["hbm_gbs"]})
+        del x, y
+    print(json.dumps({"workload": "permute, 2^28 complex64 elements", "roofline": {
+        "bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src},
+        "cases": out}), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- kernel case
 def run_kstep(args):
     """The dominant contraction step alone (K = N = 256 as in the 7x7x32 interior steps)
@@ -493,7 +577,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="qfx", choices=["qfx", "reference"])
     ap.add_argument("--workload", default="full",
-                    choices=sorted(WORKLOADS) + ["kstep", "batch", "batch_small"])
+                    choices=sorted(WORKLOADS) + ["kstep", "batch", "batch_small", "permute", "adjoint"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "bf16x3_fast"],
@@ -507,6 +591,10 @@ def main():
         return run_kstep(args)
     if args.workload in ("batch", "batch_small"):
         return run_batch(args)
+    if args.workload == "permute":
+        return run_permute(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_qfx(args)
 
 

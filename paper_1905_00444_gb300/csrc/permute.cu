@@ -1,8 +1,9 @@
 // Tensor transpose for complex64 tensors of rank <= 10 (the "T" steps of TTGT,
 // Sec. III.E).  Axes that stay adjacent are fused first.  If the innermost output axis
-// is also innermost in the input, rows are copied with 16-byte vectors; otherwise a
-// 32 x 32 tile of (output-innermost axis, input-innermost axis) goes through shared
-// memory so that both the reads and the writes are coalesced.
+// is also innermost in the input, rows are copied with 16-byte vectors, 4096 output
+// elements per block; otherwise a 32 x 32 tile of (output-innermost axis,
+// input-innermost axis) goes through shared memory so that both the reads and the
+// writes are coalesced, each block walking 8 consecutive batch coordinates.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -24,62 +25,95 @@ struct PermArgs {
 };
 
 // ---- case 1: innermost axis shared -> contiguous rows ------------------------
+// Each block copies 4096 consecutive output elements (any number of rows): thread pairs
+// of elements stay in one row when D is even, so they move as 16-byte vectors.
+constexpr int kRowChunk = 4096;
 __global__ void __launch_bounds__(256) permute_rows_kernel(const float2* __restrict__ in,
                                                            float2* __restrict__ out,
-                                                           const PermArgs a, int64_t rows,
-                                                           int64_t chunks) {
-  const int64_t row = blockIdx.x / chunks;
-  const int64_t chunk = blockIdx.x % chunks;
-  if (row >= rows) return;
+                                                           const PermArgs a, int64_t total) {
   const int64_t D = a.dim[a.rank - 1];
-  int64_t r = row, ib = 0, ob = 0;
-  for (int ax = a.rank - 2; ax >= 0; --ax) {
-    const int64_t c = r % a.dim[ax];
-    r /= a.dim[ax];
-    ib += c * a.istr[ax];
-    ob += c * a.ostr[ax];
-  }
-  const int64_t base = chunk * 512;
-  const bool vec = (D % 2 == 0) && (ib % 2 == 0) && (ob % 2 == 0);
-  if (vec) {
-    const int64_t e = base + 2 * threadIdx.x;
-    if (e < D)
-      *reinterpret_cast<float4*>(out + ob + e) = *reinterpret_cast<const float4*>(in + ib + e);
-  } else {
-    for (int64_t e = base + threadIdx.x; e < base + 512 && e < D; e += 256) out[ob + e] = in[ib + e];
+  const int64_t base = (int64_t)blockIdx.x * kRowChunk;
+  const bool even = (D % 2) == 0;
+#pragma unroll 2
+  for (int k = 0; k < kRowChunk / 512; ++k) {
+    const int64_t o = base + k * 512 + 2 * threadIdx.x;
+    if (o >= total) break;
+    int64_t row = o / D;
+    const int64_t col = o - row * D;
+    int64_t ib = 0;
+    for (int ax = a.rank - 2; ax >= 0; --ax) {
+      const int64_t c = row % a.dim[ax];
+      row /= a.dim[ax];
+      ib += c * a.istr[ax];
+    }
+    if (even && (ib % 2) == 0) {
+      *reinterpret_cast<float4*>(out + o) = *reinterpret_cast<const float4*>(in + ib + col);
+    } else {
+      out[o] = in[ib + col];
+      if (o + 1 < total) {
+        if (col + 1 < D) {
+          out[o + 1] = in[ib + col + 1];
+        } else {   // next element starts the next row
+          int64_t r2 = (o + 1) / D, ib2 = 0;
+          for (int ax = a.rank - 2; ax >= 0; --ax) {
+            const int64_t c = r2 % a.dim[ax];
+            r2 /= a.dim[ax];
+            ib2 += c * a.istr[ax];
+          }
+          out[o + 1] = in[ib2];
+        }
+      }
+    }
   }
 }
 
 // ---- case 2: tiled transpose -------------------------------------------------
+// A block handles kTileBatch consecutive batch coordinates of one (a, b) tile position,
+// stepping the batch odometer instead of decomposing every tile's index.
+constexpr int kTileBatch = 8;
 __global__ void __launch_bounds__(256) permute_tile_kernel(const float2* __restrict__ in,
                                                            float2* __restrict__ out,
-                                                           const PermArgs a) {
+                                                           const PermArgs a, int64_t batch) {
   __shared__ float2 tile[32][33];
   const int64_t per = a.tiles_a * a.tiles_b;
-  const int64_t bidx = blockIdx.x / per;
   const int64_t t = blockIdx.x % per;
+  const int64_t b0 = (int64_t)(blockIdx.x / per) * kTileBatch;
   const int64_t ta = t % a.tiles_a, tb = t / a.tiles_a;
-  int64_t r = bidx, ib = 0, ob = 0;
+  // batch coordinates of b0
+  int64_t coord[kMaxRank];
+  int64_t r = b0, ib = 0, ob = 0;
   for (int ax = a.rank - 1; ax >= 0; --ax) {
+    coord[ax] = 0;
     if (ax == a.la || ax == a.lb) continue;
-    const int64_t c = r % a.dim[ax];
+    coord[ax] = r % a.dim[ax];
     r /= a.dim[ax];
-    ib += c * a.istr[ax];
-    ob += c * a.ostr[ax];
+    ib += coord[ax] * a.istr[ax];
+    ob += coord[ax] * a.ostr[ax];
   }
   const int64_t A0 = ta * 32, B0 = tb * 32;
   const int64_t Da = a.dim[a.la], Db = a.dim[a.lb];
   const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
-  // read: consecutive x walk the input-innermost axis lb
-  for (int yy = y; yy < 32; yy += 8) {
-    const int64_t ia = A0 + yy, jb = B0 + x;
-    if (ia < Da && jb < Db) tile[yy][x] = in[ib + ia * a.istr[a.la] + jb];
-  }
-  __syncthreads();
-  // write: consecutive x walk the output-innermost axis la
-  for (int yy = y; yy < 32; yy += 8) {
-    const int64_t jb = B0 + yy, ia = A0 + x;
-    if (ia < Da && jb < Db) out[ob + ia + jb * a.ostr[a.lb]] = tile[x][yy];
+  for (int64_t bi = b0; bi < b0 + kTileBatch && bi < batch; ++bi) {
+    for (int yy = y; yy < 32; yy += 8) {
+      const int64_t ia = A0 + yy, jb = B0 + x;
+      if (ia < Da && jb < Db) tile[yy][x] = in[ib + ia * a.istr[a.la] + jb];
+    }
+    __syncthreads();
+    for (int yy = y; yy < 32; yy += 8) {
+      const int64_t jb = B0 + yy, ia = A0 + x;
+      if (ia < Da && jb < Db) out[ob + ia + jb * a.ostr[a.lb]] = tile[x][yy];
+    }
+    __syncthreads();
+    // odometer: next batch coordinate (innermost batch axis first)
+    for (int ax = a.rank - 1; ax >= 0; --ax) {
+      if (ax == a.la || ax == a.lb) continue;
+      ib += a.istr[ax];
+      ob += a.ostr[ax];
+      if (++coord[ax] < a.dim[ax]) break;
+      ib -= coord[ax] * a.istr[ax];
+      ob -= coord[ax] * a.ostr[ax];
+      coord[ax] = 0;
+    }
   }
 }
 
@@ -117,11 +151,9 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
   const float2* src = (const float2*)in;
   float2* dst = (float2*)out;
   if (a.istr[fr - 1] == 1) {
-    const int64_t D = a.dim[fr - 1];
-    const int64_t rows = total / D;
-    const int64_t chunks = (D + 511) / 512;
-    if (rows * chunks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
-    permute_rows_kernel<<<(unsigned)(rows * chunks), 256, 0, st>>>(src, dst, a, rows, chunks);
+    const int64_t blocks = (total + kRowChunk - 1) / kRowChunk;
+    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
+    permute_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, a, total);
   } else {
     a.la = fr - 1;
     a.lb = -1;
@@ -131,9 +163,9 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
     a.tiles_a = (a.dim[a.la] + 31) / 32;
     a.tiles_b = (a.dim[a.lb] + 31) / 32;
     const int64_t batch = total / (a.dim[a.la] * a.dim[a.lb]);
-    const int64_t blocks = batch * a.tiles_a * a.tiles_b;
+    const int64_t blocks = ((batch + kTileBatch - 1) / kTileBatch) * a.tiles_a * a.tiles_b;
     if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
-    permute_tile_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, a);
+    permute_tile_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, a, batch);
   }
   count_launch();
   return (int)cudaGetLastError();

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/qfx.h"
+#include "qfx.h"
 
 namespace qfx {
 

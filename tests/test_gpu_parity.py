@@ -245,7 +245,10 @@ def test_contract_step_variants(qfx, variant, shape):
                                   ((2, 3, 4, 5, 6), (4, 2, 0, 3, 1)), ((7, 8, 9), (0, 2, 1)),
                                   ((64, 3, 64), (2, 1, 0)), ((5, 1, 7), (1, 2, 0)),
                                   ((2,) * 10, tuple(reversed(range(10)))), ((100,), (0,)),
-                                  ((8, 8, 8), (0, 1, 2))])
+                                  ((8, 8, 8), (0, 1, 2)), ((16,) * 5, (4, 3, 2, 1, 0)),
+                                  ((64, 64, 16), (1, 0, 2)), ((3, 5, 7, 9), (2, 0, 3, 1)),
+                                  ((5, 7, 3), (1, 0, 2)), ((33, 17, 40), (2, 1, 0)),
+                                  ((16, 16, 16, 16, 16), (0, 1, 3, 2, 4))])
 def test_permute_vs_numpy(qfx, case):
     shape, perm = case
     x = ri.random_complex(int(np.prod(shape)), seed=3)
