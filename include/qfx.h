@@ -122,6 +122,10 @@ typedef struct {
  * core's FP32 accumulation loses a little at each addition).  QFX_TC_FAST_ACCUMULATION:
  * 128 x 256 tiles with one accumulator pair (fewer shared-memory reads, larger error). */
 #define QFX_TC_FAST_ACCUMULATION 1
+/* Default tiles stage the FP32 rows of B by tensor-map copies when the shape allows it
+ * (Sd even and Sd a multiple or a divisor of 128, 16-byte aligned buffers).
+ * QFX_TC_REGISTER_ROWS loads them with per-thread loads instead (same arithmetic). */
+#define QFX_TC_REGISTER_ROWS 4
 
 /* Sec. III.D (contraction order and cuts), Sec. III.A (slices), Sec. III.B (x2), Eq. 1.
  * Host only: the plan sweeps the grid line by line (along the shorter grid dimension),
@@ -271,7 +275,9 @@ qfx_status qfx_sync(void* stream);
  * term's k step (16 for BF16x3, 8 for TF32x3) and P*Sd >= 128, otherwise on the FP32
  * path; they need `scratch` of qfx_step_scratch_bytes(K, N, precision) bytes, 256-byte
  * aligned (NULL is fine for FP32).  Variant 12 selects fast accumulation (see
- * QFX_TC_FAST_ACCUMULATION) for a tensor-core step.  Test hook: variant 99 with a tensor-core step
+ * QFX_TC_FAST_ACCUMULATION) for a tensor-core step; variant 13 keeps the default tile but
+ * loads the FP32 rows of B with per-thread loads instead of tensor-map copies (same
+ * arithmetic, for comparison).  Test hook: variant 99 with a tensor-core step
  * withholds the stream of S, so every CTA's bounded waits expire (about 1 s each, run
  * it on at most a few hundred columns); qfx_sync then reports QFX_ETIMEOUT and the
  * context stays usable.  Errors: QFX_EINVAL, QFX_ENOMEM (scratch), QFX_ECUDA. */

@@ -13,20 +13,32 @@
 //   TF32x3: x = b + s, products bb, bs, sb  (error ~2^-21 relative).
 // Accumulation is FP32 in TMEM.
 //
-// Tile: one CTA owns 128 columns j of the step (M = 128, the boundary tensor B is the A
-// operand, rows j) and all N <= 256 rows n (the site matrix S is the B operand), with
-// the real and imaginary accumulators in TMEM columns [0, N) and [256, 256 + N).
-// Roles (192 threads):
-//   warps 0-3  load B (FP32) straight from global, split it into term planes in shared
-//              memory (K-major, no-swizzle core-matrix layout), later run the epilogue;
-//   warp 4     allocates TMEM; lane 0 issues the tcgen05.mma instructions;
-//   warp 5     lane 0 streams the pre-split image of S (written once per step by
-//              split_site_kernel in the same layout) with one bulk copy per stage.
-// A 3-stage ring of shared-memory stages is guarded by mbarriers.  Every wait has a
-// deadline; on expiry the kernel records an error, drains its own copies and MMAs,
-// frees TMEM and returns (the host reports QFX_ETIMEOUT).
+// Tiles: a persistent CTA per SM walks tiles of 128 columns j (M = 128; the boundary
+// tensor B is the A operand, rows j) by Nt rows n of the site matrix S (the B operand).
+// Default tiles are 128 x 128 with split accumulators in TMEM: hi x hi products go to
+// "main" accumulators (re [0,128), im [128,256)), every cross-term product to "small"
+// ones (re [256,384), im [384,512)), added in the epilogue, so the large accumulators
+// see two additions per k-stage.  QFX_TC_FAST_ACCUMULATION tiles are 128 x 256 with one
+// accumulator pair (re [0,256), im [256,512)).
+// Roles (14 warps):
+//   warps 0-3   producers: FP32 rows of B -> term planes in shared memory (K-major,
+//               no-swizzle core-matrix layout).  Default tiles take the rows from
+//               staging buffers filled by tensor-map copies (cp.async.bulk.tensor) when
+//               the shape allows it, otherwise they load them one k-stage ahead;
+//   warps 4-11  epilogue: TMEM -> registers -> C (two warps per TMEM lane quarter);
+//   warp 12     allocates TMEM; lane 0 issues tcgen05.mma;
+//   warp 13     lane 0 streams the pre-split image of S (written once per step by
+//               split_site_kernel in the same layout) with one bulk copy per stage;
+//               lane 1 issues the tensor-map copies of B.
+// Rings of shared-memory stages are guarded by mbarriers.  Every wait has a deadline;
+// on expiry the kernel records an error, drains its own copies and MMAs, frees TMEM and
+// returns (the host reports QFX_ETIMEOUT).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
 
 #include "qfx_internal.h"
 
@@ -222,6 +234,8 @@ struct TcArgs {
   int64_t JT;        // 128-row tiles per item
   int64_t tiles;     // total tiles (items x JT x NHt)
   int withhold_s;    // test hook: never stream S, so the bounded waits expire
+  int use_tma;       // producers read FP32 rows staged by tensor-map copies (default tiles)
+  int box_s, box_p;  // tensor-map box: box_s consecutive s (columns), box_p values of p
 };
 
 // Persistent CTA, one per SM.  TMEM columns: with SPLITACC the hh-term products go to
@@ -230,6 +244,8 @@ struct TcArgs {
 // k-stage instead of 2 x NPROD; without SPLITACC re = [0, Nt), im = [256, 256 + Nt).
 // Warps: 0-3 producers, 4-11 epilogue (two per TMEM lane quarter, each half the columns),
 // 12 TMEM owner + MMA issuer, 13 S stream.
+constexpr uint32_t kAlignPad = 128;
+
 template <int MODE, bool SPLITACC>
 struct TcCfg {
   using M_ = Mode<MODE>;
@@ -238,24 +254,42 @@ struct TcCfg {
   static constexpr int PLANES = 2 * M_::TERMS;
   static constexpr int STAGE_A = PLANES * kPlaneA;
   static constexpr int THREADS = 14 * 32;
+  // FP32 rows of the default tile arrive by tensor-map copies into NBUF staging buffers;
+  // the fast tile's operand ring leaves no room and keeps register prefetch
+  static constexpr int STAGE_IN = kRows * M_::KS * 8;
+  static constexpr int NBUF = SPLITACC ? (M_::KS == 16 ? 2 : 4) : 0;
   static size_t smem(int nt) {
-    return (size_t)STAGES * (STAGE_A + PLANES * nt * 32) + (3 * STAGES + 3) * sizeof(uint64_t);
+    return kAlignPad + (size_t)STAGES * (STAGE_A + PLANES * nt * 32) + (size_t)NBUF * STAGE_IN +
+           (3 * STAGES + 3 + 2 * NBUF) * sizeof(uint64_t);
   }
 };
 
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
 template <int MODE, bool SPLITACC>
-__global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
+    cgemm_tc_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tmA) {
   using M_ = Mode<MODE>;
   using CF = TcCfg<MODE, SPLITACC>;
   constexpr int TERMS = M_::TERMS, KS = M_::KS, STAGES = CF::STAGES;
-  extern __shared__ __align__(16) char smem[];
+  extern __shared__ __align__(16) char smem_raw[];
+  // tensor-map copies land on 128-byte boundaries; the dynamic window itself is only
+  // 16-byte aligned behind the static shared variables
+  char* smem = smem_raw + ((kAlignPad - (smem_u32(smem_raw) & (kAlignPad - 1))) & (kAlignPad - 1));
   const int stageA = CF::STAGE_A;
   const int planeS = a.Nt * 32;
   const int stageS = CF::PLANES * planeS;
   char* sA = smem;
   char* sS = smem + STAGES * stageA;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sS + STAGES * stageS);
-  // bars: fullA[S], fullS[S], empty[S], acc_full, tmem_free, done
+  char* sIn = sS + STAGES * stageS;                 // NBUF x [box_p][KS][box_s] float2
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sIn + CF::NBUF * CF::STAGE_IN);
+  // bars: fullA[S], fullS[S], empty[S], acc_full, tmem_free, done, in_full[NBUF], in_empty[NBUF]
   __shared__ uint32_t tmem_base_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -267,6 +301,8 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
   const uint32_t acc_full = smem_u32(&bars[3 * STAGES]);
   const uint32_t tmem_free = smem_u32(&bars[3 * STAGES + 1]);
   const uint32_t done = smem_u32(&bars[3 * STAGES + 2]);
+  auto in_full = [&](int b) { return smem_u32(&bars[3 * STAGES + 3 + b]); };
+  auto in_empty = [&](int b) { return smem_u32(&bars[3 * STAGES + 3 + CF::NBUF + b]); };
 
   if (tid == 0) {
     abort_flag = 0;
@@ -278,6 +314,10 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
     mbar_init(acc_full, 1);
     mbar_init(tmem_free, 8);
     mbar_init(done, 1);
+    for (int b = 0; b < CF::NBUF; ++b) {
+      mbar_init(in_full(b), 1);
+      mbar_init(in_empty(b), kRows);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 12) {
@@ -294,9 +334,39 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
 
   if (warp < 4) {
     // ---- producers: split 128 rows of B per k-stage into term planes -------------------
-    // The loads of the next (tile, stage) are issued before the current one is split, so
-    // their latency overlaps the split and the wait for a free stage.
+    // Rows arrive either through tensor-map copies staged NBUF k-stages ahead (default
+    // tiles, issued by warp 13) or through loads issued one k-stage ahead into registers,
+    // so their latency overlaps the split and the wait for a free operand stage.
     int64_t t = blockIdx.x, it = 0, q = 0;
+    if (CF::NBUF > 0 && a.use_tma) {
+      const int ps = tid / a.box_s, ss = tid % a.box_s;     // this row inside the box
+      while (t < a.tiles && !*abort) {
+        const int b = (int)(q % (CF::NBUF > 0 ? CF::NBUF : 1));
+        if (!mbar_wait(in_full(b), (uint32_t)((q / (CF::NBUF > 0 ? CF::NBUF : 1)) & 1), abort)) break;
+        const float2* in = reinterpret_cast<const float2*>(sIn + b * CF::STAGE_IN);
+        float re[KS], im[KS];
+#pragma unroll
+        for (int kk = 0; kk < KS; ++kk) {
+          const float2 v = in[(ps * KS + kk) * a.box_s + ss];
+          re[kk] = v.x;
+          im[kk] = v.y;
+        }
+        // the next tensor-map copy rewrites this buffer through the async proxy: order
+        // these generic reads before it (without the fence, fast consumers saw rows of the
+        // following k-stage)
+        fence_async_smem();
+        mbar_arrive(in_empty(b));
+        const int s = (int)(q % STAGES);
+        if (q >= STAGES && !mbar_wait(empty(s), (uint32_t)((q / STAGES - 1) & 1), abort)) break;
+        char* st = sA + s * stageA;
+        store_row_terms<MODE>(st, kPlaneA, tid, re);
+        store_row_terms<MODE>(st + TERMS * kPlaneA, kPlaneA, tid, im);
+        fence_async_smem();
+        mbar_arrive(fullA(s));
+        ++q;
+        if (++it == KT) { it = 0; t += gridDim.x; }
+      }
+    } else {
     auto row_ptr = [&](int64_t tt, int64_t& pofs) -> const float2* {
       const int64_t g = tt / per_item, jt = (tt % per_item) / a.NHt;
       const int64_t jg = jt * kRows + tid;
@@ -330,6 +400,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
       t = nt;
       it = ni;
     }
+    }
   } else if (warp == 13) {
     // ---- S image stream ------------------------------------------------------------
     if (lane == 0) {
@@ -351,6 +422,29 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1) cgemm_tc_ke
         const int s = (int)(i % STAGES);
         const unsigned long long deadline = globaltimer() + kWaitNs;
         while (!mbar_try(fullS(s), (uint32_t)((i / STAGES) & 1)) && globaltimer() < deadline) {
+        }
+      }
+    } else if (lane == 1 && CF::NBUF > 0 && a.use_tma) {
+      // ---- FP32 rows of B: one tensor-map copy per (tile, k-stage) into staging --------
+      constexpr int NB = CF::NBUF > 0 ? CF::NBUF : 1;
+      int64_t q = 0, issued = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
+        const int64_t g = t / per_item, jt = (t % per_item) / a.NHt;
+        const int64_t j0 = jt * kRows;
+        const int c0 = (int)(j0 % a.Sd), c2 = (int)(j0 / a.Sd);
+        for (int64_t it = 0; it < KT; ++it, ++q) {
+          const int b = (int)(q % NB);
+          if (q >= NB && !mbar_wait(in_empty(b), (uint32_t)((q / NB - 1) & 1), abort, 32)) { ok = false; break; }
+          mbar_arrive_tx(in_full(b), (uint32_t)CF::STAGE_IN);
+          tma_load_4d(smem_u32(sIn + b * CF::STAGE_IN), &tmA, c0, (int)(it * KS), c2, (int)g, in_full(b));
+          issued = q + 1;
+        }
+      }
+      for (int64_t i = (issued > NB ? issued - NB : 0); i < issued; ++i) {
+        const int b = (int)(i % NB);
+        const unsigned long long deadline = globaltimer() + kWaitNs;
+        while (!mbar_try(in_full(b), (uint32_t)((i / NB) & 1)) && globaltimer() < deadline) {
         }
       }
     }
@@ -500,10 +594,50 @@ int num_sms() {
   return n[dev] > 0 ? n[dev] : 1;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up at run time (the library links only
+// the static CUDA runtime, so it loads on machines without a driver).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+// Tensor map over B viewed as (s, k, p, item) 8-byte elements, box (box_s, KS, box_p, 1)
+// = one 128-row, KS-deep k-stage of a tile.  False if the shape does not allow it (the
+// box's inner extent must be at least 16 bytes: Sd >= 2; tiles must not straddle p
+// unevenly: Sd a multiple of 128 or a divisor of it).
+bool make_b_map(CUtensorMap* map, const void* B, int64_t b_stride, int batch, int64_t P, int64_t K,
+                int64_t Sd, int ks, int* box_s, int* box_p) {
+  auto enc = tensor_map_encoder();
+  if (!enc || Sd < 2 || (Sd % 128 != 0 && 128 % Sd != 0)) return false;
+  const int bs = (int)(Sd < 128 ? Sd : 128), bp = 128 / bs;
+  const cuuint64_t dims[4] = {(cuuint64_t)Sd, (cuuint64_t)K, (cuuint64_t)P, (cuuint64_t)batch};
+  const cuuint64_t item = (cuuint64_t)(batch > 1 ? b_stride : P * K * Sd) * 8;
+  const cuuint64_t strides[3] = {(cuuint64_t)Sd * 8, (cuuint64_t)(K * Sd) * 8, item};
+  const cuuint32_t box[4] = {(cuuint32_t)bs, (cuuint32_t)ks, (cuuint32_t)bp, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (((uintptr_t)B & 15) || (item & 15)) return false;
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(B), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  *box_s = bs;
+  *box_p = bp;
+  return true;
+}
+
 template <int MODE, bool SPLITACC>
 int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
                    int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
-                   int batch, char* scratch, int64_t scratch_stride, int withhold,
+                   int batch, char* scratch, int64_t scratch_stride, int withhold, bool no_tma,
                    cudaStream_t st) {
   using M_ = Mode<MODE>;
   using CF = TcCfg<MODE, SPLITACC>;
@@ -525,6 +659,11 @@ int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_str
   a.JT = (a.J + kRows - 1) / kRows;
   a.tiles = (int64_t)batch * a.JT * a.NHt;
   a.withhold_s = withhold;
+  alignas(64) CUtensorMap tmA;
+  std::memset(&tmA, 0, sizeof(tmA));
+  a.use_tma = 0;
+  if (CF::NBUF > 0 && !no_tma)
+    a.use_tma = make_b_map(&tmA, B, b_stride, batch, P, K, Sd, M_::KS, &a.box_s, &a.box_p) ? 1 : 0;
   auto kern = cgemm_tc_kernel<MODE, SPLITACC>;
   static int attr_done[64] = {0};
   int dev = 0;
@@ -535,7 +674,7 @@ int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_str
     attr_done[dev] = 1;
   }
   const int64_t grid = a.tiles < num_sms() ? a.tiles : num_sms();
-  kern<<<(unsigned)grid, CF::THREADS, CF::smem(Nt), st>>>(a);
+  kern<<<(unsigned)grid, CF::THREADS, CF::smem(Nt), st>>>(a, tmA);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -563,16 +702,17 @@ int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_str
   cudaStream_t st = (cudaStream_t)stream;
   const bool fast = (flags & kTcFast) != 0;
   const int withhold = (flags & kTcWithhold) ? 1 : 0;
+  const bool no_tma = (flags & kTcNoTma) != 0;
   if (precision == QFX_PREC_C3M_BF16X3)
     return fast ? launch_tc_mode<QFX_PREC_C3M_BF16X3, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                             Sd, batch, scratch, scratch_stride, withhold, st)
+                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, st)
                 : launch_tc_mode<QFX_PREC_C3M_BF16X3, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                            Sd, batch, scratch, scratch_stride, withhold, st);
+                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, st);
   if (precision == QFX_PREC_C3M_TF32X3)
     return fast ? launch_tc_mode<QFX_PREC_C3M_TF32X3, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                             Sd, batch, scratch, scratch_stride, withhold, st)
+                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, st)
                 : launch_tc_mode<QFX_PREC_C3M_TF32X3, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                            Sd, batch, scratch, scratch_stride, withhold, st);
+                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, st);
   return (int)cudaErrorInvalidValue;
 }
 

@@ -140,7 +140,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     p->lines = geo.W;
     p->line_len = geo.L;
     p->precision = o->precision;
-    if (o->tc_flags & ~QFX_TC_FAST_ACCUMULATION) return qfx::fail(QFX_EINVAL, "unknown tc_flags bits");
+    if (o->tc_flags & ~(QFX_TC_FAST_ACCUMULATION | QFX_TC_REGISTER_ROWS)) return qfx::fail(QFX_EINVAL, "unknown tc_flags bits");
     p->tc_flags = o->tc_flags;
     p->transposed = geo.transposed;
     for (int line = 0; line < geo.W; ++line)

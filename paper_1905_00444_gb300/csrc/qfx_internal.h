@@ -159,6 +159,7 @@ int pick_variant(int64_t N, int64_t Sd);
 constexpr int kVariantTcBf16 = 10, kVariantTcTf32 = 11;
 constexpr int kTcFast = 1;       // QFX_TC_FAST_ACCUMULATION
 constexpr int kTcWithhold = 2;   // test hook: S stream withheld
+constexpr int kTcNoTma = 4;      // QFX_TC_REGISTER_ROWS
 bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags);
 uint64_t tc_scratch_bytes(int precision, int64_t K, int64_t N);
 int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,

@@ -279,6 +279,7 @@ extern "C" qfx_status qfx_contract_step(const void* S, const void* B, void* C, i
   int flags = 0;
   if (variant == 99 && tc) { flags = kTcWithhold; variant = -1; }
   if (variant == 12 && tc) { flags = kTcFast; variant = -1; }
+  if (variant == 13 && tc) { flags = kTcNoTma; variant = -1; }
   if (variant >= 10) return fail(QFX_EINVAL, "qfx_contract_step: unknown variant");
   if (variant >= 0 && variant < 5 && Sd % 2)
     return fail(QFX_EINVAL, "qfx_contract_step: variants 0-4 need an even Sd");

@@ -181,7 +181,7 @@ class Plan:
     def __init__(self, circuit: Circuit, *, open_sites: Optional[Sequence[int]] = None,
                  n_open: int = 0, max_intermediate_bytes: int = 0,
                  cuts: Iterable = (), precision: str = "fp32", fast_accumulation: bool = False,
-                 autotune_cache: Optional[str] = None):
+                 autotune_cache: Optional[str] = None, tensor_maps: bool = True):
         opts = PlanOpts()
         opts.max_intermediate_bytes = int(max_intermediate_bytes)
         self._open_arr = None
@@ -196,7 +196,7 @@ class Plan:
         opts.forced_cuts = C.cast(self._cut_arr, C.POINTER(Cut))
         opts.n_forced_cuts = len(cuts)
         opts.precision = PRECISIONS[precision]
-        opts.tc_flags = 1 if fast_accumulation else 0
+        opts.tc_flags = (1 if fast_accumulation else 0) | (0 if tensor_maps else 4)
         opts.autotune_cache = autotune_cache.encode() if autotune_cache else None
         h = C.c_void_p()
         _check(lib.qfx_plan_create(circuit._h, C.byref(opts), C.byref(h)))

@@ -35,7 +35,8 @@ def step_ref(S, B, P, K, N, NL, Sd):
 @pytest.mark.parametrize("shape", [(1, 256, 256, 256, 1024), (16, 256, 256, 256, 16),
                                    (3, 64, 64, 32, 64), (2000, 16, 16, 16, 1),
                                    (1, 32, 48, 48, 300), (5, 256, 32, 16, 40),
-                                   (2, 48, 112, 112, 200), (1, 16, 240, 48, 136)])
+                                   (2, 48, 112, 112, 200), (1, 16, 240, 48, 136),
+                                   (77, 32, 32, 32, 2), (3, 48, 64, 64, 128)])
 def test_step_vs_oracle(qfx, prec, shape, fast):
     P, K, N, NL, Sd = shape
     S = ri.random_complex((K, N), seed=3)
@@ -61,6 +62,46 @@ def test_step_matches_fp32_path(qfx, prec):
     qfx.sync()
     rel = (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
     assert rel < STEP_BOUND[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("shape", [(1, 64, 64, 64, 4096), (8, 64, 64, 64, 512), (64, 64, 64, 64, 64),
+                                   (512, 64, 64, 64, 8), (4, 64, 16, 8, 512), (16, 64, 16, 8, 8),
+                                   (77, 32, 32, 32, 2), (3, 48, 64, 64, 128), (9, 32, 256, 64, 16),
+                                   (4096, 64, 64, 64, 8)])
+def test_tensor_map_rows_match_register_rows(qfx, prec, shape):
+    """The default tile stages the FP32 rows of B by tensor-map copies (variant -1) or by
+    per-thread loads (variant 13): the same values reach the same MMAs, so the results
+    agree bit for bit, including ragged p tails the copies fill with zeros.  Repeated:
+    CTAs that run several tiles reuse each staging buffer many times, and a missing
+    proxy fence between the producers' reads and the next copy showed up only in some
+    launches."""
+    P, K, N, NL, Sd = shape
+    S = torch.from_numpy(ri.random_complex((K * N,), seed=11)).cuda()
+    B = torch.from_numpy(ri.random_complex((P * K * Sd,), seed=12)).cuda()
+    b = qfx.contract_step(S, B, P, K, N, NL, Sd, precision=prec, variant=13)
+    for _ in range(6):
+        a = qfx.contract_step(S, B, P, K, N, NL, Sd, precision=prec)
+        qfx.sync()
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(1, 8, 64, 64, 4096), (2, 8, 16, 8, 4096), (512, 8, 64, 64, 1),
+                                   (40, 8, 32, 32, 4)])
+def test_tf32_single_kstage_steps(qfx, shape):
+    """K = 8 is one TF32 k-stage per tile (each tile's only stage is also its last)."""
+    P, K, N, NL, Sd = shape
+    S = ri.random_complex((K, N), seed=13)
+    B = ri.random_complex((P, K, Sd), seed=14)
+    want = step_ref(S, B, P, K, N, NL, Sd)
+    for v in (-1, 13):
+        out = qfx.contract_step(torch.from_numpy(S.reshape(-1)).cuda(),
+                                torch.from_numpy(B.reshape(-1)).cuda(), P, K, N, NL, Sd,
+                                precision="tf32x3", variant=v)
+        qfx.sync()
+        got = out.cpu().numpy().reshape(want.shape)
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert rel < STEP_BOUND["tf32x3"], (v, rel)
 
 
 def run(qfx, circ, x1s, prec, n_open, ws_items=1, fast=False):
