@@ -536,11 +536,16 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
           if (lane == 0) mbar_arrive(tmem_free);
         }
         if (valid) {
+          // one division per chunk, then step along n with a carry into nh (a 64-bit
+          // division per element cost more than the MMAs of the tile)
+          const int n0 = (int)nh * a.Nt + c0, NL = (int)a.NL;
+          int nl = n0 % NL;
+          float2* dst = Cg + (int64_t)(n0 / NL) * strideNH + (int64_t)nl * a.Sd + jofs;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int64_t n = nh * a.Nt + c0 + i;
-            const int64_t nhh = n / a.NL, nl = n % a.NL;
-            Cg[nhh * strideNH + nl * a.Sd + jofs] = make_float2(vr[i], vi[i]);
+            *dst = make_float2(vr[i], vi[i]);
+            dst += a.Sd;
+            if (++nl == NL) { nl = 0; dst += strideNH - (int64_t)NL * a.Sd; }
           }
         }
       }

@@ -163,17 +163,22 @@ __device__ __forceinline__ void cgemm_tile(const StepArgs& a, int64_t tile, int6
   // epilogue: C[nh][p][nl][s]
   const int64_t NL = a.NL;
   const int64_t strideNH = a.P * NL * Sd;
+  // (nh, nl) of this thread's first row once; the rows below step with a carry (a 64-bit
+  // division per element is a large share of the epilogue)
+  const int nfirst = (int)(n0 + ty * TM), NLi = (int)NL;
+  const int nh_first = nfirst / NLi, nl_first = nfirst % NLi;
 #pragma unroll
   for (int c = 0; c < TJ / 2; ++c) {
     const int64_t j = j0 + c * 2 * TXN + tx * 2;
     if (j >= J) continue;
     const int64_t p = j / Sd, s = j % Sd;
     const int64_t p1 = (j + 1) / Sd, s1 = (j + 1) % Sd;
+    int nh = nh_first, nl = nl_first;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      const int64_t n = n0 + ty * TM + i;
+      const int64_t n = nfirst + i;
       if (n >= N) break;
-      const int64_t nh = n / NL, nl = n % NL;
+      if (i > 0 && ++nl == NLi) { nl = 0; ++nh; }
       const float2 v0 = make_float2(accr[i][2 * c], acci[i][2 * c]);
       const float2 v1 = make_float2(accr[i][2 * c + 1], acci[i][2 * c + 1]);
       float2* dst0 = C + nh * strideNH + p * (NL * Sd) + nl * Sd + s;
