@@ -18,8 +18,11 @@
 // Default tiles are 128 x 128 with split accumulators in TMEM: hi x hi products go to
 // "main" accumulators (re [0,128), im [128,256)), every cross-term product to "small"
 // ones (re [256,384), im [384,512)), added in the epilogue, so the large accumulators
-// see two additions per k-stage.  QFX_TC_FAST_ACCUMULATION tiles are 128 x 256 with one
-// accumulator pair (re [0,256), im [256,512)).
+// see two additions per k-stage.  There the complex product is embedded in N: S is held
+// per term as planes Sr, Si, -Sr, and one MMA of N = 256 takes Ar x [Sr; Si] into
+// (re, im) and another -Ai x [Si; -Sr], so each MMA reads A once for both halves.
+// QFX_TC_FAST_ACCUMULATION tiles are 128 x 256 with one accumulator pair
+// (re [0,256), im [256,512)) and four real products per term pair (4M).
 // Roles (14 warps):
 //   warps 0-3   producers: FP32 rows of B -> term planes in shared memory (K-major,
 //               no-swizzle core-matrix layout).  Default tiles take the rows from
@@ -239,19 +242,21 @@ struct TcArgs {
 };
 
 // Persistent CTA, one per SM.  TMEM columns: with SPLITACC the hh-term products go to
-// "main" accumulators (re [0,128), im [128,256)) and every cross-term product to "small"
-// ones (re [256,384), im [384,512)), so the large accumulator sees 2 additions per
-// k-stage instead of 2 x NPROD; without SPLITACC re = [0, Nt), im = [256, 256 + Nt).
+// "main" accumulators (re [0,Nt), im [Nt,2Nt)) and every cross-term product to "small"
+// ones (re [256,256+Nt), im [256+Nt,256+2Nt)), so the large accumulator sees 2 additions
+// per k-stage instead of 2 x NPROD; without SPLITACC re = [0, Nt), im = [256, 256 + Nt).
 // Warps: 0-3 producers, 4-11 epilogue (two per TMEM lane quarter, each half the columns),
-// 12 TMEM owner + MMA issuer, 13 S stream.
+// 12 TMEM owner + MMA issuer, 13 S stream and tensor-map copies.
 constexpr uint32_t kAlignPad = 128;
 
 template <int MODE, bool SPLITACC>
 struct TcCfg {
   using M_ = Mode<MODE>;
   static constexpr int NT_MAX = SPLITACC ? 128 : 256;
-  static constexpr int STAGES = SPLITACC ? 4 : 3;
-  static constexpr int PLANES = 2 * M_::TERMS;
+  // default tiles hold S as [Sr; Si; -Sr] per term (the complex product embedded in N)
+  static constexpr int PLANES = 2 * M_::TERMS;             // A planes per stage
+  static constexpr int SPLANES = SPLITACC ? 3 * M_::TERMS : PLANES;   // S planes per stage
+  static constexpr int STAGES = SPLITACC ? (M_::TERMS == 3 ? 3 : 4) : 3;
   static constexpr int STAGE_A = PLANES * kPlaneA;
   static constexpr int THREADS = 14 * 32;
   // FP32 rows of the default tile arrive by tensor-map copies into NBUF staging buffers;
@@ -259,7 +264,7 @@ struct TcCfg {
   static constexpr int STAGE_IN = kRows * M_::KS * 8;
   static constexpr int NBUF = SPLITACC ? (M_::KS == 16 ? 2 : 4) : 0;
   static size_t smem(int nt) {
-    return kAlignPad + (size_t)STAGES * (STAGE_A + PLANES * nt * 32) + (size_t)NBUF * STAGE_IN +
+    return kAlignPad + (size_t)STAGES * (STAGE_A + SPLANES * nt * 32) + (size_t)NBUF * STAGE_IN +
            (3 * STAGES + 3 + 2 * NBUF) * sizeof(uint64_t);
   }
 };
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
   char* smem = smem_raw + ((kAlignPad - (smem_u32(smem_raw) & (kAlignPad - 1))) & (kAlignPad - 1));
   const int stageA = CF::STAGE_A;
   const int planeS = a.Nt * 32;
-  const int stageS = CF::PLANES * planeS;
+  const int stageS = CF::SPLANES * planeS;
   char* sA = smem;
   char* sS = smem + STAGES * stageA;
   char* sIn = sS + STAGES * stageS;                 // NBUF x [box_p][KS][box_s] float2
@@ -453,32 +458,48 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
     if (lane == 0) {
       int64_t q = 0, tc = 0;
       bool ok = true;
-      const uint32_t idesc_p = instr_desc<MODE>(a.Nt, false), idesc_n = instr_desc<MODE>(a.Nt, true);
+      // default tiles: one MMA covers re and im (N = 2 Nt); fast tiles: N = Nt
+      const int n_mma = SPLITACC ? 2 * a.Nt : a.Nt;
+      const uint32_t idesc_p = instr_desc<MODE>(n_mma, false), idesc_n = instr_desc<MODE>(n_mma, true);
       for (int64_t t = blockIdx.x; t < a.tiles && ok; t += gridDim.x, ++tc) {
         if (tc > 0 && !mbar_wait(tmem_free, (uint32_t)((tc - 1) & 1), abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        bool started[4] = {false, false, false, false};
+        bool started[2] = {false, false};
         for (int64_t it = 0; it < KT; ++it, ++q) {
           const int s = (int)(q % STAGES);
           const uint32_t par = (uint32_t)((q / STAGES) & 1);
           if (!mbar_wait(fullA(s), par, abort) || !mbar_wait(fullS(s), par, abort)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_u32(sA + s * stageA), b0 = smem_u32(sS + s * stageS);
+          if constexpr (SPLITACC) {
+            // Ar x [Sr; Si] -> (re, im) += (Ar Sr, Ar Si);  (-Ai) x [Si; -Sr] -> += (-Ai Si, Ai Sr)
 #pragma unroll
-          for (int rp = 0; rp < 4; ++rp) {
-            const int ca = (rp == 0 || rp == 2) ? 0 : 1;          // Ar, Ai, Ar, Ai
-            const int cb = (rp == 0 || rp == 3) ? 0 : 1;          // Sr, Si, Si, Sr
-            const int to_im = rp >= 2 ? 1 : 0;
-            const uint32_t idesc = rp == 1 ? idesc_n : idesc_p;   // - Ai Si
+            for (int ca = 0; ca < 2; ++ca) {
 #pragma unroll
-            for (int pi = 0; pi < M_::NPROD; ++pi) {
-              const bool main_term = M_::ta(pi) == 0 && M_::tb(pi) == 0;
-              const int acc = (SPLITACC && !main_term) ? 2 + to_im : to_im;
-              const uint32_t d = SPLITACC ? tmem + (uint32_t)(acc * 128) : tmem + (uint32_t)(to_im * 256);
-              const uint64_t ad = smem_desc(a0 + (ca * TERMS + M_::ta(pi)) * kPlaneA);
-              const uint64_t bd = smem_desc(b0 + (cb * TERMS + M_::tb(pi)) * planeS);
-              mma<MODE>(d, ad, bd, idesc, started[acc] ? 1u : 0u);
-              started[acc] = true;
+              for (int pi = 0; pi < M_::NPROD; ++pi) {
+                const bool main_term = M_::ta(pi) == 0 && M_::tb(pi) == 0;
+                const int acc = main_term ? 0 : 1;
+                const uint64_t ad = smem_desc(a0 + (ca * TERMS + M_::ta(pi)) * kPlaneA);
+                const uint64_t bd = smem_desc(b0 + (3 * M_::tb(pi) + ca) * planeS);
+                mma<MODE>(tmem + (uint32_t)(acc * 256), ad, bd, ca ? idesc_n : idesc_p, started[acc] ? 1u : 0u);
+                started[acc] = true;
+              }
+            }
+          } else {
+            // 4M with re in TMEM columns [0, Nt) and im in [256, 256 + Nt)
+#pragma unroll
+            for (int rp = 0; rp < 4; ++rp) {
+              const int ca = (rp == 0 || rp == 2) ? 0 : 1;          // Ar, Ai, Ar, Ai
+              const int cb = (rp == 0 || rp == 3) ? 0 : 1;          // Sr, Si, Si, Sr
+              const int to_im = rp >= 2 ? 1 : 0;
+              const uint32_t idesc = rp == 1 ? idesc_n : idesc_p;   // - Ai Si
+#pragma unroll
+              for (int pi = 0; pi < M_::NPROD; ++pi) {
+                const uint64_t ad = smem_desc(a0 + (ca * TERMS + M_::ta(pi)) * kPlaneA);
+                const uint64_t bd = smem_desc(b0 + (cb * TERMS + M_::tb(pi)) * planeS);
+                mma<MODE>(tmem + (uint32_t)(to_im * 256), ad, bd, idesc, started[to_im] ? 1u : 0u);
+                started[to_im] = true;
+              }
             }
           }
           mma_commit(empty(s));
@@ -516,11 +537,12 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
         const int c0 = ci * 16;
         float vr[16], vi[16];
         if (SPLITACC) {
+          // main (re, im) in columns [0, Nt), [Nt, 2 Nt); small ones 256 further
           float sr[16], si[16];
           tmem_ld16(tmem + lane_base + c0, vr);
-          tmem_ld16(tmem + lane_base + 128 + c0, vi);
+          tmem_ld16(tmem + lane_base + a.Nt + c0, vi);
           tmem_ld16(tmem + lane_base + 256 + c0, sr);
-          tmem_ld16(tmem + lane_base + 384 + c0, si);
+          tmem_ld16(tmem + lane_base + 256 + a.Nt + c0, si);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int i = 0; i < 16; ++i) { vr[i] += sr[i]; vi[i] += si[i]; }
@@ -561,9 +583,12 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
   }
 }
 
-// Pre-split of the site matrix S[k][n] into the per-stage shared-memory image:
-// [stage ks][n tile][component][term][row n within the tile][32 bytes].
-template <int MODE>
+// Pre-split of the site matrix S[k][n] into the per-stage shared-memory image, per
+// (stage ks, n tile), each plane [row n within the tile][32 bytes]:
+//   EMB (default tiles): per term t the planes Sr_t, Si_t, -Sr_t, so that [Sr_t; Si_t]
+//     and [Si_t; -Sr_t] are contiguous 2 Nt-row operands (complex product embedded in N);
+//   otherwise: Sr terms then Si terms.
+template <int MODE, bool EMB>
 __global__ void __launch_bounds__(128) split_site_kernel(const float2* __restrict__ S, int64_t s_stride,
                                                           int K, int N, int Nt, char* image,
                                                           int64_t img_stride) {
@@ -585,9 +610,18 @@ __global__ void __launch_bounds__(128) split_site_kernel(const float2* __restric
   }
   const int planeS = Nt * 32;
   const int nht = N / Nt, nh = n / Nt, r = n % Nt;
-  char* st = image + (int64_t)g * img_stride + ((int64_t)ks * nht + nh) * 2 * TERMS * planeS;
-  store_row_terms<MODE>(st, planeS, r, re);
-  store_row_terms<MODE>(st + TERMS * planeS, planeS, r, im);
+  constexpr int SPL = EMB ? 3 * TERMS : 2 * TERMS;
+  char* st = image + (int64_t)g * img_stride + ((int64_t)ks * nht + nh) * SPL * planeS;
+  if constexpr (EMB) {
+    store_row_terms<MODE>(st, 3 * planeS, r, re);
+    store_row_terms<MODE>(st + planeS, 3 * planeS, r, im);
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) re[kk] = -re[kk];
+    store_row_terms<MODE>(st + 2 * planeS, 3 * planeS, r, re);
+  } else {
+    store_row_terms<MODE>(st, planeS, r, re);
+    store_row_terms<MODE>(st + TERMS * planeS, planeS, r, im);
+  }
 }
 
 int num_sms() {
@@ -649,7 +683,7 @@ int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_str
   const int Nt = (int)(N < CF::NT_MAX ? N : CF::NT_MAX);   // N % 16 == 0, N <= 256
   const int KT = (int)(K / M_::KS);
   dim3 sg((unsigned)((N + 127) / 128), KT, batch);
-  split_site_kernel<MODE><<<sg, 128, 0, st>>>((const float2*)S, s_stride, (int)K, (int)N, Nt,
+  split_site_kernel<MODE, SPLITACC><<<sg, 128, 0, st>>>((const float2*)S, s_stride, (int)K, (int)N, Nt,
                                               scratch, scratch_stride);
   count_launch();
   cudaError_t e = cudaGetLastError();
@@ -695,8 +729,9 @@ bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags) {
 }
 
 uint64_t tc_scratch_bytes(int precision, int64_t K, int64_t N) {
-  if (precision == QFX_PREC_C3M_BF16X3) return (uint64_t)(K / 16) * 6 * (uint64_t)N * 32;
-  if (precision == QFX_PREC_C3M_TF32X3) return (uint64_t)(K / 8) * 4 * (uint64_t)N * 32;
+  // per k-stage and column n: 3 planes per term (the embedded layout of default tiles)
+  if (precision == QFX_PREC_C3M_BF16X3) return (uint64_t)(K / 16) * 9 * (uint64_t)N * 32;
+  if (precision == QFX_PREC_C3M_TF32X3) return (uint64_t)(K / 8) * 6 * (uint64_t)N * 32;
   return 0;
 }
 

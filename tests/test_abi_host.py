@@ -160,8 +160,8 @@ def test_permute_and_step_argument_checks():
     # tensor-core precision without scratch
     assert q.lib.qfx_contract_step(fake, fake, fake, 1, 256, 256, 256, 256, 1, -1, None, 0,
                                    None) == q.QFX_ENOMEM
-    assert q.lib.qfx_step_scratch_bytes(256, 256, 1) == 16 * 6 * 256 * 32
-    assert q.lib.qfx_step_scratch_bytes(256, 256, 2) == 32 * 4 * 256 * 32
+    assert q.lib.qfx_step_scratch_bytes(256, 256, 1) == 16 * 9 * 256 * 32
+    assert q.lib.qfx_step_scratch_bytes(256, 256, 2) == 32 * 6 * 256 * 32
     assert q.lib.qfx_step_scratch_bytes(256, 256, 0) == 0
 
 
