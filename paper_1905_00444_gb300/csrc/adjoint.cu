@@ -75,6 +75,14 @@ __global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S,
   const int64_t k0 = kt * BM, j0 = jt * BJ;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int64_t strideNH = P * NL * Sd;
+  // every element this thread loads has column c = threadIdx.x % BM (kT is a multiple of
+  // BM): the j part of the address is computed once, the n part with 32-bit divisions
+  static_assert(kT % BM == 0, "column per thread");
+  const int c = threadIdx.x % BM, r0 = threadIdx.x / BM;
+  const int64_t jc = j0 + c;
+  const bool jok = jc < J;
+  const int64_t joff = jok ? (jc / Sd) * NL * Sd + jc % Sd : 0;
+  const int NLi = (int)NL;
   float2 acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -83,15 +91,16 @@ __global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S,
   for (int64_t n0 = 0; n0 < N; n0 += BR) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int e = threadIdx.x + i * kT;
-      const int r = e / BM, c = e % BM;
+      const int r = r0 + i * (kT / BM);
       const int64_t k = k0 + c, n = n0 + r;
       float2 v = make_float2(0.f, 0.f);
       if (k < K && n < N) { v = S[k * N + n]; v.y = -v.y; }
       As[r][c] = v;
-      const int64_t j = j0 + c;
       float2 b = make_float2(0.f, 0.f);
-      if (j < J && n < N) b = Rin[(n / NL) * strideNH + (j / Sd) * NL * Sd + (n % NL) * Sd + j % Sd];
+      if (jok && n < N) {
+        const int ni = (int)n;
+        b = Rin[(int64_t)(ni / NLi) * strideNH + (int64_t)(ni % NLi) * Sd + joff];
+      }
       Bs[r][c] = b;
     }
     __syncthreads();
@@ -111,12 +120,16 @@ __global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S,
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int j = 0; j < 4; ++j) {
+    const int64_t jj = j0 + tx * 4 + j;
+    if (jj >= J) continue;
+    const int64_t jp = jj / Sd, js = jj - jp * Sd;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t k = k0 + ty * 4 + i, jj = j0 + tx * 4 + j;
-      if (k < K && jj < J) Rout[(jj / Sd) * K * Sd + k * Sd + jj % Sd] = acc[i][j];
+    for (int i = 0; i < 4; ++i) {
+      const int64_t k = k0 + ty * 4 + i;
+      if (k < K) Rout[jp * K * Sd + k * Sd + js] = acc[i][j];
     }
+  }
 }
 
 // ---- site gradient, split over columns: part[c][k][n] = sum_{j in c} conj(L(k,j)) R(n,j) ----
@@ -136,16 +149,29 @@ __global__ void __launch_bounds__(kT) grads_kernel(const float2* __restrict__ Li
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  // every element this thread loads has column jj = threadIdx.x % BJ and rows
+  // c = threadIdx.x / BJ + i kT / BJ: the k and n parts of the addresses are fixed, the j
+  // part takes one division per step
+  static_assert(kT % BJ == 0, "column per thread");
+  const int jj = threadIdx.x % BJ, c0 = threadIdx.x / BJ;
+  int64_t koff[4], noff[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int c = c0 + i * (kT / BJ);
+    const int64_t k = k0 + c, n = n0 + c;
+    koff[i] = k < K ? k * Sd : -1;
+    noff[i] = n < N ? (n / NL) * strideNH + (n % NL) * Sd : -1;
+  }
   for (int64_t j0 = jb; j0 < je; j0 += BJ) {
+    const int64_t j = j0 + jj;
+    const bool jok = j < je;
+    const int64_t jp = jok ? j / Sd : 0, js = jok ? j - jp * Sd : 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int e = threadIdx.x + i * kT;
-      const int jj = e % BJ, c = e / BJ;
-      const int64_t j = j0 + jj;
-      const int64_t k = k0 + c, n = n0 + c;
+      const int c = c0 + i * (kT / BJ);
       float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-      if (j < je && k < K) { a = Lin[(j / Sd) * K * Sd + k * Sd + j % Sd]; a.y = -a.y; }
-      if (j < je && n < N) b = Rin[(n / NL) * strideNH + (j / Sd) * NL * Sd + (n % NL) * Sd + j % Sd];
+      if (jok && koff[i] >= 0) { a = Lin[jp * K * Sd + koff[i] + js]; a.y = -a.y; }
+      if (jok && noff[i] >= 0) b = Rin[jp * NL * Sd + noff[i] + js];
       As[jj][c] = a;
       Bs[jj][c] = b;
     }
