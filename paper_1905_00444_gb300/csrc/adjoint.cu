@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kMaxEvents = 64;     // events per site the fold adjoint supports
-constexpr int64_t kJChunk = 4096;  // columns per partial in the site-gradient GEMM
+constexpr int64_t kGradsBlocks = 608;   // site-gradient grid target: 4 blocks per SM of 152
 
 uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
@@ -64,10 +64,13 @@ __global__ void __launch_bounds__(kT) seed_kernel(const double* __restrict__ gou
 }
 
 // ---- reverse step: Rout[p][k][s] = sum_n conj(S[k][n]) Rin[n/NL][p][n%NL][s] ------------
+// BM (16 or 64) rows k by 64 columns j per block; thread (ty, tx) owns BM/16 x 4 outputs.
+template <int BM>
 __global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S, const float2* __restrict__ Rin,
                                                    float2* __restrict__ Rout, int64_t P, int64_t K,
                                                    int64_t N, int64_t NL, int64_t Sd) {
-  constexpr int BM = 64, BJ = 64, BR = 16;
+  constexpr int BJ = 64, BR = 16, TMK = BM / 16;
+  static_assert(kT == 256 && (BM == 16 || BM == 64), "thread layout");
   __shared__ float2 As[BR][BM + 1];
   __shared__ float2 Bs[BR][BJ + 1];
   const int64_t J = P * Sd, KT_ = (K + BM - 1) / BM;
@@ -75,27 +78,32 @@ __global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S,
   const int64_t k0 = kt * BM, j0 = jt * BJ;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int64_t strideNH = P * NL * Sd;
-  // every element this thread loads has column c = threadIdx.x % BM (kT is a multiple of
-  // BM): the j part of the address is computed once, the n part with 32-bit divisions
-  static_assert(kT % BM == 0, "column per thread");
-  const int c = threadIdx.x % BM, r0 = threadIdx.x / BM;
+  // B elements of this thread: column c = threadIdx.x % BJ, rows r0 + 4 i; the j part of
+  // the address is computed once, the n part with 32-bit divisions
+  const int c = threadIdx.x % BJ, r0 = threadIdx.x / BJ;
   const int64_t jc = j0 + c;
   const bool jok = jc < J;
   const int64_t joff = jok ? (jc / Sd) * NL * Sd + jc % Sd : 0;
   const int NLi = (int)NL;
-  float2 acc[4][4];
+  float2 acc[TMK][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TMK; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
   for (int64_t n0 = 0; n0 < N; n0 += BR) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = r0 + i * (kT / BM);
-      const int64_t k = k0 + c, n = n0 + r;
+    for (int i = 0; i < TMK; ++i) {   // A: BR x BM elements, BM / 16 per thread
+      const int e = threadIdx.x + i * kT;
+      const int ra = e / BM, ca = e % BM;
+      const int64_t k = k0 + ca, n = n0 + ra;
       float2 v = make_float2(0.f, 0.f);
       if (k < K && n < N) { v = S[k * N + n]; v.y = -v.y; }
-      As[r][c] = v;
+      As[ra][ca] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {     // B: BR x BJ elements, 4 per thread
+      const int r = r0 + i * (kT / BJ);
+      const int64_t n = n0 + r;
       float2 b = make_float2(0.f, 0.f);
       if (jok && n < N) {
         const int ni = (int)n;
@@ -106,11 +114,13 @@ __global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S,
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < BR; ++r) {
-      float2 a[4], b[4];
+      float2 a[TMK], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { a[i] = As[r][ty * 4 + i]; b[i] = Bs[r][tx * 4 + i]; }
+      for (int i = 0; i < TMK; ++i) a[i] = As[r][ty * TMK + i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) b[j] = Bs[r][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < TMK; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
@@ -125,41 +135,61 @@ __global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S,
     if (jj >= J) continue;
     const int64_t jp = jj / Sd, js = jj - jp * Sd;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t k = k0 + ty * 4 + i;
+    for (int i = 0; i < TMK; ++i) {
+      const int64_t k = k0 + ty * TMK + i;
       if (k < K) Rout[jp * K * Sd + k * Sd + js] = acc[i][j];
     }
   }
 }
 
+int launch_rstep(const float2* S, const float2* Rin, float2* Rout, int64_t P, int64_t K, int64_t N, int64_t NL,
+                 int64_t Sd, cudaStream_t st) {
+  const int64_t J = P * Sd;
+  if (K <= 16) {
+    const int64_t blocks = ((K + 15) / 16) * ((J + 63) / 64);
+    rstep_kernel<16><<<(unsigned)blocks, kT, 0, st>>>(S, Rin, Rout, P, K, N, NL, Sd);
+  } else {
+    const int64_t blocks = ((K + 63) / 64) * ((J + 63) / 64);
+    rstep_kernel<64><<<(unsigned)blocks, kT, 0, st>>>(S, Rin, Rout, P, K, N, NL, Sd);
+  }
+  return (int)cudaGetLastError();
+}
+
 // ---- site gradient, split over columns: part[c][k][n] = sum_{j in c} conj(L(k,j)) R(n,j) ----
+// BM x BN output tiles (16 or 64 each, so that K or N of 8 or 16 does not fill 64-wide
+// tiles with zeros); thread (ty, tx) owns BM/16 x BN/16 outputs.  The columns j are cut
+// into chunks so that the grid has about kGradsBlocks blocks whatever K and N are.
+template <int BM, int BN>
 __global__ void __launch_bounds__(kT) grads_kernel(const float2* __restrict__ Lin, const float2* __restrict__ Rin,
                                                    float2* __restrict__ part, int64_t P, int64_t K,
-                                                   int64_t N, int64_t NL, int64_t Sd) {
-  constexpr int BM = 64, BN = 64, BJ = 16;
+                                                   int64_t N, int64_t NL, int64_t Sd, int64_t chunk) {
+  constexpr int BJ = 16, TMK = BM / 16, TNN = BN / 16;
+  static_assert(kT == 256 && BM % 16 == 0 && BN % 16 == 0, "thread layout");
   __shared__ float2 As[BJ][BM + 1];
   __shared__ float2 Bs[BJ][BN + 1];
   const int64_t J = P * Sd;
   const int64_t k0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
-  const int64_t jb = (int64_t)blockIdx.z * kJChunk, je = min(J, jb + kJChunk);
+  const int64_t jb = (int64_t)blockIdx.z * chunk, je = min(J, jb + chunk);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int64_t strideNH = P * NL * Sd;
-  float2 acc[4][4];
+  float2 acc[TMK][TNN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TMK; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < TNN; ++j) acc[i][j] = make_float2(0.f, 0.f);
   // every element this thread loads has column jj = threadIdx.x % BJ and rows
-  // c = threadIdx.x / BJ + i kT / BJ: the k and n parts of the addresses are fixed, the j
-  // part takes one division per step
-  static_assert(kT % BJ == 0, "column per thread");
+  // c = threadIdx.x / BJ + 16 i: the k and n parts of the addresses are fixed, the j part
+  // takes one division per step
   const int jj = threadIdx.x % BJ, c0 = threadIdx.x / BJ;
-  int64_t koff[4], noff[4];
+  int64_t koff[TMK], noff[TNN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int c = c0 + i * (kT / BJ);
-    const int64_t k = k0 + c, n = n0 + c;
+  for (int i = 0; i < TMK; ++i) {
+    const int64_t k = k0 + c0 + 16 * i;
     koff[i] = k < K ? k * Sd : -1;
+  }
+#pragma unroll
+  for (int i = 0; i < TNN; ++i) {
+    const int64_t n = n0 + c0 + 16 * i;
     noff[i] = n < N ? (n / NL) * strideNH + (n % NL) * Sd : -1;
   }
   for (int64_t j0 = jb; j0 < je; j0 += BJ) {
@@ -167,24 +197,29 @@ __global__ void __launch_bounds__(kT) grads_kernel(const float2* __restrict__ Li
     const bool jok = j < je;
     const int64_t jp = jok ? j / Sd : 0, js = jok ? j - jp * Sd : 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int c = c0 + i * (kT / BJ);
-      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    for (int i = 0; i < TMK; ++i) {
+      float2 a = make_float2(0.f, 0.f);
       if (jok && koff[i] >= 0) { a = Lin[jp * K * Sd + koff[i] + js]; a.y = -a.y; }
+      As[jj][c0 + 16 * i] = a;
+    }
+#pragma unroll
+    for (int i = 0; i < TNN; ++i) {
+      float2 b = make_float2(0.f, 0.f);
       if (jok && noff[i] >= 0) b = Rin[jp * NL * Sd + noff[i] + js];
-      As[jj][c] = a;
-      Bs[jj][c] = b;
+      Bs[jj][c0 + 16 * i] = b;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < BJ; ++r) {
-      float2 a[4], b[4];
+      float2 a[TMK], b[TNN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { a[i] = As[r][ty * 4 + i]; b[i] = Bs[r][tx * 4 + i]; }
+      for (int i = 0; i < TMK; ++i) a[i] = As[r][ty * TMK + i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < TNN; ++j) b[j] = Bs[r][tx * TNN + j];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+      for (int i = 0; i < TMK; ++i)
+#pragma unroll
+        for (int j = 0; j < TNN; ++j) {
           acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
           acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
         }
@@ -193,25 +228,61 @@ __global__ void __launch_bounds__(kT) grads_kernel(const float2* __restrict__ Li
   }
   float2* out = part + (int64_t)blockIdx.z * K * N;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TMK; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t k = k0 + ty * 4 + i, n = n0 + tx * 4 + j;
+    for (int j = 0; j < TNN; ++j) {
+      const int64_t k = k0 + ty * TMK + i, n = n0 + tx * TNN + j;
       if (k < K && n < N) out[k * N + n] = acc[i][j];
     }
 }
 
+// Geometry of the site-gradient GEMM of one step (the same on the host for the workspace
+// size and for the launch).
+struct GradsGeom {
+  int bm, bn;
+  int64_t chunk, chunks;
+};
+GradsGeom grads_geom(int64_t K, int64_t N, int64_t J) {
+  GradsGeom g;
+  g.bm = K <= 16 ? 16 : 64;
+  g.bn = N <= 16 ? 16 : 64;
+  const int64_t tiles = ((K + g.bm - 1) / g.bm) * ((N + g.bn - 1) / g.bn);
+  const int64_t steps = (J + 15) / 16;
+  const int64_t want = std::max<int64_t>(1, std::min<int64_t>(steps, (kGradsBlocks + tiles - 1) / tiles));
+  g.chunk = ((steps + want - 1) / want) * 16;
+  g.chunks = (J + g.chunk - 1) / g.chunk;
+  return g;
+}
+
+int launch_grads(const GradsGeom& g, const float2* Lin, const float2* Rin, float2* part, int64_t P, int64_t K,
+                 int64_t N, int64_t NL, int64_t Sd, cudaStream_t st) {
+  dim3 grid((unsigned)((K + g.bm - 1) / g.bm), (unsigned)((N + g.bn - 1) / g.bn), (unsigned)g.chunks);
+  if (g.bm == 16 && g.bn == 16) grads_kernel<16, 16><<<grid, kT, 0, st>>>(Lin, Rin, part, P, K, N, NL, Sd, g.chunk);
+  else if (g.bm == 16) grads_kernel<16, 64><<<grid, kT, 0, st>>>(Lin, Rin, part, P, K, N, NL, Sd, g.chunk);
+  else if (g.bn == 16) grads_kernel<64, 16><<<grid, kT, 0, st>>>(Lin, Rin, part, P, K, N, NL, Sd, g.chunk);
+  else grads_kernel<64, 64><<<grid, kT, 0, st>>>(Lin, Rin, part, P, K, N, NL, Sd, g.chunk);
+  return (int)cudaGetLastError();
+}
+
+// One warp per output element: lane l sums chunks l, l + 32, ... in order, then a fixed
+// butterfly adds the lanes (deterministic).
 __global__ void __launch_bounds__(kT) reduce_chunks_kernel(const float2* __restrict__ part, int64_t chunks,
                                                            int64_t KN, float2* __restrict__ out) {
-  const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
-  if (t >= KN) return;
+  const int64_t t = ((int64_t)blockIdx.x * kT + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= KN) return;   // warp-uniform: t is the same for all lanes of a warp
   float re = 0.f, im = 0.f;
-  for (int64_t c = 0; c < chunks; ++c) {
+  for (int64_t c = lane; c < chunks; c += 32) {
     const float2 v = part[c * KN + t];
     re += v.x;
     im += v.y;
   }
-  out[t] = make_float2(re, im);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) out[t] = make_float2(re, im);
 }
 
 // ---- fold adjoint: per-block partial gradients of every event's matrix ----------------
@@ -392,8 +463,8 @@ BwdLayout bwd_layout(const qfx_plan* p) {
   uint64_t gp = 0;
   for (size_t i = 1; i < p->steps.size(); ++i) {
     const Step& s = p->steps[i];
-    const uint64_t chunks = (uint64_t)((s.P * s.Sd + kJChunk - 1) / kJChunk);
-    gp = std::max(gp, chunks * (uint64_t)s.K * (uint64_t)s.N * 8);
+    const GradsGeom g = grads_geom(s.K, s.N, s.P * s.Sd);
+    gp = std::max(gp, (uint64_t)g.chunks * (uint64_t)s.K * (uint64_t)s.N * 8);
   }
   L.gpart = o; o += a256(gp);
   uint64_t bp = 0;
@@ -522,16 +593,14 @@ extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t*
           continue;
         }
         const float2* Lin = (const float2*)line_in(j);
-        const int64_t J = sp.P * sp.Sd, chunks = (J + kJChunk - 1) / kJChunk;
-        dim3 gg((unsigned)((sp.K + 63) / 64), (unsigned)((sp.N + 63) / 64), (unsigned)chunks);
+        const int64_t J = sp.P * sp.Sd;
+        const GradsGeom gg = grads_geom(sp.K, sp.N, J);
         float2* part = (float2*)(ws + Lw.gpart);
-        grads_kernel<<<gg, kT, 0, st>>>(Lin, Rcur, part, sp.P, sp.K, sp.N, sp.NL, sp.Sd);
+        launch_grads(gg, Lin, Rcur, part, sp.P, sp.K, sp.N, sp.NL, sp.Sd, st);
         const int64_t KN = sp.K * sp.N;
-        reduce_chunks_kernel<<<(unsigned)((KN + kT - 1) / kT), kT, 0, st>>>(part, chunks, KN, gdst);
+        reduce_chunks_kernel<<<(unsigned)((KN * 32 + kT - 1) / kT), kT, 0, st>>>(part, gg.chunks, KN, gdst);
         float2* Rnext = (float2*)rr(rsel ^ 1);
-        const int64_t blocks = ((sp.K + 63) / 64) * ((J + 63) / 64);
-        rstep_kernel<<<(unsigned)blocks, kT, 0, st>>>((const float2*)site_ptr(sp.site), Rcur, Rnext, sp.P,
-                                                      sp.K, sp.N, sp.NL, sp.Sd);
+        launch_rstep((const float2*)site_ptr(sp.site), Rcur, Rnext, sp.P, sp.K, sp.N, sp.NL, sp.Sd, st);
         count_launch(3);
         rsel ^= 1;
         Rcur = Rnext;
