@@ -289,7 +289,7 @@ def run_qfx(args):
     }
     if not args.no_modes:
         line["precision_modes"] = {m: run_mode(qfx, torch, circ, w, m, x1_dev, args, dev, stream)
-                                   for m in ("bf16x3", "tf32x3", "bf16x3_fast")}
+                                   for m in ("bf16x3", "tf32x3", "bf16x2", "bf16x3_fast")}
     if world == 1 and not args.no_cpu:
         rate, reps, dt = cpu_oracle_sample(seconds=args.cpu_seconds)
         line["cpu_baseline"] = {
@@ -305,11 +305,10 @@ def run_qfx(args):
 
 
 # Tensor-pipe work per counted complex multiply-add (8 counted flops): 4 real products,
-# each the sum of 6 (BF16x3) or 3 (TF32x3) term products -> 48 or 24 flops of the mode's
-# type.  TF32 runs at half the BF16 rate (nominal ratio), so both modes cost 6x the
-# counted flops in BF16-equivalent tensor work.
-TENSOR_FACTOR = {"bf16x3": 48 / 8, "tf32x3": 24 / 8}
-TENSOR_PEAK_RATIO = {"bf16x3": 1.0, "tf32x3": 0.5}
+# each the sum of 6 (BF16x3) or 3 (TF32x3, BF16x2) term products -> 48 or 24 flops of the
+# mode's type.  TF32 runs at half the BF16 rate (nominal ratio).
+TENSOR_FACTOR = {"bf16x3": 48 / 8, "tf32x3": 24 / 8, "bf16x2": 24 / 8}
+TENSOR_PEAK_RATIO = {"bf16x3": 1.0, "tf32x3": 0.5, "bf16x2": 1.0}
 
 
 def measured_peaks():
@@ -587,7 +586,7 @@ def main():
                     choices=sorted(WORKLOADS) + ["kstep", "batch", "batch_small", "permute", "adjoint"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "bf16x3_fast"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "bf16x2", "bf16x3_fast"],
                     help="kernel case only; the amplitude run reports every mode")
     ap.add_argument("--no-modes", action="store_true", help="skip the split-precision runs")
     ap.add_argument("--no-autotune", action="store_true", help="batch case: planner's default tiles")

@@ -89,8 +89,12 @@ void qfx_circuit_destroy(qfx_circuit* c);
 
 typedef enum {
   QFX_PREC_FP32_SIMT = 0,   /* complex FP32 on the FMA pipes, 4 real FMAs per complex MAC */
-  QFX_PREC_C3M_BF16X3 = 1,  /* 3M complex product on tcgen05, operands split into 3 BF16 terms */
-  QFX_PREC_C3M_TF32X3 = 2   /* 3M complex product on tcgen05, operands split into 2 TF32 terms */
+  /* Split-precision modes on tcgen05 with FP32 accumulation.  The complex product is formed
+   * from 4 real products (4M; the C3M names are the modes' family names), each the sum of
+   * the term products above the mode's precision: */
+  QFX_PREC_C3M_BF16X3 = 1,  /* 3 BF16 terms h, m, l; 6 term products; ~FP32 error */
+  QFX_PREC_C3M_TF32X3 = 2,  /* 2 TF32 terms; 3 term products; ~2^-21 */
+  QFX_PREC_C3M_BF16X2 = 3   /* 2 BF16 terms h, m; 3 term products (hm, mh, hh); ~2^-16, fastest */
 } qfx_precision;
 
 /* A cut (Sec. III.A): the bond between grid neighbours qa and qb is sliced into pieces

@@ -65,6 +65,13 @@ struct Mode<QFX_PREC_C3M_BF16X3> {
   __device__ static constexpr int tb(int i) { return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 0 : i == 3 ? 1 : i == 4 ? 0 : 0; }
 };
 template <>
+struct Mode<QFX_PREC_C3M_BF16X2> {
+  static constexpr int TERMS = 2, KS = 16, NPROD = 3;
+  static constexpr uint32_t FMT = 1;   // BF16: h, m with products hm, mh, hh (~2^-16)
+  __device__ static constexpr int ta(int i) { return i == 0 ? 0 : i == 1 ? 1 : 0; }
+  __device__ static constexpr int tb(int i) { return i == 0 ? 1 : i == 1 ? 0 : 0; }
+};
+template <>
 struct Mode<QFX_PREC_C3M_TF32X3> {
   static constexpr int TERMS = 2, KS = 8, NPROD = 3;
   static constexpr uint32_t FMT = 2;   // TF32
@@ -73,15 +80,16 @@ struct Mode<QFX_PREC_C3M_TF32X3> {
 };
 
 // ---- term splitting ------------------------------------------------------------
-__device__ __forceinline__ void split_bf16x3(float x, uint16_t t[3]) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(h);
-  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(m);
-  const __nv_bfloat16 l = __float2bfloat16_rn(r2);
-  t[0] = __bfloat16_as_ushort(h);
-  t[1] = __bfloat16_as_ushort(m);
-  t[2] = __bfloat16_as_ushort(l);
+// T BF16 terms of x: each the round-to-nearest of what the previous ones left
+template <int T>
+__device__ __forceinline__ void split_bf16(float x, uint16_t t[T]) {
+  float r = x;
+#pragma unroll
+  for (int i = 0; i < T; ++i) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(r);
+    t[i] = __bfloat16_as_ushort(h);
+    r -= __bfloat162float(h);
+  }
 }
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -101,18 +109,19 @@ __device__ __forceinline__ void store_row_terms(char* plane0, int plane_bytes, i
                                                 const float* x) {
   using M_ = Mode<MODE>;
   const int base = (row >> 3) * 256 + (row & 7) * 16;
-  if constexpr (MODE == QFX_PREC_C3M_BF16X3) {
-    uint32_t w[3][8];
+  if constexpr (M_::FMT == 1) {   // BF16 terms, 16 per row
+    constexpr int T = M_::TERMS;
+    uint32_t w[T][8];
 #pragma unroll
     for (int k = 0; k < 16; k += 2) {
-      uint16_t a[3], b[3];
-      split_bf16x3(x[k], a);
-      split_bf16x3(x[k + 1], b);
+      uint16_t a[T], b[T];
+      split_bf16<T>(x[k], a);
+      split_bf16<T>(x[k + 1], b);
 #pragma unroll
-      for (int t = 0; t < 3; ++t) w[t][k / 2] = (uint32_t)a[t] | ((uint32_t)b[t] << 16);
+      for (int t = 0; t < T; ++t) w[t][k / 2] = (uint32_t)a[t] | ((uint32_t)b[t] << 16);
     }
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < T; ++t) {
       char* pl = plane0 + t * plane_bytes + base;
       *reinterpret_cast<uint4*>(pl) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
       *reinterpret_cast<uint4*>(pl + 128) = make_uint4(w[t][4], w[t][5], w[t][6], w[t][7]);
@@ -723,7 +732,8 @@ int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_str
 bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags) {
   // default tiles are 128 columns wide (N <= 128 or exactly two tiles); fast ones up to 256
   const bool n_ok = N % 16 == 0 && ((flags & kTcFast) ? N <= 256 : (N <= 128 || N == 256));
-  if (precision == QFX_PREC_C3M_BF16X3) return n_ok && K % 16 == 0 && J >= kRows;
+  if (precision == QFX_PREC_C3M_BF16X3 || precision == QFX_PREC_C3M_BF16X2)
+    return n_ok && K % 16 == 0 && J >= kRows;
   if (precision == QFX_PREC_C3M_TF32X3) return n_ok && K % 8 == 0 && J >= kRows;
   return false;
 }
@@ -731,6 +741,7 @@ bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags) {
 uint64_t tc_scratch_bytes(int precision, int64_t K, int64_t N) {
   // per k-stage and column n: 3 planes per term (the embedded layout of default tiles)
   if (precision == QFX_PREC_C3M_BF16X3) return (uint64_t)(K / 16) * 9 * (uint64_t)N * 32;
+  if (precision == QFX_PREC_C3M_BF16X2) return (uint64_t)(K / 16) * 6 * (uint64_t)N * 32;
   if (precision == QFX_PREC_C3M_TF32X3) return (uint64_t)(K / 8) * 6 * (uint64_t)N * 32;
   return 0;
 }
@@ -747,6 +758,11 @@ int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_str
     return fast ? launch_tc_mode<QFX_PREC_C3M_BF16X3, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
                                                              Sd, batch, scratch, scratch_stride, withhold, no_tma, st)
                 : launch_tc_mode<QFX_PREC_C3M_BF16X3, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
+                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, st);
+  if (precision == QFX_PREC_C3M_BF16X2)
+    return fast ? launch_tc_mode<QFX_PREC_C3M_BF16X2, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
+                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, st)
+                : launch_tc_mode<QFX_PREC_C3M_BF16X2, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, st);
   if (precision == QFX_PREC_C3M_TF32X3)
     return fast ? launch_tc_mode<QFX_PREC_C3M_TF32X3, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,

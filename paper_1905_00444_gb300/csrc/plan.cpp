@@ -126,7 +126,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
   *out = nullptr;
   try {
     if (o->plan_family != 0) return qfx::fail(QFX_EUNSUPPORTED, "plan_family: only 0 (line sweep)");
-    if (o->precision < QFX_PREC_FP32_SIMT || o->precision > QFX_PREC_C3M_TF32X3)
+    if (o->precision < QFX_PREC_FP32_SIMT || o->precision > QFX_PREC_C3M_BF16X2)
       return qfx::fail(QFX_EINVAL, "unknown precision");
     const int n = c->rows * c->cols;
     Geometry geo{c->rows, c->cols, c->rows > c->cols, 0, 0};
@@ -278,7 +278,9 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     for (auto& st : p->steps) {
       st.variant = qfx::pick_variant(st.N, st.Sd);
       if (&st != &p->steps[0] && qfx::tc_eligible(p->precision, st.K, st.N, st.P * st.Sd, p->tc_flags)) {
-        st.variant = p->precision == QFX_PREC_C3M_BF16X3 ? qfx::kVariantTcBf16 : qfx::kVariantTcTf32;
+        st.variant = p->precision == QFX_PREC_C3M_BF16X3   ? qfx::kVariantTcBf16
+                     : p->precision == QFX_PREC_C3M_BF16X2 ? qfx::kVariantTcBf16x2
+                                                           : qfx::kVariantTcTf32;
         simage = std::max(simage, qfx::tc_scratch_bytes(p->precision, st.K, st.N));
       }
     }

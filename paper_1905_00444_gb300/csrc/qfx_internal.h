@@ -156,7 +156,7 @@ int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride
                 int batch, int variant, int precision, void* stream);
 int pick_variant(int64_t N, int64_t Sd);
 // tensor-core steps (variants 10 = BF16x3, 11 = TF32x3)
-constexpr int kVariantTcBf16 = 10, kVariantTcTf32 = 11;
+constexpr int kVariantTcBf16 = 10, kVariantTcTf32 = 11, kVariantTcBf16x2 = 14;
 constexpr int kTcFast = 1;       // QFX_TC_FAST_ACCUMULATION
 constexpr int kTcWithhold = 2;   // test hook: S stream withheld
 constexpr int kTcNoTma = 4;      // QFX_TC_REGISTER_ROWS

@@ -268,7 +268,7 @@ extern "C" qfx_status qfx_contract_step(const void* S, const void* B, void* C, i
     return fail(QFX_EINVAL, "qfx_contract_step: need positive sizes and NL | N");
   if ((((uintptr_t)S) | ((uintptr_t)B) | ((uintptr_t)C)) & 15)
     return fail(QFX_EINVAL, "qfx_contract_step: pointers must be 16-byte aligned");
-  if (precision < QFX_PREC_FP32_SIMT || precision > QFX_PREC_C3M_TF32X3)
+  if (precision < QFX_PREC_FP32_SIMT || precision > QFX_PREC_C3M_BF16X2)
     return fail(QFX_EINVAL, "qfx_contract_step: unknown precision");
   const bool tc = precision != QFX_PREC_FP32_SIMT &&
                   tc_eligible(precision, K, N, P * Sd, variant == 12 ? kTcFast : 0);
@@ -288,7 +288,8 @@ extern "C" qfx_status qfx_contract_step(const void* S, const void* B, void* C, i
   int v = variant < 0 ? pick_variant(N, Sd) : variant;
   int err;
   if (tc) {
-    v = precision == QFX_PREC_C3M_BF16X3 ? kVariantTcBf16 : kVariantTcTf32;
+    v = precision == QFX_PREC_C3M_BF16X3 ? kVariantTcBf16
+        : precision == QFX_PREC_C3M_BF16X2 ? kVariantTcBf16x2 : kVariantTcTf32;
     err = launch_step_tc(S, 0, B, 0, C, 0, P, K, N, NL, Sd, 1, precision, (char*)scratch, 0, stream,
                          flags);
   } else {

@@ -16,7 +16,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "qfx.h")
 
 QFX_OK, QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA, QFX_ETIMEOUT, QFX_EUNSUPPORTED, QFX_EPLAN = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EUNSUPPORTED", "EPLAN"]
-PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 2}
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 2, "bf16x2": 3}
 
 
 class QfxError(RuntimeError):

@@ -8,7 +8,9 @@ meets the FP32 path's 1e-5 amplitude bar in BF16x3 (measured 4.4e-6 at 7x7x(1+32
 TF32x3 is limited by its two-term split (about 2^-21 per product): stated bound 3e-5
 (measured 1.4e-5 at 7x7x(1+32+1)).  Fast accumulation (one accumulator pair, all
 term products in it; measured 3.4e-6 per K = 256 step and 5e-5 at 7x7x(1+32+1)) has a
-stated amplitude bound of 1e-4.
+stated amplitude bound of 1e-4.  BF16x2 (x = h + m, products hm, mh, hh) drops terms near
+2^-16 relative (measured 4.5e-6 per step, 3e-5 to 5e-5 per amplitude up to 7x7x(1+32+1)):
+stated bounds 2e-5 per step and 2e-4 per amplitude.
 """
 import numpy as np
 import pytest
@@ -19,9 +21,9 @@ from oracle import network, primitives, stabilizer
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-BOUND = {"bf16x3": 1e-5, "tf32x3": 3e-5}
+BOUND = {"bf16x3": 1e-5, "tf32x3": 3e-5, "bf16x2": 2e-4}
 FAST_BOUND = 1e-4
-STEP_BOUND = {"bf16x3": 1e-6, "tf32x3": 3e-6}
+STEP_BOUND = {"bf16x3": 1e-6, "tf32x3": 3e-6, "bf16x2": 2e-5}
 FAST_STEP_BOUND = 1e-5
 
 
@@ -31,7 +33,7 @@ def step_ref(S, B, P, K, N, NL, Sd):
 
 
 @pytest.mark.parametrize("fast", [False, True])
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "bf16x2"])
 @pytest.mark.parametrize("shape", [(1, 256, 256, 256, 1024), (16, 256, 256, 256, 16),
                                    (3, 64, 64, 32, 64), (2000, 16, 16, 16, 1),
                                    (1, 32, 48, 48, 300), (5, 256, 32, 16, 40),
@@ -49,10 +51,10 @@ def test_step_vs_oracle(qfx, prec, shape, fast):
     got = out.cpu().numpy().reshape(want.shape)
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     print(f"step {prec} fast={fast} {shape}: {err:.2e}")
-    assert err < (FAST_STEP_BOUND if fast else STEP_BOUND[prec]), err
+    assert err < max(FAST_STEP_BOUND if fast else 0.0, STEP_BOUND[prec]), err
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "bf16x2"])
 def test_step_matches_fp32_path(qfx, prec):
     P, K, N, NL, Sd = 4, 256, 256, 256, 512
     S = torch.from_numpy(ri.random_complex((K * N,), seed=5)).cuda()
@@ -64,7 +66,7 @@ def test_step_matches_fp32_path(qfx, prec):
     assert rel < STEP_BOUND[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "bf16x2"])
 @pytest.mark.parametrize("shape", [(1, 64, 64, 64, 4096), (8, 64, 64, 64, 512), (64, 64, 64, 64, 64),
                                    (512, 64, 64, 64, 8), (4, 64, 16, 8, 512), (16, 64, 16, 8, 8),
                                    (77, 32, 32, 32, 2), (3, 48, 64, 64, 128), (9, 32, 256, 64, 16),
@@ -121,7 +123,7 @@ def errors(got, want, n):
     return per, nw
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "bf16x2"])
 @pytest.mark.parametrize("shape", [(5, 5, 24), (6, 6, 24), (7, 7, 24)])
 def test_amplitudes_vs_oracle(qfx, prec, shape):
     rows, cols, d = shape
@@ -136,7 +138,7 @@ def test_amplitudes_vs_oracle(qfx, prec, shape):
     assert per <= BOUND[prec] and nw <= BOUND[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "bf16x2"])
 def test_7x7x32_clifford_exact(qfx, prec):
     c = ri.rqc(7, 7, 32, seed=11, gate_set=(ri.SQRT_X, ri.SQRT_Y))
     x1 = int(ri.random_bitstrings(49, 1, seed=12)[0])
@@ -158,14 +160,14 @@ def test_7x7x32_split_modes_agree_with_fp32(qfx):
     x1 = int(ri.random_bitstrings(49, 1, seed=1)[0])
     _, ref = run(qfx, c, [x1], "fp32", 6)
     floor = 2.0 ** (-49 / 2)
-    for prec, fast in (("bf16x3", False), ("tf32x3", False), ("bf16x3", True)):
+    for prec, fast in (("bf16x3", False), ("tf32x3", False), ("bf16x2", False), ("bf16x3", True)):
         _, out = run(qfx, c, [x1], prec, 6, fast=fast)
         per = np.max(np.abs(out - ref) / np.maximum(np.abs(ref), floor))
         print(f"7x7x32 {prec} fast={fast} vs fp32: {per:.2e}")
         assert per <= (FAST_BOUND if fast else BOUND[prec])
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "bf16x2"])
 def test_batched_items_and_slices(qfx, prec):
     # several (slice, x1) items per launch, uneven shapes, through the tensor-core path
     c = ri.rqc(6, 6, 24, seed=2)
