@@ -43,6 +43,7 @@
 
 #include <cstring>
 
+#include "ptx_async.cuh"
 #include "qfx_internal.h"
 
 namespace qfx {
@@ -50,6 +51,8 @@ namespace qfx {
 __device__ unsigned int g_tc_status = 0;
 
 namespace {
+
+using namespace ptx;
 
 constexpr int kRows = 128;        // UMMA M
 constexpr int kPlaneA = kRows * 32;   // bytes of one A term plane per stage
@@ -146,31 +149,6 @@ __device__ __forceinline__ void store_row_terms(char* plane0, int plane_bytes, i
 }
 
 // ---- PTX helpers -----------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(bar),
-               "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-  return ok != 0;
-}
 // Bounded wait: false if the deadline passed or another role gave up.  Roles off the
 // critical path pass sleep_ns > 0 so that their polling does not take issue slots from
 // the producers.
@@ -188,14 +166,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     if (sleep_ns) __nanosleep(sleep_ns);
   }
   return true;
-}
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   // K-major, no swizzle: LBO = 128 B (next core matrix along K), SBO = 256 B (next
@@ -278,14 +248,6 @@ struct TcCfg {
   }
 };
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-      : "memory");
-}
-
 template <int MODE, bool SPLITACC>
 __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
     cgemm_tc_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tmA) {
@@ -332,7 +294,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
       mbar_init(in_full(b), 1);
       mbar_init(in_empty(b), kRows);
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   if (warp == 12) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base_slot))
@@ -640,22 +602,6 @@ int num_sms() {
   if (dev >= 64) dev = 63;
   if (!n[dev]) cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev);
   return n[dev] > 0 ? n[dev] : 1;
-}
-
-// cuTensorMapEncodeTiled from the driver, looked up at run time (the library links only
-// the static CUDA runtime, so it loads on machines without a driver).
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess && q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
-  }
-  return fn;
 }
 
 // Tensor map over B viewed as (s, k, p, item) 8-byte elements, box (box_s, KS, box_p, 1)

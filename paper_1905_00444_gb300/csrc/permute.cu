@@ -1,17 +1,31 @@
 // Tensor transpose for complex64 tensors of rank <= 10 (the "T" steps of TTGT,
-// Sec. III.E).  Axes that stay adjacent are fused first.  If the innermost output axis
-// is also innermost in the input, rows are copied with 16-byte vectors, 4096 output
-// elements per block; otherwise a 32 x 32 tile of (output-innermost axis,
-// input-innermost axis) goes through shared memory so that both the reads and the
-// writes are coalesced, each block walking 8 consecutive batch coordinates.
+// Sec. III.E).  Axes that stay adjacent are fused first.
+// - Innermost output axis also innermost in the input: rows are copied with 16-byte
+//   vectors, 4096 output elements per block.
+// - Otherwise, when both innermost axes have at least 16 elements and the strides allow
+//   a tensor map: tiles of 16 (input-innermost axis lb) x TA (output-innermost axis la)
+//   x BZ (consecutive values of one more axis) elements arrive by tensor-map copies with
+//   128-byte swizzle into a ring of shared buffers; each warp instruction then reads 16
+//   consecutive la by 2 consecutive lb (conflict-free under the swizzle) and writes two
+//   128-byte output segments.  The input is viewed as a 5-D tensor: lb, la, and the
+//   other axes merged into at most three runs that are contiguous in the input.
+// - Otherwise a 32 x 32 tile goes through shared memory with plain loads, each block
+//   walking 8 consecutive batch coordinates.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
+#include "ptx_async.cuh"
 #include "qfx_internal.h"
 
 namespace qfx {
+
+__device__ unsigned int g_perm_status = 0;
+
 namespace {
+
+using namespace ptx;
 
 constexpr int kMaxRank = 10;
 
@@ -117,6 +131,242 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const float2* __restr
   }
 }
 
+
+// ---- case 3: tensor-map staged transpose -------------------------------------------
+struct PermTma {
+  int64_t Da, Db;           // extents of la (output stride 1) and lb (input stride 1)
+  int64_t tiles_a, tiles_b, nbatch, total;
+  int64_t ostr_b;           // output stride of lb
+  int nseg;                 // runs of the other axes, contiguous in the input (<= 3)
+  int64_t segE[3];          // run extents (coordinates 2..4 of the tensor map)
+  int seg_n[3];             // axes per run, innermost first
+  int64_t ax_dim[kMaxRank], ax_ostr[kMaxRank];   // the runs' axes, run by run
+  int BZ;                   // box extent along run 0 (divides its innermost axis)
+  int64_t tiles_z;          // segE[0] / BZ (1 if there is no run)
+  int64_t ostr_z;           // output stride of run 0's innermost axis
+};
+constexpr unsigned long long kPermWaitNs = 1000000000ull;   // 1 s per wait
+
+__device__ __forceinline__ bool perm_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long deadline = globaltimer() + kPermWaitNs;
+  while (!mbar_try(bar, parity)) {
+    if (globaltimer() > deadline) {
+      atomicOr(&g_perm_status, 1u);
+      return false;
+    }
+  }
+  return true;
+}
+
+struct TileMeta {
+  int64_t obase;
+  int na, nb;
+};
+
+// Thread 0: tensor-map coordinates and output placement of tile t; issues its copy.
+template <int TA>
+__device__ __forceinline__ void perm_issue(const PermTma& a, const CUtensorMap* map, int64_t t, uint32_t dst,
+                                           uint32_t bar, TileMeta* meta) {
+  constexpr int TB = 16;
+  const int64_t ta = t % a.tiles_a, r = t / a.tiles_a;
+  const int64_t tb = r % a.tiles_b;
+  int64_t bi = r / a.tiles_b;
+  int z[3] = {0, 0, 0};
+  int64_t obase = ta * TA + tb * TB * a.ostr_b;
+  for (int g = a.nseg - 1; g >= 1; --g) {   // run 0 most significant
+    const int64_t zg = bi % a.segE[g];
+    bi /= a.segE[g];
+    z[g] = (int)zg;
+  }
+  if (a.nseg > 0) z[0] = (int)(bi * a.BZ);  // run 0 advances a box of BZ at a time
+  int ax = 0;
+  for (int g = 0; g < a.nseg; ++g) {
+    int64_t zg = z[g];
+    for (int i = 0; i < a.seg_n[g]; ++i, ++ax) {
+      const int64_t c = zg % a.ax_dim[ax];
+      zg /= a.ax_dim[ax];
+      obase += c * a.ax_ostr[ax];
+    }
+  }
+  meta->obase = obase;
+  const int64_t ra = a.Da - ta * TA, rb = a.Db - tb * TB;
+  meta->na = (int)(ra < TA ? ra : TA);
+  meta->nb = (int)(rb < TB ? rb : TB);
+  mbar_arrive_tx(bar, (uint32_t)(TB * TA * a.BZ * 8));
+  tma_load_5d(dst, map, (int)(tb * TB), (int)(ta * TA), z[0], z[1], z[2], bar);
+}
+
+template <int TA, int NB>
+__global__ void __launch_bounds__(128) permute_tma_kernel(const PermTma a, float2* __restrict__ out,
+                                                          const __grid_constant__ CUtensorMap map) {
+  constexpr int TB = 16;
+  const int TILE = TB * TA * 8 * a.BZ, UNITS = 8 * (TA / 16) * a.BZ;
+  extern __shared__ char smem_raw[];
+  // 128-byte swizzled boxes must start on 1024-byte boundaries
+  char* buf = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ uint64_t full[NB];
+  __shared__ TileMeta meta[NB];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int b = 0; b < NB; ++b) mbar_init(smem_u32(&full[b]), 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int64_t stride = gridDim.x;
+  int issued[NB];
+  if (tid == 0) {
+    for (int b = 0; b < NB; ++b) {
+      issued[b] = 0;
+      const int64_t t = blockIdx.x + b * stride;
+      if (t < a.total) {
+        perm_issue<TA>(a, &map, t, smem_u32(buf + b * TILE), smem_u32(&full[b]), &meta[b]);
+        issued[b] = 1;
+      }
+    }
+  }
+  int64_t k = 0;
+  bool ok = true;
+  for (int64_t t = blockIdx.x; t < a.total; t += stride, ++k) {
+    const int b = (int)(k % NB);
+    const uint32_t par = (uint32_t)((k / NB) & 1);
+    if (tid == 0) s_ok = perm_wait(smem_u32(&full[b]), par) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) { ok = false; break; }   // uniform across the block
+    mbar_try(smem_u32(&full[b]), par);   // this thread's own acquire of the completed phase
+    const TileMeta m = meta[b];
+    const char* tile = buf + b * TILE;
+    const int ia_lo = lane & 15, h = lane >> 4;
+    for (int u = warp; u < UNITS; u += 4) {
+      const int c = u & 7, iz = (u >> 3) / (TA / 16), ia = ((u >> 3) % (TA / 16)) * 16 + ia_lo, ib = 2 * c + h;
+      // row (iz, ia) of the box is 128 bytes of lb; its 16-byte chunk c sits at
+      // c ^ (row mod 8), and row mod 8 = ia mod 8 since TA is a multiple of 8
+      const float2 v = *reinterpret_cast<const float2*>(tile + (iz * TA + ia) * 128 + ((c ^ (ia & 7)) << 4) + h * 8);
+      if (ia < m.na && ib < m.nb) out[m.obase + iz * a.ostr_z + ia + (int64_t)ib * a.ostr_b] = v;
+    }
+    // the next copy into this buffer goes through the async proxy: order the reads first
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      const int64_t tn = t + NB * stride;
+      if (tn < a.total) {
+        perm_issue<TA>(a, &map, tn, smem_u32(buf + b * TILE), smem_u32(&full[b]), &meta[b]);
+        ++issued[b];
+      }
+    }
+  }
+  if (!ok && tid == 0) {
+    // copies still in flight must land before the block exits
+    for (int b = 0; b < NB; ++b)
+      if (issued[b] > 0) {
+        const uint32_t par = (uint32_t)((issued[b] - 1) & 1);
+        const unsigned long long deadline = globaltimer() + kPermWaitNs;
+        while (!mbar_try(smem_u32(&full[b]), par) && globaltimer() < deadline) {
+        }
+      }
+  }
+}
+
+// Host: the 5-D view and tensor map of the input, or false when this path does not apply.
+bool perm_tma_plan(const PermArgs& f, const void* in, PermTma* t, CUtensorMap* map, int* ta_out) {
+  auto enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)in & 15)) return false;
+  const int fr = f.rank, la = f.la, lb = f.lb;
+  const int64_t Da = f.dim[la], Db = f.dim[lb];
+  if (Da < 16 || Db < 16 || Da > 0x7fffffff || Db > 0x7fffffff) return false;
+  // the other axes in input order (outermost first), cut into runs contiguous in the input
+  int order[kMaxRank], n = 0;
+  for (int i = 0; i < fr; ++i)
+    if (i != la && i != lb) order[n++] = i;
+  for (int i = 1; i < n; ++i)   // sort by input stride, descending
+    for (int j = i; j > 0 && f.istr[order[j]] > f.istr[order[j - 1]]; --j) std::swap(order[j], order[j - 1]);
+  PermTma a{};
+  a.Da = Da;
+  a.Db = Db;
+  a.ostr_b = f.ostr[lb];
+  int64_t segS[3] = {1, 1, 1};
+  int ax = 0;
+  for (int i = 0; i < n;) {
+    if (a.nseg == 3) return false;
+    int j = i;   // run [i, j]: each next axis sits right inside the previous one in memory
+    while (j + 1 < n && f.istr[order[j]] == f.istr[order[j + 1]] * f.dim[order[j + 1]]) ++j;
+    int64_t E = 1;
+    for (int q = j; q >= i; --q) {   // innermost first
+      a.ax_dim[ax] = f.dim[order[q]];
+      a.ax_ostr[ax] = f.ostr[order[q]];
+      ++ax;
+      E *= f.dim[order[q]];
+    }
+    if (E > 0x7fffffff) return false;
+    a.segE[a.nseg] = E;
+    a.seg_n[a.nseg] = j - i + 1;
+    segS[a.nseg] = f.istr[order[j]];
+    ++a.nseg;
+    i = j + 1;
+  }
+  // strides of map dimensions 1..4 in bytes must be multiples of 16
+  if ((f.istr[la] & 1) || (a.nseg > 0 && (segS[0] & 1)) || (a.nseg > 1 && (segS[1] & 1)) ||
+      (a.nseg > 2 && (segS[2] & 1)))
+    return false;
+  const int TA = Da >= 64 ? 64 : Da >= 32 ? 32 : 16;
+  a.tiles_a = (Da + TA - 1) / TA;
+  a.tiles_b = (Db + 15) / 16;
+  // boxes of 8 KB or more: BZ values of run 0's innermost axis (a divisor of its extent)
+  a.BZ = 1;
+  a.ostr_z = 0;
+  if (a.nseg > 0) {
+    const int want = 64 / TA;   // 1, 2 or 4 ... up to 8 for TA = 16
+    const int64_t d0 = a.ax_dim[0];   // run 0's innermost axis
+    int bz = 1;
+    while (bz * 2 <= (TA == 16 ? 8 : want) && d0 % (bz * 2) == 0) bz *= 2;
+    a.BZ = bz;
+    a.ostr_z = a.ax_ostr[0];
+  }
+  a.nbatch = 1;
+  for (int g = 1; g < a.nseg; ++g) a.nbatch *= a.segE[g];
+  if (a.nseg > 0) a.nbatch *= a.segE[0] / a.BZ;
+  a.total = a.tiles_a * a.tiles_b * a.nbatch;
+  int64_t total_el = 1;
+  for (int i = 0; i < fr; ++i) total_el *= f.dim[i];
+  const cuuint64_t pad_stride = (cuuint64_t)((total_el * 8 + 15) / 16 * 16);
+  cuuint64_t dims[5] = {(cuuint64_t)Db, (cuuint64_t)Da, 1, 1, 1};
+  cuuint64_t strides[4] = {(cuuint64_t)f.istr[la] * 8, pad_stride, pad_stride, pad_stride};
+  for (int g = 0; g < a.nseg; ++g) {
+    dims[2 + g] = (cuuint64_t)a.segE[g];
+    strides[1 + g] = (cuuint64_t)segS[g] * 8;
+  }
+  const cuuint32_t box[5] = {16, (cuuint32_t)TA, (cuuint32_t)a.BZ, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(in), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  *t = a;
+  *ta_out = TA;
+  return true;
+}
+
+template <int TA, int NB>
+int launch_perm_tma(const PermTma& a, const CUtensorMap& map, float2* out, cudaStream_t st) {
+  const size_t smem = (size_t)NB * 16 * TA * 8 * a.BZ + 1024;   // NB x 8 or 16 KB
+  static int attr_dev[64] = {0};
+  int dev0 = 0;
+  cudaGetDevice(&dev0);
+  if (dev0 < 64 && !attr_dev[dev0]) {
+    cudaError_t e = cudaFuncSetAttribute(permute_tma_kernel<TA, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         NB * 16384 + 1024);   // boxes are at most 16 KB
+    if (e != cudaSuccess) return (int)e;
+    attr_dev[dev0] = 1;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (int64_t)(sms > 0 ? sms : 1) * 4;
+  const unsigned grid = (unsigned)(a.total < want ? a.total : want);
+  permute_tma_kernel<TA, NB><<<grid, 128, smem, st>>>(a, out, map);
+  return (int)cudaGetLastError();
+}
 }  // namespace
 
 int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
@@ -160,6 +410,17 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
     for (int i = 0; i < fr; ++i)
       if (a.istr[i] == 1) a.lb = i;
     if (a.lb < 0) return (int)cudaErrorInvalidValue;
+    PermTma tp;
+    alignas(64) CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    int TA = 0;
+    if (perm_tma_plan(a, in, &tp, &map, &TA)) {
+      const int err = TA == 64 ? launch_perm_tma<64, 4>(tp, map, dst, st)
+                    : TA == 32 ? launch_perm_tma<32, 4>(tp, map, dst, st)
+                               : launch_perm_tma<16, 4>(tp, map, dst, st);
+      count_launch();
+      return err;
+    }
     a.tiles_a = (a.dim[a.la] + 31) / 32;
     a.tiles_b = (a.dim[a.lb] + 31) / 32;
     const int64_t batch = total / (a.dim[a.la] * a.dim[a.lb]);
@@ -169,6 +430,16 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
   }
   count_launch();
   return (int)cudaGetLastError();
+}
+
+int perm_take_status() {
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_perm_status, sizeof(v)) != cudaSuccess) return -1;
+  if (v) {
+    const unsigned int z = 0;
+    cudaMemcpyToSymbol(g_perm_status, &z, sizeof(z));
+  }
+  return v ? 1 : 0;
 }
 
 }  // namespace qfx

@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "ptx_async.cuh"
 #include "qfx_internal.h"
 
 namespace qfx {
@@ -241,6 +242,22 @@ extern "C" qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int6
   return exec_amplitudes(p, *tp, x1, n_batch, slice_begin, slice_end, workspace, G, out, stream);
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up at run time (the library links only
+// the static CUDA runtime, so it loads on machines without a driver).
+PFN_cuTensorMapEncodeTiled_v12000 qfx::tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
 extern "C" qfx_status qfx_sync(void* stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "qfx_sync");
@@ -252,6 +269,9 @@ extern "C" qfx_status qfx_sync(void* stream) {
   const int bt = batch_take_status();
   if (bt < 0) return fail(QFX_ECUDA, "qfx_sync: reading the batch status word failed");
   if (bt > 0) return fail(QFX_ETIMEOUT, "qfx_sync: the batch scheduler gave up a dependency wait (bounded wait expired)");
+  const int pt = perm_take_status();
+  if (pt < 0) return fail(QFX_ECUDA, "qfx_sync: reading the permute status word failed");
+  if (pt > 0) return fail(QFX_ETIMEOUT, "qfx_sync: a permute copy did not arrive (bounded wait expired)");
   return QFX_OK;
 }
 

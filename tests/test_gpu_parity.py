@@ -248,7 +248,11 @@ def test_contract_step_variants(qfx, variant, shape):
                                   ((8, 8, 8), (0, 1, 2)), ((16,) * 5, (4, 3, 2, 1, 0)),
                                   ((64, 64, 16), (1, 0, 2)), ((3, 5, 7, 9), (2, 0, 3, 1)),
                                   ((5, 7, 3), (1, 0, 2)), ((33, 17, 40), (2, 1, 0)),
-                                  ((16, 16, 16, 16, 16), (0, 1, 3, 2, 4))])
+                                  ((16, 16, 16, 16, 16), (0, 1, 3, 2, 4)),
+                                  # tensor-map path: two input runs, edge tiles, no batch
+                                  # axis, a batch axis of 2
+                                  ((6, 16, 5, 18, 32), (3, 0, 4, 2, 1)), ((48, 20, 100), (2, 1, 0)),
+                                  ((130, 72), (1, 0)), ((16, 2, 16), (2, 1, 0))])
 def test_permute_vs_numpy(qfx, case):
     shape, perm = case
     x = ri.random_complex(int(np.prod(shape)), seed=3)
