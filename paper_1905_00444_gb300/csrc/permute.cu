@@ -40,45 +40,64 @@ struct PermArgs {
 
 // ---- case 1: innermost axis shared -> contiguous rows ------------------------
 // Each block copies 4096 consecutive output elements (any number of rows): thread pairs
-// of elements stay in one row when D is even, so they move as 16-byte vectors.
+// of elements stay in one row when D is even, so they move as 16-byte vectors.  The
+// input offset of every row the block touches is computed once into shared memory
+// (the mixed-radix divisions per row, not per element).
 constexpr int kRowChunk = 4096;
+constexpr int kMaxChunkRows = kRowChunk / 8 + 2;   // D >= 8 for this kernel
 __global__ void __launch_bounds__(256) permute_rows_kernel(const float2* __restrict__ in,
                                                            float2* __restrict__ out,
                                                            const PermArgs a, int64_t total) {
+  __shared__ int64_t rowoff[kMaxChunkRows];
   const int64_t D = a.dim[a.rank - 1];
   const int64_t base = (int64_t)blockIdx.x * kRowChunk;
-  const bool even = (D % 2) == 0;
-#pragma unroll 2
-  for (int k = 0; k < kRowChunk / 512; ++k) {
-    const int64_t o = base + k * 512 + 2 * threadIdx.x;
-    if (o >= total) break;
-    int64_t row = o / D;
-    const int64_t col = o - row * D;
-    int64_t ib = 0;
+  const int64_t r0 = base / D;
+  const int64_t end = min(total, base + kRowChunk);
+  const int nrows = (int)((end - 1) / D - r0 + 1);
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+    int64_t row = r0 + i, ib = 0;
     for (int ax = a.rank - 2; ax >= 0; --ax) {
       const int64_t c = row % a.dim[ax];
       row /= a.dim[ax];
       ib += c * a.istr[ax];
     }
+    rowoff[i] = ib;
+  }
+  __syncthreads();
+  const int Di = (int)D, first = (int)(base - r0 * D);   // column of the block's first element
+  const bool even = (D % 2) == 0;
+#pragma unroll 2
+  for (int k = 0; k < kRowChunk / 512; ++k) {
+    const int lo = k * 512 + 2 * threadIdx.x;   // element offset inside the chunk
+    const int64_t o = base + lo;
+    if (o >= total) break;
+    const int rl = (first + lo) / Di, col = first + lo - rl * Di;
+    const int64_t ib = rowoff[rl];
     if (even && (ib % 2) == 0) {
       *reinterpret_cast<float4*>(out + o) = *reinterpret_cast<const float4*>(in + ib + col);
     } else {
       out[o] = in[ib + col];
-      if (o + 1 < total) {
-        if (col + 1 < D) {
-          out[o + 1] = in[ib + col + 1];
-        } else {   // next element starts the next row
-          int64_t r2 = (o + 1) / D, ib2 = 0;
-          for (int ax = a.rank - 2; ax >= 0; --ax) {
-            const int64_t c = r2 % a.dim[ax];
-            r2 /= a.dim[ax];
-            ib2 += c * a.istr[ax];
-          }
-          out[o + 1] = in[ib2];
-        }
-      }
+      if (o + 1 < total) out[o + 1] = col + 1 < Di ? in[ib + col + 1] : in[rowoff[rl + 1]];
     }
   }
+}
+
+// Rows shorter than 8 elements (or longer than 2^30): the mixed-radix divisions stay per
+// element.
+__global__ void __launch_bounds__(256) permute_short_rows_kernel(const float2* __restrict__ in,
+                                                                 float2* __restrict__ out,
+                                                                 const PermArgs a, int64_t total) {
+  const int64_t D = a.dim[a.rank - 1];
+  const int64_t o = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (o >= total) return;
+  int64_t row = o / D, ib = 0;
+  const int64_t col = o - row * D;
+  for (int ax = a.rank - 2; ax >= 0; --ax) {
+    const int64_t c = row % a.dim[ax];
+    row /= a.dim[ax];
+    ib += c * a.istr[ax];
+  }
+  out[o] = in[ib + col];
 }
 
 // ---- case 2: tiled transpose -------------------------------------------------
@@ -147,18 +166,6 @@ struct PermTma {
 };
 constexpr unsigned long long kPermWaitNs = 1000000000ull;   // 1 s per wait
 
-__device__ __forceinline__ bool perm_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long deadline = globaltimer() + kPermWaitNs;
-  while (!mbar_try(bar, parity)) {
-    if (globaltimer() > deadline) {
-      atomicOr(&g_perm_status, 1u);
-      return false;
-    }
-  }
-  return true;
-}
-
 struct TileMeta {
   int64_t obase;
   int na, nb;
@@ -197,47 +204,71 @@ __device__ __forceinline__ void perm_issue(const PermTma& a, const CUtensorMap* 
   tma_load_5d(dst, map, (int)(tb * TB), (int)(ta * TA), z[0], z[1], z[2], bar);
 }
 
+// Warps 0-3 consume tiles; lane 0 of warp 4 issues the copies NB tiles ahead, reusing a
+// buffer once its 128 consumers have released it.  Every wait is bounded; a timeout sets
+// the status word and makes the other roles give up too.
 template <int TA, int NB>
-__global__ void __launch_bounds__(128) permute_tma_kernel(const PermTma a, float2* __restrict__ out,
+__global__ void __launch_bounds__(160) permute_tma_kernel(const PermTma a, float2* __restrict__ out,
                                                           const __grid_constant__ CUtensorMap map) {
   constexpr int TB = 16;
   const int TILE = TB * TA * 8 * a.BZ, UNITS = 8 * (TA / 16) * a.BZ;
   extern __shared__ char smem_raw[];
   // 128-byte swizzled boxes must start on 1024-byte boundaries
   char* buf = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  __shared__ uint64_t full[NB];
+  __shared__ uint64_t full[NB], empty[NB];
   __shared__ TileMeta meta[NB];
-  __shared__ int s_ok;
+  __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
-    for (int b = 0; b < NB; ++b) mbar_init(smem_u32(&full[b]), 1);
+    for (int b = 0; b < NB; ++b) {
+      mbar_init(smem_u32(&full[b]), 1);
+      mbar_init(smem_u32(&empty[b]), 128);
+    }
+    abort_flag = 0;
     mbar_init_fence();
   }
   __syncthreads();
-  const int64_t stride = gridDim.x;
-  int issued[NB];
-  if (tid == 0) {
-    for (int b = 0; b < NB; ++b) {
-      issued[b] = 0;
-      const int64_t t = blockIdx.x + b * stride;
-      if (t < a.total) {
-        perm_issue<TA>(a, &map, t, smem_u32(buf + b * TILE), smem_u32(&full[b]), &meta[b]);
-        issued[b] = 1;
+  volatile int* abort = &abort_flag;
+  auto wait = [&](uint32_t bar, uint32_t parity) -> bool {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long deadline = globaltimer() + kPermWaitNs;
+    while (!mbar_try(bar, parity)) {
+      if (*abort) return false;
+      if (globaltimer() > deadline) {
+        *abort = 1;
+        atomicOr(&g_perm_status, 1u);
+        return false;
       }
     }
+    return true;
+  };
+  const int64_t stride = gridDim.x;
+  if (warp == 4) {
+    if (lane == 0) {
+      int64_t k = 0, issued = 0;
+      for (int64_t t = blockIdx.x; t < a.total; t += stride, ++k) {
+        const int b = (int)(k % NB);
+        if (k >= NB && !wait(smem_u32(&empty[b]), (uint32_t)((k / NB - 1) & 1))) break;
+        perm_issue<TA>(a, &map, t, smem_u32(buf + b * TILE), smem_u32(&full[b]), &meta[b]);
+        issued = k + 1;
+      }
+      // copies still in flight must land before the block exits
+      for (int64_t i = (issued > NB ? issued - NB : 0); i < issued; ++i) {
+        const int b = (int)(i % NB);
+        const unsigned long long deadline = globaltimer() + kPermWaitNs;
+        while (!mbar_try(smem_u32(&full[b]), (uint32_t)((i / NB) & 1)) && globaltimer() < deadline) {
+        }
+      }
+    }
+    return;
   }
+  const int ia_lo = lane & 15, h = lane >> 4;
   int64_t k = 0;
-  bool ok = true;
   for (int64_t t = blockIdx.x; t < a.total; t += stride, ++k) {
     const int b = (int)(k % NB);
-    const uint32_t par = (uint32_t)((k / NB) & 1);
-    if (tid == 0) s_ok = perm_wait(smem_u32(&full[b]), par) ? 1 : 0;
-    __syncthreads();
-    if (!s_ok) { ok = false; break; }   // uniform across the block
-    mbar_try(smem_u32(&full[b]), par);   // this thread's own acquire of the completed phase
+    if (!wait(smem_u32(&full[b]), (uint32_t)((k / NB) & 1))) break;
     const TileMeta m = meta[b];
     const char* tile = buf + b * TILE;
-    const int ia_lo = lane & 15, h = lane >> 4;
     for (int u = warp; u < UNITS; u += 4) {
       const int c = u & 7, iz = (u >> 3) / (TA / 16), ia = ((u >> 3) % (TA / 16)) * 16 + ia_lo, ib = 2 * c + h;
       // row (iz, ia) of the box is 128 bytes of lb; its 16-byte chunk c sits at
@@ -247,24 +278,7 @@ __global__ void __launch_bounds__(128) permute_tma_kernel(const PermTma a, float
     }
     // the next copy into this buffer goes through the async proxy: order the reads first
     fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      const int64_t tn = t + NB * stride;
-      if (tn < a.total) {
-        perm_issue<TA>(a, &map, tn, smem_u32(buf + b * TILE), smem_u32(&full[b]), &meta[b]);
-        ++issued[b];
-      }
-    }
-  }
-  if (!ok && tid == 0) {
-    // copies still in flight must land before the block exits
-    for (int b = 0; b < NB; ++b)
-      if (issued[b] > 0) {
-        const uint32_t par = (uint32_t)((issued[b] - 1) & 1);
-        const unsigned long long deadline = globaltimer() + kPermWaitNs;
-        while (!mbar_try(smem_u32(&full[b]), par) && globaltimer() < deadline) {
-        }
-      }
+    mbar_arrive(smem_u32(&empty[b]));
   }
 }
 
@@ -362,9 +376,12 @@ int launch_perm_tma(const PermTma& a, const CUtensorMap& map, float2* out, cudaS
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t want = (int64_t)(sms > 0 ? sms : 1) * 4;
+  // as many blocks per SM as 220 KB of shared memory holds, at most 8
+  int per_sm = (int)((220u << 10) / (smem + 512));
+  per_sm = per_sm < 1 ? 1 : per_sm > 8 ? 8 : per_sm;
+  const int64_t want = (int64_t)(sms > 0 ? sms : 1) * per_sm;
   const unsigned grid = (unsigned)(a.total < want ? a.total : want);
-  permute_tma_kernel<TA, NB><<<grid, 128, smem, st>>>(a, out, map);
+  permute_tma_kernel<TA, NB><<<grid, 160, smem, st>>>(a, out, map);
   return (int)cudaGetLastError();
 }
 }  // namespace
@@ -401,9 +418,15 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
   const float2* src = (const float2*)in;
   float2* dst = (float2*)out;
   if (a.istr[fr - 1] == 1) {
-    const int64_t blocks = (total + kRowChunk - 1) / kRowChunk;
-    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
-    permute_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, a, total);
+    if (a.dim[fr - 1] >= 8 && a.dim[fr - 1] < (int64_t(1) << 30)) {
+      const int64_t blocks = (total + kRowChunk - 1) / kRowChunk;
+      if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
+      permute_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, a, total);
+    } else {
+      const int64_t blocks = (total + 255) / 256;
+      if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
+      permute_short_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, a, total);
+    }
   } else {
     a.la = fr - 1;
     a.lb = -1;
