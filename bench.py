@@ -373,17 +373,18 @@ BATCH_MIX_SMALL = [  # many tiny items: launch overhead dominates per-item execu
     (5, 5, 24, 1 << 30, 1024, "x1"),
 ]
 BATCH_MIX = [  # (rows, cols, depth, per-item cap bytes, items, kind)
-    (6, 6, 24, 1 << 30, 256, "x1"),       # bond dim 2^3, whole item per x1
-    (7, 7, 24, 1 << 30, 128, "x1"),       # 2^3
-    (8, 8, 24, 256 << 20, 96, "slice"),   # 2^3, seeded sample of slices (path subsampling)
-    (7, 7, 32, 1 << 30, 32, "slice"),     # 2^4
+    (6, 6, 24, 1 << 30, 171, "x1"),       # bond dim 2^3, whole item per x1
+    (7, 7, 32, 1 << 30, 171, "slice"),    # 2^4, seeded sample of slices (path subsampling)
+    (8, 8, 32, 2 << 30, 166, "slice"),    # 2^4; the line sweep needs a 2 GiB cap (2^57 slices)
+    (7, 7, 40, 8 << 30, 4, "slice"),      # 2^5; an 8 GiB cap (2^59 slices), 4.6e13 flop each
 ]
 
 
 def run_batch(args):
     """512 work items of uneven shapes from mixed grids, |x2| = 8 (256 amplitudes per
     item): one persistent launch replayed from a CUDA graph vs one qfx_amplitudes call
-    per item (each its own fold, step and accumulate launches)."""
+    per item (each its own fold, step and accumulate launches).  The 512-item mix costs
+    ~1.4e15 flop per batch, so it times at most 2 batches after 1 warm-up."""
     import torch
     import paper_1905_00444_gb300 as qfx
     dev = torch.device("cuda", 0)
@@ -393,6 +394,7 @@ def run_batch(args):
     mix = BATCH_MIX_SMALL if args.workload == "batch_small" else BATCH_MIX
     n_open = 4 if args.workload == "batch_small" else 8
     for (r, c, d, cap, count, kind) in mix:
+        n0 = len(items)
         circ = qfx.Circuit(ri.rqc(r, c, d, seed=r * 10 + d))
         plan = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap)
         if not args.no_autotune:
@@ -406,8 +408,13 @@ def run_batch(args):
             x1 = torch.tensor(ri.random_bitstrings(r * c, 1, seed=r + d).view(np.int64), device=dev)
             for sl in sorted(set(int(v) for v in rng.integers(0, plan.n_slices, size=count))):
                 items.append((plan, x1, sl, sl + 1))
-        flops += plan.stats["flops_per_item"] * count
-    batch = qfx.Batch(items, slots=16)
+        flops += plan.stats["flops_per_item"] * (len(items) - n0)
+    if args.workload == "batch":
+        args.steps, args.warmup = min(args.steps, 2), 1
+    # slots hold the largest item; keep the batch workspace under ~96 GiB
+    block = max(p.workspace_bytes(1) for p, _, _, _ in items)
+    slots = int(max(2, min(16, (96 << 30) // block)))
+    batch = qfx.Batch(items, slots=slots)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         for _ in range(max(1, args.warmup)):
@@ -443,9 +450,10 @@ def run_batch(args):
     t_items = e0.elapsed_time(e1) / 1e3 / args.steps
     per_item_launches = (qfx.launch_count() - l1) // args.steps
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
-    desc = ("batch of 512 work items: 256 x 6x6x(1+24+1), 128 x 7x7x(1+24+1) x1 batches; "
-            "96 sampled slices of 8x8x(1+24+1) (256 MiB cap), 32 of 7x7x(1+32+1) (1 GiB cap); "
-            "|x2| = 8; FP32 SIMT tiles") if args.workload == "batch" else (
+    desc = ("batch of 512 work items: 171 x 6x6x(1+24+1) x1 batches (bond dim 2^3); sampled "
+            "slices: 171 of 7x7x(1+32+1) (1 GiB cap), 166 of 8x8x(1+32+1) (2 GiB cap), both "
+            "bond dim 2^4, and 4 of 7x7x(1+40+1) (8 GiB cap, bond dim 2^5); |x2| = 8; "
+            "FP32 SIMT tiles") if args.workload == "batch" else (
             "batch of 4096 small work items: 2048 x 4x4x(1+16+1), 1024 x 4x5x(1+16+1), "
             "1024 x 5x5x(1+24+1) x1 batches; |x2| = 4; FP32 SIMT tiles")
     print(json.dumps({

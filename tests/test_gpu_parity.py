@@ -93,7 +93,7 @@ def test_4x4x16_open_sites_anywhere(qfx):
 # --- shapes: non-square grids, lines, one site, shallow circuits ---------------------
 
 @pytest.mark.parametrize("shape", [(3, 5, 16), (5, 3, 16), (2, 6, 24), (1, 7, 8), (6, 1, 8),
-                                   (1, 1, 4), (2, 2, 3), (4, 5, 24), (3, 3, 40)])
+                                   (1, 1, 4), (2, 2, 3), (4, 5, 24), (3, 3, 40), (4, 4, 40)])
 def test_shapes_vs_statevector(qfx, shape):
     rows, cols, d = shape
     c = ri.rqc(rows, cols, d, seed=rows + cols + d)
