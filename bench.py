@@ -393,6 +393,7 @@ def run_batch(args):
     cache = os.path.join("/tmp", "qfx_autotune_batch.json")
     mix = BATCH_MIX_SMALL if args.workload == "batch_small" else BATCH_MIX
     n_open = 4 if args.workload == "batch_small" else 8
+    tc_plan, nq = {}, []   # split-precision twin of each plan; qubits per item
     for (r, c, d, cap, count, kind) in mix:
         n0 = len(items)
         circ = qfx.Circuit(ri.rqc(r, c, d, seed=r * 10 + d))
@@ -409,6 +410,9 @@ def run_batch(args):
             for sl in sorted(set(int(v) for v in rng.integers(0, plan.n_slices, size=count))):
                 items.append((plan, x1, sl, sl + 1))
         flops += plan.stats["flops_per_item"] * (len(items) - n0)
+        if args.workload == "batch":
+            tc_plan[id(plan)] = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap, precision="bf16x3")
+        nq += [r * c] * (len(items) - n0)
     if args.workload == "batch":
         args.steps, args.warmup = min(args.steps, 2), 1
     # slots hold the largest item; keep the batch workspace under ~96 GiB
@@ -450,6 +454,31 @@ def run_batch(args):
     t_items = e0.elapsed_time(e1) / 1e3 / args.steps
     per_item_launches = (qfx.launch_count() - l1) // args.steps
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    tc_line = None
+    if args.workload == "batch":
+        # the same items with the steps on the tensor cores (BF16x3, default accumulation)
+        tc_items = [(tc_plan[id(p)], x1, sb, se) for p, x1, sb, se in items]
+        ws_tc = torch.empty(max(p.workspace_bytes(1) for p, _, _, _ in tc_items), dtype=torch.uint8, device=dev)
+        outs_tc = [torch.empty_like(o) for o in ref]
+        for (plan, x1, sb, se), o in zip(tc_items, outs_tc):
+            qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws_tc, out=o)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(args.steps):
+            for (plan, x1, sb, se), o in zip(tc_items, outs_tc):
+                qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws_tc, out=o)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        qfx.sync()
+        t_tc = e0.elapsed_time(e1) / 1e3 / args.steps
+        worst = 0.0
+        for a, b, n in zip(outs_tc, ref, nq):
+            fl = 2.0 ** (-n / 2)
+            worst = max(worst, float((torch.abs(a - b) / torch.clamp(torch.abs(b), min=fl)).max()))
+        tc_line = {"value": flops / t_tc / 1e12, "ms_per_batch": 1e3 * t_tc,
+                   "max_rel_diff_vs_fp32": worst,
+                   "note": "per-item qfx_amplitudes launches with BF16x3 plans; per-amplitude "
+                           "difference to the FP32 results, floor 2^(-n/2)"}
     desc = ("batch of 512 work items: 171 x 6x6x(1+24+1) x1 batches (bond dim 2^3); sampled "
             "slices: 171 of 7x7x(1+32+1) (1 GiB cap), 166 of 8x8x(1+32+1) (2 GiB cap), both "
             "bond dim 2^4, and 4 of 7x7x(1+40+1) (8 GiB cap, bond dim 2^5); |x2| = 8; "
@@ -465,6 +494,7 @@ def run_batch(args):
         "per_item_launches": {"value": flops / t_items / 1e12, "ms_per_batch": 1e3 * t_items,
                               "items_per_s": len(items) / t_items, "kernel_launches": per_item_launches},
         "identical_results": bool(same), "flops_per_batch": flops, "n_items": len(items),
+        "bf16x3_per_item_launches": tc_line,
         "autotuned": not args.no_autotune}), flush=True)
     return 0
 
