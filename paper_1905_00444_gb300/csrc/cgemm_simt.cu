@@ -11,16 +11,16 @@ namespace qfx {
 namespace {
 using namespace simt;
 
-template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES>
-__global__ void __launch_bounds__(256) cgemm_step_kernel(const StepArgs a) {
+template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES, int NTH>
+__global__ void __launch_bounds__(NTH) cgemm_step_kernel(const StepArgs a) {
   extern __shared__ float4 smem_raw[];
-  cgemm_tile<BM, BJ, TM, TJ, KMODE, STAGES>(a, blockIdx.x, blockIdx.y, smem_raw);
+  cgemm_tile<BM, BJ, TM, TJ, KMODE, STAGES, NTH>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES>
+template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES, int NTH = 256>
 int launch_cfg(const StepArgs& a, int batch, cudaStream_t stream) {
-  using C_ = Cfg<BM, BJ, TM, TJ, KMODE, STAGES>;
-  auto kern = cgemm_step_kernel<BM, BJ, TM, TJ, KMODE, STAGES>;
+  using C_ = Cfg<BM, BJ, TM, TJ, KMODE, STAGES, NTH>;
+  auto kern = cgemm_step_kernel<BM, BJ, TM, TJ, KMODE, STAGES, NTH>;
   static int attr_done[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -34,7 +34,7 @@ int launch_cfg(const StepArgs& a, int batch, cudaStream_t stream) {
   const int64_t JT = (a.J + BJ - 1) / BJ;
   const int64_t blocks = NT * JT;
   if (blocks > 0x7fffffffLL || batch > 65535) return (int)cudaErrorInvalidConfiguration;
-  kern<<<dim3((unsigned)blocks, batch), 256, C_::SMEM, stream>>>(a);
+  kern<<<dim3((unsigned)blocks, batch), NTH, C_::SMEM, stream>>>(a);
   count_launch();
   return (int)cudaGetLastError();
 }

@@ -8,7 +8,8 @@
 // counts 8*N*J*K flops; each complex multiply-add is 4 real FMAs (the paper's complex
 // FP32 CGEMM, without tensor cores).
 //
-// Tiling: one CTA computes BM x BJ outputs with 256 threads, each thread TM x TJ; the
+// Tiling: one CTA computes BM x BJ outputs with NTH threads (256 unless a variant says
+// otherwise), each thread TM x TJ; the
 // k loop moves BK = 8 slabs of S and B through a STAGES-deep cp.async ring in shared
 // memory.  Column fragments are read as 2-complex (16-byte) vectors spaced so that 8
 // consecutive lanes cover 128 contiguous bytes (no bank conflicts); row fragments are
@@ -45,24 +46,26 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 constexpr int BK = 8;
 
-template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES>
+template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES, int NTH = 256>
 struct Cfg {
   static constexpr int TYN = BM / TM, TXN = BJ / TJ;
   static constexpr int LDA = BM + 2, LDB = BJ + 2;
-  static constexpr int A_IT = (BK * BM + 255) / 256;
-  static constexpr int B_IT = KMODE ? (BK * BJ) / 256 : (BK * BJ) / 512;
+  static constexpr int A_IT = (BK * BM + NTH - 1) / NTH;
+  static constexpr int B_IT = KMODE ? (BK * BJ) / NTH : (BK * BJ) / (2 * NTH);
   static constexpr size_t SMEM = (size_t)STAGES * BK * (LDA + LDB) * sizeof(float2);
-  static_assert(TYN * TXN == 256, "256 threads");
+  static_assert(TYN * TXN == NTH, "one thread per TM x TJ outputs");
   static_assert(TM % 2 == 0 && TJ % 2 == 0, "even thread tiles");
-  static_assert(KMODE ? (BK * BJ) % 256 == 0 : (BK * BJ) % 512 == 0, "B loader coverage");
+  static_assert(KMODE ? (BK * BJ) % NTH == 0 : (BK * BJ) % (2 * NTH) == 0, "B loader coverage");
 };
 
 // One BM x BJ output tile of the step; `tile` enumerates (n tile, j tile) with the n tile
-// fastest, `item` selects the batch entry.  256 threads; `smem_raw` holds Cfg::SMEM bytes.
-template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES>
+// fastest, `item` selects the batch entry.  NTH threads; `smem_raw` holds Cfg::SMEM bytes.
+// Every output accumulates its k terms in the same order whatever the tile shape, so all
+// variants give bit-identical results.
+template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES, int NTH = 256>
 __device__ __forceinline__ void cgemm_tile(const StepArgs& a, int64_t tile, int64_t item,
                                            float4* smem_raw) {
-  using C_ = Cfg<BM, BJ, TM, TJ, KMODE, STAGES>;
+  using C_ = Cfg<BM, BJ, TM, TJ, KMODE, STAGES, NTH>;
   constexpr int TXN = C_::TXN, LDA = C_::LDA, LDB = C_::LDB;
   float2* As = reinterpret_cast<float2*>(smem_raw);
   float2* Bs = As + STAGES * BK * LDA;
@@ -82,7 +85,7 @@ __device__ __forceinline__ void cgemm_tile(const StepArgs& a, int64_t tile, int6
   int bkk[C_::B_IT], bjj[C_::B_IT];
 #pragma unroll
   for (int i = 0; i < C_::B_IT; ++i) {
-    const int v = tid + i * 256;
+    const int v = tid + i * NTH;
     if (KMODE) { bkk[i] = v % BK; bjj[i] = v / BK; }
     else       { bkk[i] = v / (BJ / 2); bjj[i] = (v % (BJ / 2)) * 2; }
     const int64_t j = j0 + bjj[i];
@@ -93,7 +96,7 @@ __device__ __forceinline__ void cgemm_tile(const StepArgs& a, int64_t tile, int6
     const int64_t k0 = kt * BK;
 #pragma unroll
     for (int i = 0; i < C_::A_IT; ++i) {
-      const int e = tid + i * 256;
+      const int e = tid + i * NTH;
       if (e < BK * BM) {
         const int kk = e / BM, m = e % BM;
         const int64_t k = k0 + kk, n = n0 + m;
