@@ -275,8 +275,9 @@ qfx_status qfx_sync(void* stream);
 /* One contraction step of the TTGT form (Sec. III.E), for tests and microbenchmarks:
  * C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] * B[p][k][s], complex64, all device pointers,
  * 16-byte aligned, no aliasing.  `variant` < 0 lets the library choose (FP32 only).
- * Tensor-core precisions run on tcgen05 when N % 16 == 0, N <= 256, K a multiple of the
- * term's k step (16 for BF16x3, 8 for TF32x3) and P*Sd >= 128, otherwise on the FP32
+ * Tensor-core precisions run on tcgen05 when N % 16 == 0 and N <= 128 or a multiple of 128
+ * (fast accumulation: N <= 256 or a multiple of 256), K a multiple of the term's k step
+ * (16 for BF16x3 and BF16x2, 8 for TF32x3) and P*Sd >= 128, otherwise on the FP32
  * path; they need `scratch` of qfx_step_scratch_bytes(K, N, precision) bytes, 256-byte
  * aligned (NULL is fine for FP32).  Variant 12 selects fast accumulation (see
  * QFX_TC_FAST_ACCUMULATION) for a tensor-core step; variant 13 keeps the default tile but

@@ -676,8 +676,10 @@ int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_str
 }  // namespace
 
 bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags) {
-  // default tiles are 128 columns wide (N <= 128 or exactly two tiles); fast ones up to 256
-  const bool n_ok = N % 16 == 0 && ((flags & kTcFast) ? N <= 256 : (N <= 128 || N == 256));
+  // default tiles are 128 columns wide (N <= 128 or whole 128-column tiles); fast ones
+  // 256 (N <= 256 or whole 256-column tiles)
+  const int64_t nt = (flags & kTcFast) ? 256 : 128;
+  const bool n_ok = N % 16 == 0 && (N <= nt || N % nt == 0);
   if (precision == QFX_PREC_C3M_BF16X3 || precision == QFX_PREC_C3M_BF16X2)
     return n_ok && K % 16 == 0 && J >= kRows;
   if (precision == QFX_PREC_C3M_TF32X3) return n_ok && K % 8 == 0 && J >= kRows;

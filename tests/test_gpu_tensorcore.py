@@ -38,7 +38,8 @@ def step_ref(S, B, P, K, N, NL, Sd):
                                    (3, 64, 64, 32, 64), (2000, 16, 16, 16, 1),
                                    (1, 32, 48, 48, 300), (5, 256, 32, 16, 40),
                                    (2, 48, 112, 112, 200), (1, 16, 240, 48, 136),
-                                   (77, 32, 32, 32, 2), (3, 48, 64, 64, 128)])
+                                   (77, 32, 32, 32, 2), (3, 48, 64, 64, 128),
+                                   (2, 32, 512, 512, 128), (1, 16, 1024, 256, 256), (40, 32, 768, 384, 4)])
 def test_step_vs_oracle(qfx, prec, shape, fast):
     P, K, N, NL, Sd = shape
     S = ri.random_complex((K, N), seed=3)
