@@ -411,7 +411,12 @@ def run_batch(args):
                 items.append((plan, x1, sl, sl + 1))
         flops += plan.stats["flops_per_item"] * (len(items) - n0)
         if args.workload == "batch":
-            tc_plan[id(plan)] = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap, precision="bf16x3")
+            tp = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap, precision="bf16x3")
+            if not args.no_autotune:   # tensor cores or FP32 tiles, per step shape, by timing
+                qfx.autotune(tp, cache)
+                tp = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap, precision="bf16x3",
+                              autotune_cache=cache)
+            tc_plan[id(plan)] = tp
         nq += [r * c] * (len(items) - n0)
     if args.workload == "batch":
         args.steps, args.warmup = min(args.steps, 2), 1
@@ -477,7 +482,8 @@ def run_batch(args):
             worst = max(worst, float((torch.abs(a - b) / torch.clamp(torch.abs(b), min=fl)).max()))
         tc_line = {"value": flops / t_tc / 1e12, "ms_per_batch": 1e3 * t_tc,
                    "max_rel_diff_vs_fp32": worst,
-                   "note": "per-item qfx_amplitudes launches with BF16x3 plans; per-amplitude "
+                   "note": "per-item qfx_amplitudes launches with BF16x3 plans (autotuned: "
+                           "tensor cores or FP32 tiles per step shape); per-amplitude "
                            "difference to the FP32 results, floor 2^(-n/2)"}
     desc = ("batch of 512 work items: 171 x 6x6x(1+24+1) x1 batches (bond dim 2^3); sampled "
             "slices: 171 of 7x7x(1+32+1) (1 GiB cap), 166 of 8x8x(1+32+1) (2 GiB cap), both "

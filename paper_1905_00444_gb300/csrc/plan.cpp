@@ -274,17 +274,21 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
 
     // steps
     p->steps = sim.steps;
-    uint64_t simage = 0;
     for (auto& st : p->steps) {
       st.variant = qfx::pick_variant(st.N, st.Sd);
-      if (&st != &p->steps[0] && qfx::tc_eligible(p->precision, st.K, st.N, st.P * st.Sd, p->tc_flags)) {
-        st.variant = p->precision == QFX_PREC_C3M_BF16X3   ? qfx::kVariantTcBf16
-                     : p->precision == QFX_PREC_C3M_BF16X2 ? qfx::kVariantTcBf16x2
-                                                           : qfx::kVariantTcTf32;
-        simage = std::max(simage, qfx::tc_scratch_bytes(p->precision, st.K, st.N));
-      }
+      // Steps with fewer than 32 columns n stay on the FP32 tiles (unless the autotuner
+      // measured otherwise): the tensor-core tile splits every row of B into term planes
+      // for only N outputs, and at N = 16 that split bounds it below the FP32 tiles
+      // (measured ~22 against ~30 TFLOP/s).
+      if (&st != &p->steps[0] && st.N >= 32 &&
+          qfx::tc_eligible(p->precision, st.K, st.N, st.P * st.Sd, p->tc_flags))
+        st.variant = qfx::tc_variant_of(p->precision);
     }
     if (o->autotune_cache) qfx::apply_autotune_cache(p, o->autotune_cache);
+    uint64_t simage = 0;   // site image of the tensor-core steps, after the cache's choices
+    for (auto& st : p->steps)
+      if (st.variant >= qfx::kVariantTcBf16)
+        simage = std::max(simage, qfx::tc_scratch_bytes(p->precision, st.K, st.N));
     p->max_elements = 1;
     p->flops_per_item = sim.flops;
     p->bytes_per_item = sim.bytes;

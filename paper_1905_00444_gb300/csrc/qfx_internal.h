@@ -174,6 +174,7 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
                    const int32_t* perm, void* stream);
 
 void apply_autotune_cache(qfx_plan* p, const char* path);
+int tc_variant_of(int precision);   // plan-step variant marking a tensor-core step
 
 // device tables of a plan (uploaded once per device)
 qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out);
