@@ -39,7 +39,7 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the
 # same kernel build on the small case (2^18 columns, 1.028e9 B) scaled by the columns of a
 # full launch (2^24): profiles/cgemm_step_simt_dominant_step_ncu_full.md.
-TRAFFIC = {"full": 1.028e9 * 64, "small": None}
+TRAFFIC = {"full": 1.0291e9 * 64, "small": None}
 
 
 def workload_desc(w):
