@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -104,6 +105,19 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "processor\t: 0")) and ":" in ln:
+                    v = ln.split(":", 1)[1].strip()
+                    if v and not v.isdigit():
+                        return v
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -296,7 +310,7 @@ def run_qfx(args):
             "value": rate, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
             "sample": f"oracle.primitives.contract_step (numpy complex128 einsum, one thread) on "
                       f"2^14 of the 2^24 columns of the dominant step (K=N=256), {reps} reps in "
-                      f"{dt:.1f} s; host has {os.cpu_count()} cores",
+                      f"{dt:.1f} s; host has {os.cpu_count()} cores ({cpu_model()})",
             "amplitudes_per_s": rate * 1e12 / flops_step * amps_step}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -353,12 +367,17 @@ def run_mode(qfx, torch, circ, w, mode, x1_dev, args, dev, stream):
     peak = peaks["bf16_tflops_sustained"] * TENSOR_PEAK_RATIO[mode]
     burst = peaks["bf16_tflops"] * TENSOR_PEAK_RATIO[mode]
     achieved = counted * TENSOR_FACTOR[mode]
+    probe = qfx.tensor_peak(mode, 1 << 16)   # this kind's MMA rate, measured here
     return {"value": flops * args.steps / el / 1e12, "unit": "TFLOP/s",
             "amplitudes_per_s": (1 << w["n_open"]) * args.steps / el,
             "ms_per_step": 1e3 * el / args.steps,
             "largest_step_counted_tflops": counted,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "frac_of_burst": achieved / burst, "traffic": None,
+                         "tensor_probe": {"tflops": probe, "frac": achieved / probe,
+                                          "what": "qfx_tensor_peak: back-to-back 128x256 MMAs of "
+                                                  "this operand kind from shared memory, one CTA "
+                                                  "per SM"},
                          "note": f"tensor-pipe flops = {TENSOR_FACTOR[mode]:g} x counted; peak = "
                                  f"{src} bf16 sustained x {TENSOR_PEAK_RATIO[mode]} (the sustained "
                                  f"GEMM ran power-capped; this kernel is bound by shared-memory "
@@ -615,8 +634,26 @@ def run_kstep(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     flops = 8.0 * P * K * N * Sd
-    print(json.dumps({"workload": "dominant step (P,K,N,Sd)=(1,256,256,2^18)", "precision": args.precision, "ms": ms,
-                      "tflops": flops / ms / 1e9, "steps": args.steps}), flush=True)
+    line = {"workload": "dominant step (P,K,N,Sd)=(1,256,256,2^18)", "precision": args.precision, "ms": ms,
+            "tflops": flops / ms / 1e9, "steps": args.steps}
+    if args.precision == "fp32":
+        # library comparator, run only: cuBLAS complex64 GEMM (torch.matmul, TF32 off) on
+        # the same product, C[n][s] = sum_k S[k][n] B[k][s] (P = 1)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        St, Bm = S.view(K, N).t(), B.view(K, Sd)
+        Cm = torch.empty(N, Sd, dtype=torch.complex64, device="cuda")
+        for _ in range(args.warmup):
+            torch.matmul(St, Bm, out=Cm)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            torch.matmul(St, Bm, out=Cm)
+        e1.record()
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1) / args.steps
+        rel = (torch.linalg.vector_norm(Cm.reshape(-1) - C) / torch.linalg.vector_norm(Cm)).item()
+        line["cublas_cgemm"] = {"ms": cms, "tflops": flops / cms / 1e9, "rel_diff_to_qfx": rel}
+    print(json.dumps(line), flush=True)
     return 0
 
 

@@ -272,6 +272,14 @@ qfx_status qfx_autotune(const qfx_plan* p, const char* cache_path, void* workspa
  * tensor-core kernel that gave up a bounded wait (about 1 s) as QFX_ETIMEOUT. */
 qfx_status qfx_sync(void* stream);
 
+/* Measured tensor-core peak of a precision's operand kind (BF16 for the BF16 modes, TF32
+ * for TF32x3): one CTA per SM issues `mmas_per_sm` (>= 256, rounded up to a multiple of
+ * 256) back-to-back tcgen05.mma of M = 128, N = 256 and one K step from shared memory
+ * into TMEM; `*tflops` = dense flop/s of that kind (2 M N K per MMA) over the timed launch.
+ * Runs one warm-up launch and one timed launch on `stream` and synchronises.  Errors:
+ * QFX_EINVAL, QFX_ECUDA, QFX_ETIMEOUT. */
+qfx_status qfx_tensor_peak(int32_t precision, int64_t mmas_per_sm, double* tflops, void* stream);
+
 /* One contraction step of the TTGT form (Sec. III.E), for tests and microbenchmarks:
  * C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] * B[p][k][s], complex64, all device pointers,
  * 16-byte aligned, no aliasing.  `variant` < 0 lets the library choose (FP32 only).

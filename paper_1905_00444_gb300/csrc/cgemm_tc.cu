@@ -673,6 +673,113 @@ int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_str
   return (int)cudaGetLastError();
 }
 
+// ---- tensor-core rate probe -------------------------------------------------------
+// One CTA per SM (its shared-memory request leaves room for no second one) issues `iters`
+// MMAs of the mode's operand kind, M = 128, N = 256, one K step, from fixed pseudo-random
+// shared-memory operands into two alternating TMEM accumulators, committing every 256
+// MMAs.  The host times the launch: dense tensor flop/s of that kind as this code issues it.
+constexpr size_t kProbeSmem = 128 << 10;
+template <int MODE>
+__global__ void __launch_bounds__(128, 1) tc_probe_kernel(int64_t iters) {
+  extern __shared__ __align__(16) char probe_raw[];
+  char* sm = probe_raw + ((128u - (smem_u32(probe_raw) & 127u)) & 127u);
+  char* sA = sm;               // 128 rows x 32 B
+  char* sB = sm + kPlaneA;     // 256 rows x 32 B
+  __shared__ uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  // operands: 12 KB of small pseudo-random values of the mode's type
+  for (int i = tid; i < 3 * kPlaneA / 4; i += blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u + 0x9e3779b9u * (blockIdx.x + 1);
+    h ^= h >> 15;
+    const float x = (float)(h & 0xffff) * (1.0f / 65536.0f) - 0.5f;
+    uint32_t w;
+    if constexpr (Mode<MODE>::FMT == 1) {
+      const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+      w = b | (b << 16);
+    } else {
+      w = __float_as_uint(x) & 0xffffe000u;   // TF32: 10 explicit mantissa bits
+    }
+    reinterpret_cast<uint32_t*>(sm)[i] = w;
+  }
+  fence_async_smem();
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(smem_u32(&bars[0]), 1);
+    mbar_init(smem_u32(&bars[1]), 1);
+    mbar_init_fence();
+  }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (tid < 32) {
+    // warp-uniform loop; lane 0 issues 16 MMAs per iteration (a thread issuing one MMA per
+    // loop iteration kept the tensor pipe about half idle)
+    volatile int* abort = &abort_flag;
+    const uint64_t ad = smem_desc(smem_u32(sA)), bd = smem_desc(smem_u32(sB));
+    const uint32_t idesc = instr_desc<MODE>(256, false);
+    // commit groups of 256 MMAs alternate between two barriers (a barrier never has two
+    // commits outstanding); group g completes phase g / 2 of barrier g % 2
+    auto wait_group = [&](int64_t g) {
+      return mbar_wait(smem_u32(&bars[g & 1]), (uint32_t)((g >> 1) & 1), abort);
+    };
+    int64_t groups = 0;
+    bool ok = true;
+    for (int64_t i0 = 0; i0 < iters && ok; i0 += 16) {   // iters is a multiple of 256
+      if (tid == 0) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          mma<MODE>(tmem + (uint32_t)((u & 1) * 256), ad, bd, idesc, (i0 + u) >= 2 ? 1u : 0u);
+      }
+      if (((i0 + 15) & 255) == 255) {
+        if (tid == 0) mma_commit(smem_u32(&bars[groups & 1]));
+        __syncwarp();
+        if (groups > 0) ok = wait_group(groups - 1);   // at most two groups in flight
+        ++groups;
+      }
+    }
+    if (ok && groups > 0) wait_group(groups - 1);   // the last group covers every MMA
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid < 32) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+template <int MODE>
+int run_tc_probe(int64_t iters, double* tflops, cudaStream_t st) {
+  auto kern = tc_probe_kernel<MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProbeSmem);
+  if (e != cudaSuccess) return (int)e;
+  const int grid = num_sms();
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return (int)cudaErrorUnknown;
+  iters = (iters + 255) / 256 * 256;
+  kern<<<grid, 128, kProbeSmem, st>>>((iters / 8 + 255) / 256 * 256);   // warm-up
+  cudaEventRecord(e0, st);
+  kern<<<grid, 128, kProbeSmem, st>>>(iters);
+  cudaEventRecord(e1, st);
+  count_launch(2);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return (int)e;
+  const double flop_per_mma = 2.0 * kRows * 256 * Mode<MODE>::KS;
+  *tflops = (double)grid * (double)iters * flop_per_mma / (ms * 1e-3) / 1e12;
+  return 0;
+}
+
 }  // namespace
 
 bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags) {
@@ -717,6 +824,14 @@ int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_str
                                                              Sd, batch, scratch, scratch_stride, withhold, no_tma, st)
                 : launch_tc_mode<QFX_PREC_C3M_TF32X3, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, st);
+  return (int)cudaErrorInvalidValue;
+}
+
+int tc_probe(int precision, int64_t iters, double* tflops, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == QFX_PREC_C3M_BF16X3 || precision == QFX_PREC_C3M_BF16X2)
+    return run_tc_probe<QFX_PREC_C3M_BF16X3>(iters, tflops, st);
+  if (precision == QFX_PREC_C3M_TF32X3) return run_tc_probe<QFX_PREC_C3M_TF32X3>(iters, tflops, st);
   return (int)cudaErrorInvalidValue;
 }
 

@@ -168,6 +168,7 @@ int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_str
                    int flags = 0);
 
 int tc_take_status();     // reads and clears the tensor-core kernels' timeout flag
+int tc_probe(int precision, int64_t iters, double* tflops, void* stream);
 int batch_take_status();  // reads and clears the batch scheduler's timeout flag
 int perm_take_status();   // reads and clears the permute kernel's timeout flag
 int launch_permute(const void* in, void* out, int rank, const int64_t* shape,

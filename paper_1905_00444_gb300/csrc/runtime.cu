@@ -275,6 +275,18 @@ extern "C" qfx_status qfx_sync(void* stream) {
   return QFX_OK;
 }
 
+extern "C" qfx_status qfx_tensor_peak(int32_t precision, int64_t mmas_per_sm, double* tflops, void* stream) {
+  if (!tflops) return fail(QFX_EINVAL, "qfx_tensor_peak: NULL output");
+  if (precision <= QFX_PREC_FP32_SIMT || precision > QFX_PREC_C3M_BF16X2)
+    return fail(QFX_EINVAL, "qfx_tensor_peak: not a tensor-core precision");
+  if (mmas_per_sm < 256) return fail(QFX_EINVAL, "qfx_tensor_peak: mmas_per_sm < 256");
+  const int err = tc_probe(precision, mmas_per_sm, tflops, stream);
+  if (err) return cuda_fail(err, "qfx_tensor_peak");
+  const int tc = tc_take_status();
+  if (tc != 0) return fail(QFX_ETIMEOUT, "qfx_tensor_peak: a bounded wait expired");
+  return QFX_OK;
+}
+
 extern "C" uint64_t qfx_step_scratch_bytes(int64_t K, int64_t N, int32_t precision) {
   return tc_scratch_bytes(precision, K, N);
 }

@@ -92,6 +92,7 @@ def _declare(lib):
         "qfx_batch_destroy": (None, [vp]),
         "qfx_sync": (st, [vp]),
         "qfx_contract_step": (st, [vp, vp, vp, i64, i64, i64, i64, i64, i32, i32, vp, C.c_size_t, vp]),
+        "qfx_tensor_peak": (st, [i32, i64, C.POINTER(C.c_double), vp]),
         "qfx_step_scratch_bytes": (u64, [i64, i64, i32]),
         "qfx_permute": (st, [vp, vp, i32, C.POINTER(i64), C.POINTER(i32), vp]),
         "qfx_profile_enable": (st, [i32]),
@@ -352,6 +353,13 @@ def amplitudes_static(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Option
 
 def sync(stream=None):
     _check(lib.qfx_sync(_stream_ptr(stream)))
+
+
+def tensor_peak(precision: str, mmas_per_sm: int = 1 << 16, stream=None) -> float:
+    """Measured dense tensor-core TFLOP/s of a split mode's operand kind (see qfx.h)."""
+    out = C.c_double()
+    _check(lib.qfx_tensor_peak(PRECISIONS[precision], mmas_per_sm, C.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def step_scratch_bytes(K: int, N: int, precision: str = "fp32") -> int:

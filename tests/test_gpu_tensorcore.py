@@ -201,3 +201,17 @@ def test_bounded_wait_expires_and_context_survives(qfx):
     want = step_ref(S.cpu().numpy().reshape(K, N), B.cpu().numpy().reshape(P, K, Sd), P, K, N, NL, Sd)
     got = out.cpu().numpy().reshape(want.shape)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < STEP_BOUND["bf16x3"]
+
+
+def test_tensor_peak_probe(qfx):
+    """The tensor-core peak probe: BF16 and TF32 figures below the pipe's ceiling (152 SMs x
+    8192 dense BF16 flop per clock at <= 2.07 GHz = 2.58 PFLOP/s; TF32 half of that), and
+    TF32 about half of BF16 per flop (the nominal ratio)."""
+    bf = qfx.tensor_peak("bf16x3", 1 << 14)
+    tf = qfx.tensor_peak("tf32x3", 1 << 14)
+    qfx.sync()
+    print(f"probe: bf16 {bf:.0f} TFLOP/s, tf32 {tf:.0f} TFLOP/s")
+    assert 500 < bf < 2700 and 250 < tf < 1350
+    assert 0.35 < tf / bf < 0.65
+    with pytest.raises(qfx.QfxError):
+        qfx.tensor_peak("fp32")
