@@ -211,9 +211,14 @@ qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x1, int64_t 
 
 /* Batched execution (Sec. III.A: slices are independent paths; Sec. III.B: x1 batches).
  * Many work items -- every (slice, x1) of every listed item, of any mix of plans and
- * shapes -- run in ONE persistent kernel: a device task queue of fold chunks, scale
- * chunks, contraction-step tiles (FP32 tiles, each step's plan-chosen variant) and FP64
- * accumulations, with per-segment completion counters as dependencies and bounded waits.
+ * shapes -- run together:
+ * - plans whose steps are all FP32 tiles: in ONE persistent kernel, a device task queue
+ *   of fold chunks, scale chunks, contraction-step tiles (each step's plan-chosen variant)
+ *   and FP64 accumulations, with per-segment completion counters as dependencies and
+ *   bounded waits;
+ * - batches with any split-precision plan (tensor-core steps): as ONE CUDA graph built at
+ *   prepare time, every item's launch sequence on one of up to 16 parallel lanes, each
+ *   lane with its own workspace slot (`slots` = lanes).
  * Each batch item's `out` rows get the same values qfx_amplitudes would produce. */
 typedef struct {
   const qfx_plan* plan;
@@ -234,9 +239,10 @@ uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32_t n_items,
 qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_items, void* workspace,
                              size_t ws_bytes, qfx_batch** out, void* stream);
 
-/* Clears the queue counters and launches the persistent kernel: asynchronous, no
- * allocation and no host synchronisation, so it can be captured in a CUDA graph.  A
- * dependency wait that expires (5 s) is reported by qfx_sync as QFX_ETIMEOUT. */
+/* Clears the queue counters and launches the persistent kernel (or launches the batch's
+ * graph): asynchronous, no allocation and no host synchronisation, so it can itself be
+ * captured in a CUDA graph.  A dependency wait that expires (5 s) is reported by qfx_sync
+ * as QFX_ETIMEOUT. */
 qfx_status qfx_batch_run(const qfx_batch* b, void* stream);
 
 qfx_status qfx_batch_info(const qfx_batch* b, int64_t* n_work, int64_t* n_tasks, int64_t* slots);

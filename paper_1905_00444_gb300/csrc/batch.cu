@@ -240,6 +240,31 @@ __global__ void __launch_bounds__(kT, 1) batch_kernel(const BatchArgs a) {
 
 uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
+constexpr int64_t kGraphLanes = 16;
+
+}  // namespace
+
+// Whether any item's plan runs steps on the tensor cores (those batches use the graph
+// executor: the persistent scheduler's tasks are FP32 tiles).
+bool batch_has_tc(const qfx_batch_item* items, int32_t n_items) {
+  for (int i = 0; i < n_items; ++i)
+    for (const auto& sp : items[i].plan->steps)
+      if (sp.variant >= kVariantTcBf16) return true;
+  return false;
+}
+
+// Workspace of one graph lane: the header and block of one work item of the largest plan.
+uint64_t graph_lane_bytes(const qfx_batch_item* items, int32_t n_items) {
+  uint64_t lane = 0;
+  for (int i = 0; i < n_items; ++i) {
+    const qfx_plan* p = items[i].plan;
+    lane = std::max<uint64_t>(lane, a256(p->layout.header_per_item) + p->layout.item_bytes);
+  }
+  return a256(lane);
+}
+
+namespace {
+
 size_t batch_smem() {
   size_t m = 0;
 #define QFX_SZ(V, BM, BJ, TM, TJ, KM, ST) m = std::max(m, simt::Cfg<BM, BJ, TM, TJ, KM, ST>::SMEM);
@@ -282,13 +307,99 @@ struct qfx_batch {
   int grid = 0;
   size_t smem = 0;
   int64_t n_work = 0, slots = 0;
+  // batches with split-precision plans: one CUDA graph of per-item launch sequences
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_kernels = 0;
+  ~qfx_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
 };
 
 using namespace qfx;
 
+// Graph executor for batches with split-precision plans.  Every item's ordinary launch
+// sequence (qfx_amplitudes' fold, scale, steps, accumulation; one work item in flight) is
+// recorded on one of `lanes` streams forked from a capture stream, each lane with its own
+// workspace slot, and the lanes join again: one CUDA graph, replayed by qfx_batch_run.
+// Items on different lanes overlap; an item's own launches keep their order.
+static qfx_status prepare_graph(const qfx_batch_item* items, int32_t n_items,
+                                const std::vector<const DeviceTables*>& tabs,
+                                const std::map<const qfx_plan*, int>& plan_ix, void* workspace,
+                                size_t ws_bytes, qfx_batch** out) {
+  const uint64_t lane = graph_lane_bytes(items, n_items);
+  int64_t n_work = 0;
+  for (int i = 0; i < n_items; ++i) n_work += (items[i].slice_end - items[i].slice_begin) * items[i].n_batch;
+  const int64_t lanes = std::min<int64_t>({kGraphLanes, (int64_t)(ws_bytes / lane), (int64_t)n_items});
+  if (lanes < 1) return fail(QFX_ENOMEM, "qfx_batch_prepare: workspace smaller than one work item");
+  // kernel attributes are set before the capture (a captured launch must not be the first)
+  int err = tc_prepare_attributes();
+  if (!err) err = simt_prepare_attributes();
+  if (err) return cuda_fail(err, "qfx_batch_prepare: kernel attributes");
+  auto* B = new qfx_batch;
+  std::unique_ptr<qfx_batch> guard(B);
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> ls((size_t)lanes, nullptr);
+  std::vector<cudaEvent_t> ev((size_t)lanes + 1, nullptr);
+  auto release = [&]() {
+    for (auto& x : ls) if (x) cudaStreamDestroy(x);
+    for (auto& x : ev) if (x) cudaEventDestroy(x);
+    if (cap) cudaStreamDestroy(cap);
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  for (int64_t l = 0; l < lanes && e == cudaSuccess; ++l) e = cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking);
+  for (size_t l = 0; l < ev.size() && e == cudaSuccess; ++l) e = cudaEventCreateWithFlags(&ev[l], cudaEventDisableTiming);
+  if (e != cudaSuccess) { release(); return cuda_fail(e, "qfx_batch_prepare: streams"); }
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { release(); return cuda_fail(e, "qfx_batch_prepare: begin capture"); }
+  qfx_status st = QFX_OK;
+  e = cudaEventRecord(ev[lanes], cap);
+  for (int64_t l = 0; l < lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(ls[l], ev[lanes], 0);
+  if (e != cudaSuccess) st = cuda_fail(e, "qfx_batch_prepare: fork");
+  for (int i = 0; i < n_items && st == QFX_OK; ++i) {
+    const qfx_batch_item& it = items[i];
+    const int64_t l = i % lanes;
+    st = exec_amplitudes(it.plan, *tabs[plan_ix.at(it.plan)], it.x1, it.n_batch, it.slice_begin,
+                         it.slice_end, (char*)workspace + l * lane, 1, it.out, ls[l]);
+  }
+  for (int64_t l = 0; l < lanes && st == QFX_OK; ++l) {
+    e = cudaEventRecord(ev[l], ls[l]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev[l], 0);
+    if (e != cudaSuccess) st = cuda_fail(e, "qfx_batch_prepare: join");
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cap, &g);   // ends the capture in every case
+  release();
+  if (st != QFX_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "qfx_batch_prepare: capture"); }
+  B->graph = g;
+  e = cudaGraphInstantiate(&B->exec, g, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_prepare: graph instantiation");
+  size_t nn = 0;
+  e = cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+  if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_prepare: graph nodes");
+  int64_t kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  B->graph_kernels = kernels;
+  B->n_work = n_work;
+  B->slots = lanes;
+  B->args.n_tasks = (int64_t)nn;
+  *out = guard.release();
+  return QFX_OK;
+}
+
 extern "C" uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32_t n_items,
                                               int64_t slots) {
   if (!items || n_items < 1 || slots < 1) return 0;
+  for (int i = 0; i < n_items; ++i)
+    if (!items[i].plan) return 0;
+  if (qfx::batch_has_tc(items, n_items)) return (uint64_t)slots * qfx::graph_lane_bytes(items, n_items);
   uint64_t block = 0;
   int64_t segs_est = 0, work = 0;
   for (int i = 0; i < n_items; ++i) {
@@ -330,6 +441,8 @@ extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_i
       if (s != QFX_OK) return s;
       tabs.push_back(t);
     }
+    if (batch_has_tc(items, n_items))
+      return prepare_graph(items, n_items, tabs, plan_ix, workspace, ws_bytes, out);
     // work items, slice-major within each batch item
     struct W { int plan; int64_t b, sid; const qfx_batch_item* it; bool first; };
     std::vector<W> work;
@@ -518,6 +631,28 @@ extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_i
 extern "C" qfx_status qfx_batch_run(const qfx_batch* b, void* stream) {
   if (!b) return fail(QFX_EINVAL, "qfx_batch_run: NULL batch");
   cudaStream_t st = (cudaStream_t)stream;
+  if (b->exec) {   // graph executor
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_run: capture status");
+    if (cs == cudaStreamCaptureStatusActive) {
+      // inside a caller's capture: the batch graph becomes a child node of the captured graph
+      cudaGraph_t cg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* edges = nullptr;
+      size_t nd = 0;
+      cudaGraphNode_t node = nullptr;
+      e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &edges, &nd);
+      if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&node, cg, deps, nd, b->graph);
+      if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+      if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_run: adding the batch graph to a capture");
+    } else {
+      e = cudaGraphLaunch(b->exec, st);
+      if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_run: graph launch");
+    }
+    count_launch((int)b->graph_kernels);
+    return QFX_OK;
+  }
   cudaError_t e = cudaMemsetAsync(b->control, 0, b->control_bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->args.hdrs, 0, b->hdrs_bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_run: clearing counters");

@@ -17,19 +17,28 @@ __global__ void __launch_bounds__(NTH) cgemm_step_kernel(const StepArgs a) {
   cgemm_tile<BM, BJ, TM, TJ, KMODE, STAGES, NTH>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
+// Shared-memory opt-in of one tile kernel, once per device (also called ahead of a graph
+// capture, which must not be the first launch to set it).
 template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES, int NTH = 256>
-int launch_cfg(const StepArgs& a, int batch, cudaStream_t stream) {
+int ensure_attr() {
   using C_ = Cfg<BM, BJ, TM, TJ, KMODE, STAGES, NTH>;
-  auto kern = cgemm_step_kernel<BM, BJ, TM, TJ, KMODE, STAGES, NTH>;
   static int attr_done[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C_::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(cgemm_step_kernel<BM, BJ, TM, TJ, KMODE, STAGES, NTH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM);
     if (e != cudaSuccess) return (int)e;
     attr_done[dev] = 1;
   }
+  return 0;
+}
+
+template <int BM, int BJ, int TM, int TJ, bool KMODE, int STAGES, int NTH = 256>
+int launch_cfg(const StepArgs& a, int batch, cudaStream_t stream) {
+  using C_ = Cfg<BM, BJ, TM, TJ, KMODE, STAGES, NTH>;
+  auto kern = cgemm_step_kernel<BM, BJ, TM, TJ, KMODE, STAGES, NTH>;
+  if (int e = ensure_attr<BM, BJ, TM, TJ, KMODE, STAGES, NTH>()) return e;
   const int64_t NT = (a.N + BM - 1) / BM;
   const int64_t JT = (a.J + BJ - 1) / BJ;
   const int64_t blocks = NT * JT;
@@ -40,6 +49,14 @@ int launch_cfg(const StepArgs& a, int batch, cudaStream_t stream) {
 }
 
 }  // namespace
+
+int simt_prepare_attributes() {
+#define QFX_ATTR(V, BM, BJ, TM, TJ, KM, ST) \
+  if (int e = ensure_attr<BM, BJ, TM, TJ, KM, ST>()) return e;
+  QFX_SIMT_VARIANTS(QFX_ATTR)
+#undef QFX_ATTR
+  return 0;
+}
 
 // Tile variants (QFX_SIMT_VARIANTS): 0..4 stream B along s (JMODE), 5..9 load B along k.
 int pick_variant(int64_t N, int64_t Sd) {

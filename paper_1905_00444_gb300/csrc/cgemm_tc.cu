@@ -628,6 +628,23 @@ bool make_b_map(CUtensorMap* map, const void* B, int64_t b_stride, int batch, in
   return true;
 }
 
+// Shared-memory opt-in of one tensor-core kernel, once per device (also called ahead of a
+// graph capture).
+template <int MODE, bool SPLITACC>
+int ensure_tc_attr() {
+  using CF = TcCfg<MODE, SPLITACC>;
+  static int attr_done[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<MODE, SPLITACC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::smem(CF::NT_MAX));
+    if (e != cudaSuccess) return (int)e;
+    attr_done[dev] = 1;
+  }
+  return 0;
+}
+
 template <int MODE, bool SPLITACC>
 int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
                    int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
@@ -659,14 +676,7 @@ int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_str
   if (CF::NBUF > 0 && !no_tma)
     a.use_tma = make_b_map(&tmA, B, b_stride, batch, P, K, Sd, M_::KS, &a.box_s, &a.box_p) ? 1 : 0;
   auto kern = cgemm_tc_kernel<MODE, SPLITACC>;
-  static int attr_done[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !attr_done[dev]) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::smem(CF::NT_MAX));
-    if (e != cudaSuccess) return (int)e;
-    attr_done[dev] = 1;
-  }
+  if (int err = ensure_tc_attr<MODE, SPLITACC>()) return err;
   const int64_t grid = a.tiles < num_sms() ? a.tiles : num_sms();
   kern<<<(unsigned)grid, CF::THREADS, CF::smem(Nt), st>>>(a, tmA);
   count_launch();
@@ -833,6 +843,18 @@ int tc_probe(int precision, int64_t iters, double* tflops, void* stream) {
     return run_tc_probe<QFX_PREC_C3M_BF16X3>(iters, tflops, st);
   if (precision == QFX_PREC_C3M_TF32X3) return run_tc_probe<QFX_PREC_C3M_TF32X3>(iters, tflops, st);
   return (int)cudaErrorInvalidValue;
+}
+
+int tc_prepare_attributes() {
+  (void)tensor_map_encoder();   // resolve the driver entry point outside any capture
+  int e = 0;
+  if (!e) e = ensure_tc_attr<QFX_PREC_C3M_BF16X3, true>();
+  if (!e) e = ensure_tc_attr<QFX_PREC_C3M_BF16X3, false>();
+  if (!e) e = ensure_tc_attr<QFX_PREC_C3M_BF16X2, true>();
+  if (!e) e = ensure_tc_attr<QFX_PREC_C3M_BF16X2, false>();
+  if (!e) e = ensure_tc_attr<QFX_PREC_C3M_TF32X3, true>();
+  if (!e) e = ensure_tc_attr<QFX_PREC_C3M_TF32X3, false>();
+  return e;
 }
 
 int tc_take_status() {

@@ -65,6 +65,9 @@ bool profile_on() { return g_prof_on; }
 void profile_begin(void* stream, int* slot) {
   *slot = -1;
   if (!g_prof_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return;   // launches recorded into a graph are not timed here
   std::lock_guard<std::mutex> lk(g_prof_mu);
   ProfRec r{};
   r.a = take_event();

@@ -279,7 +279,8 @@ def amplitudes_backward(plan: Plan, x1, grad_out, *, slice_begin: int = 0,
 
 
 class Batch:
-    """Many (plan, x1 batch, slice range) items in one persistent launch.
+    """Many (plan, x1 batch, slice range) items in one persistent launch (FP32 plans) or
+    one CUDA graph of per-item launches over parallel lanes (any split-precision plan).
 
     items: list of (plan, x1 tensor, slice_begin, slice_end); outputs are allocated here
     (complex128 [n_batch, 2^n_open] each) and refreshed by every run()."""

@@ -98,3 +98,78 @@ def test_sampled_paths_of_a_capped_plan(qfx):
     qfx.sync()
     for o, w in zip(outs, want):
         np.testing.assert_array_equal(o.cpu().numpy(), w)
+
+
+def mixed_tc_items(qfx):
+    specs = [  # (rows, cols, depth, seed, n_open, cuts, n_x1, precision)
+        (4, 4, 16, 0, 5, [], 3, "bf16x3"),
+        (5, 5, 24, 1, 4, [(6, 7, 4)], 2, "bf16x3"),
+        (6, 6, 24, 2, 3, [(14, 15, 2)], 2, "tf32x3"),
+        (3, 5, 16, 3, 6, [], 4, "bf16x3"),
+    ]
+    items, circuits = [], []
+    for rows, cols, d, seed, no, cuts, nx, prec in specs:
+        c = ri.rqc(rows, cols, d, seed=seed)
+        plan = qfx.Plan(qfx.Circuit(c), n_open=no, cuts=cuts, precision=prec)
+        x1 = torch.tensor(ri.random_bitstrings(rows * cols, nx, seed=seed + 50).view(np.int64),
+                          device="cuda")
+        items.append((plan, x1, 0, None))
+        circuits.append(c)
+    return items, circuits
+
+
+@pytest.mark.parametrize("slots", [1, 3, 16])
+def test_split_precision_batch_graph_matches_per_item(qfx, slots):
+    """Batches with tensor-core plans run as one CUDA graph of per-item launch sequences
+    over parallel lanes: outputs equal per-item qfx_amplitudes bit for bit (one work item
+    in flight either way), whatever the number of lanes."""
+    items, circuits = mixed_tc_items(qfx)
+    assert sum(any(s["variant"] >= 10 for s in p.steps) for p, _, _, _ in items) >= 2
+    want = per_item(qfx, items)
+    b = qfx.Batch(items, slots=slots)
+    assert b.slots == min(slots, len(items))
+    outs = b.run()
+    qfx.sync()
+    for o, w in zip(outs, want):
+        np.testing.assert_array_equal(o.cpu().numpy(), w)
+    plan, x1, _, _ = items[2]   # TF32x3 item against the oracle, within its stated bound
+    for r, x in enumerate(x1.cpu().numpy().view(np.uint64)):
+        ref = network.amplitudes_open(circuits[2], int(x), plan.open_sites)
+        assert np.linalg.norm(outs[2][r].cpu().numpy() - ref) <= 3e-5 * np.linalg.norm(ref)
+
+
+def test_split_precision_batch_replays_inside_a_cuda_graph(qfx):
+    items, _ = mixed_tc_items(qfx)
+    want = per_item(qfx, items)
+    b = qfx.Batch(items, slots=4)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(stream=s)
+    for _ in range(2):
+        for o in b.outs:
+            o.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        qfx.sync()
+        for o, w in zip(b.outs, want):
+            np.testing.assert_array_equal(o.cpu().numpy(), w)
+
+
+def test_fp32_items_in_a_split_precision_batch(qfx):
+    """An FP32 plan mixed with tensor-core plans goes through the graph executor too and
+    keeps its FP32 result."""
+    items, _ = mixed_tc_items(qfx)
+    c = ri.rqc(4, 5, 16, seed=9)
+    plan = qfx.Plan(qfx.Circuit(c), n_open=4)
+    x1 = torch.tensor(ri.random_bitstrings(20, 2, seed=3).view(np.int64), device="cuda")
+    items.append((plan, x1, 0, None))
+    want = per_item(qfx, items)
+    b = qfx.Batch(items, slots=2)
+    outs = b.run()
+    qfx.sync()
+    for o, w in zip(outs, want):
+        np.testing.assert_array_equal(o.cpu().numpy(), w)
