@@ -478,8 +478,12 @@ def run_batch(args):
     t_items = e0.elapsed_time(e1) / 1e3 / args.steps
     per_item_launches = (qfx.launch_count() - l1) // args.steps
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    n_tasks_fp32, slots_fp32 = batch.n_tasks, batch.slots
     tc_line = None
     if args.workload == "batch":
+        # free the FP32 batch's workspaces before the split-precision runs
+        del graph, batch, ws
+        torch.cuda.empty_cache()
         # the same items with the steps on the tensor cores (BF16x3, default accumulation)
         tc_items = [(tc_plan[id(p)], x1, sb, se) for p, x1, sb, se in items]
         ws_tc = torch.empty(max(p.workspace_bytes(1) for p, _, _, _ in tc_items), dtype=torch.uint8, device=dev)
@@ -499,7 +503,25 @@ def run_batch(args):
         for a, b, n in zip(outs_tc, ref, nq):
             fl = 2.0 ** (-n / 2)
             worst = max(worst, float((torch.abs(a - b) / torch.clamp(torch.abs(b), min=fl)).max()))
+        # the same items as one batch: one CUDA graph of per-item launch sequences over
+        # parallel lanes (each lane one workspace slot; slots sized like the FP32 batch's)
+        lane = max(p.workspace_bytes(1) for p, _, _, _ in tc_items)
+        gb = qfx.Batch(tc_items, slots=int(max(1, min(16, (96 << 30) // lane))))
+        with torch.cuda.stream(stream):
+            gb.run(stream=stream)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(args.steps):
+                gb.run(stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        qfx.sync()
+        t_gb = e0.elapsed_time(e1) / 1e3 / args.steps
+        same_tc = all(torch.equal(a, b) for a, b in zip(gb.outs, outs_tc))
         tc_line = {"value": flops / t_tc / 1e12, "ms_per_batch": 1e3 * t_tc,
+                   "graph_batch": {"value": flops / t_gb / 1e12, "ms_per_batch": 1e3 * t_gb,
+                                   "lanes": gb.slots, "graph_nodes": gb.n_tasks,
+                                   "identical_to_per_item": bool(same_tc)},
                    "max_rel_diff_vs_fp32": worst,
                    "note": "per-item qfx_amplitudes launches with BF16x3 plans (autotuned: "
                            "tensor cores or FP32 tiles per step shape); per-amplitude "
@@ -515,7 +537,7 @@ def run_batch(args):
         "metric": "contraction TFLOP/s", "unit": "TFLOP/s",
         "graph_persistent": {"value": flops / t_graph / 1e12, "ms_per_batch": 1e3 * t_graph,
                              "items_per_s": len(items) / t_graph, "kernel_launches": 1,
-                             "tasks": batch.n_tasks, "slots": batch.slots},
+                             "tasks": n_tasks_fp32, "slots": slots_fp32},
         "per_item_launches": {"value": flops / t_items / 1e12, "ms_per_batch": 1e3 * t_items,
                               "items_per_s": len(items) / t_items, "kernel_launches": per_item_launches},
         "identical_results": bool(same), "flops_per_batch": flops, "n_items": len(items),
