@@ -550,43 +550,49 @@ def run_batch(args):
 def run_adjoint(args):
     """6x6x(1+24+1) circuit with parametrised single-qubit gates, 128 bitstrings
     (|x2| = 7), L = sum |amp|^2: forward amplitudes and the adjoint's gradients for every
-    gate tensor, timed separately with CUDA events."""
+    gate tensor, timed separately with CUDA events; the backward both with every step output
+    stored (the default at this size) and with one checkpoint per line."""
     import torch
     import paper_1905_00444_gb300 as qfx
     circ = ri.rqc(6, 6, 24, seed=0, parametrised=True)
-    plan = qfx.Plan(qfx.Circuit(circ), n_open=7)
     x1 = torch.tensor(ri.random_bitstrings(36, 1, seed=9).view(np.int64), device="cuda")
-    ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device="cuda")
-    bws = torch.empty(int(qfx.lib.qfx_backward_workspace_bytes(plan._h)), dtype=torch.uint8,
-                      device="cuda")
     out = torch.empty((1, 128), dtype=torch.complex128, device="cuda")
-    for _ in range(args.warmup):
-        amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
-        g = qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    f_ms, b_ms = [], []
-    for _ in range(args.steps):
-        ev[0].record()
-        amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
-        ev[1].record()
-        g = qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
-        ev[2].record()
+    res = {}
+    for mode, store, model in (("stored_outputs", 0, 3), ("line_checkpoints", 1, 4)):
+        plan = qfx.Plan(qfx.Circuit(circ), n_open=7, adjoint_store_bytes=store)
+        ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device="cuda")
+        bws = torch.empty(plan.backward_workspace_bytes(), dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
+            g = qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
         torch.cuda.synchronize()
-        f_ms.append(ev[0].elapsed_time(ev[1]))
-        b_ms.append(ev[1].elapsed_time(ev[2]))
-    qfx.sync()
-    flops = plan.stats["flops_per_item"]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        f_ms, b_ms = [], []
+        for _ in range(args.steps):
+            ev[0].record()
+            amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
+            ev[1].record()
+            g = qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
+            ev[2].record()
+            torch.cuda.synchronize()
+            f_ms.append(ev[0].elapsed_time(ev[1]))
+            b_ms.append(ev[1].elapsed_time(ev[2]))
+        qfx.sync()
+        flops = plan.stats["flops_per_item"]
+        res[mode] = {"forward_ms": float(np.median(f_ms)), "backward_ms": float(np.median(b_ms)),
+                     "forward_tflops": flops / (np.median(f_ms) / 1e3) / 1e12,
+                     "backward_model_flops": model * flops,
+                     "backward_tflops": model * flops / (np.median(b_ms) / 1e3) / 1e12,
+                     "backward_workspace_bytes": plan.backward_workspace_bytes(),
+                     "grad_norm": float(torch.linalg.vector_norm(g).item())}
+        del ws, bws
     print(json.dumps({
         "workload": "adjoint: 6x6x(1+24+1) parametrised RQC, 128 bitstrings (|x2|=7), "
                     "L = sum |amp|^2, gradients of all %d gate tensors" % len(circ.gates),
-        "forward_ms": float(np.median(f_ms)), "backward_ms": float(np.median(b_ms)),
-        "forward_tflops": flops / (np.median(f_ms) / 1e3) / 1e12,
-        "backward_model_flops": 4 * flops,
-        "backward_tflops": 4 * flops / (np.median(b_ms) / 1e3) / 1e12,
-        "note": "backward work model: forward recomputed twice (checkpoints, then line by line), "
-                "plus a reverse step and a site-gradient GEMM per step, each of the forward "
-                "step's flops", "grad_norm": float(torch.linalg.vector_norm(g).item())}), flush=True)
+        **res,
+        "note": "backward work model, in units of the forward's flops: stored outputs = one "
+                "forward + a reverse step + a site-gradient GEMM per step (3); line "
+                "checkpoints add the line-by-line recompute (4)"}), flush=True)
     return 0
 
 

@@ -118,6 +118,9 @@ typedef struct {
   int32_t plan_family;             /* 0 = line sweep (the only family of this build) */
   int32_t tc_flags;                /* tensor-core options, QFX_TC_* bits; 0 = default */
   const char* autotune_cache;      /* JSON file written by qfx_autotune, or NULL */
+  uint64_t adjoint_store_bytes;    /* qfx_amplitudes_backward keeps the output of every step
+                                      when they fit in this many bytes (0 = 4 GiB), else one
+                                      boundary per grid line; 1 = always the latter */
 } qfx_plan_opts;
 
 /* Tensor-core accumulation.  Default: each complex tile is 128 x 128 with four TMEM
@@ -257,8 +260,9 @@ void qfx_batch_destroy(qfx_batch* b);
  *              list, dL/dRe + i dL/dIm of its mat entries (2x2 row-major, or the 4
  *              diagonal entries of a two-qubit gate), summed over batch and slices.
  *   workspace  device, >= qfx_backward_workspace_bytes(p), 256-byte aligned.
- * Runs the contraction in FP32 on the FMA path, keeping the boundary at each line start
- * and recomputing one line at a time.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA,
+ * Runs the contraction in FP32 on the FMA path.  The forward sweep keeps every step's
+ * output when they fit in the plan's adjoint_store_bytes; otherwise it keeps the boundary
+ * at each line start and the reverse sweep recomputes one line at a time.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA,
  * QFX_EUNSUPPORTED (more than 64 events on one site's time line). */
 qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
                                    int64_t slice_begin, int64_t slice_end, const double* grad_out,

@@ -450,6 +450,12 @@ struct BwdLayout {
   uint64_t hdr, sites, sgrad, ckpt, lb, rr, gpart, bpart, evgrad, partoff, total;
 };
 
+// Every step output is kept (no recomputation in the reverse sweep) when all of them fit in
+// the plan's adjoint_store_bytes; larger plans keep one checkpoint per line and recompute it.
+bool full_store(const qfx_plan* p) {
+  return (uint64_t)p->n * a256((uint64_t)p->max_elements * 8) <= p->adjoint_store_bytes;
+}
+
 BwdLayout bwd_layout(const qfx_plan* p) {
   BwdLayout L{};
   const uint64_t B = a256((uint64_t)p->max_elements * 8);
@@ -457,8 +463,13 @@ BwdLayout bwd_layout(const qfx_plan* p) {
   L.hdr = o; o += a256((uint64_t)p->n * 8 + 16);
   L.sites = o; o += a256((uint64_t)p->site_total * 8);
   L.sgrad = o; o += a256((uint64_t)p->site_total * 8);
-  L.ckpt = o; o += (uint64_t)p->lines * B;
-  L.lb = o; o += (uint64_t)p->line_len * B;
+  if (full_store(p)) {   // ckpt holds the output of every step
+    L.ckpt = o; o += (uint64_t)p->n * B;
+    L.lb = L.ckpt;
+  } else {
+    L.ckpt = o; o += (uint64_t)p->lines * B;
+    L.lb = o; o += (uint64_t)p->line_len * B;
+  }
   L.rr = o; o += 2 * B;
   uint64_t gp = 0;
   for (size_t i = 1; i < p->steps.size(); ++i) {
@@ -508,6 +519,7 @@ extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t*
   char* ws = (char*)workspace;
   const uint64_t B = a256((uint64_t)p->max_elements * 8);
   const int n = p->n, L = p->line_len, W = p->lines;
+  const bool full = full_store(p);
   const int n_open = (int)p->open_sites.size();
   const int64_t per = int64_t(1) << n_open;
   int64_t max_site = 1;
@@ -554,12 +566,13 @@ extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t*
                           hdr, 0, sites, 0, 0, st);
     if (!err) err = launch_scale(t, n, max_site, 1, hdr, 0, sites, 0, 0, st);
     if (err) return cuda_fail(err, "qfx_amplitudes_backward: fold");
-    // forward sweep, keeping the boundary at the start of every line
+    // forward sweep, keeping every step's output (full) or the boundary at the start of
+    // every line
     const char* cur = site_ptr(p->steps[0].site);
     int pp = 0;
     for (int i = 1; i < n - 1; ++i) {
-      char* out = ((i + 1) % L == 0) ? ckpt((i + 1) / L) : rr(pp);
-      if (out == rr(pp)) pp ^= 1;
+      char* out = full ? ckpt(i) : ((i + 1) % L == 0) ? ckpt((i + 1) / L) : rr(pp);
+      if (!full && out == rr(pp)) pp ^= 1;
       err = step_fwd(i, cur, out);
       if (err) return cuda_fail(err, "qfx_amplitudes_backward: forward step");
       cur = out;
@@ -569,43 +582,58 @@ extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t*
     int rsel = 0;
     seed_kernel<<<1, kT, 0, st>>>(grad_out + 2 * b * per, t.open_perm, n_open, Rcur, m_ptr);
     count_launch();
-    // reverse, line by line
-    for (int w = W - 1; w >= 0; --w) {
-      const int i0 = w * L;
-      // recompute this line's inputs: input of step i0 + j is lb(j) (j >= 1) or ckpt(w)
-      auto line_in = [&](int j) -> const char* {
-        if (j == 0) return w == 0 ? nullptr : ckpt(w);
-        if (w == 0 && j == 1) return site_ptr(p->steps[0].site);
-        return lb(j);
-      };
-      for (int j = 1; j < L && i0 + j < n; ++j) {
-        if (w == 0 && j == 1) continue;           // L_1 is site 0 itself
-        err = step_fwd(i0 + j - 1, line_in(j - 1), lb(j));
-        if (err) return cuda_fail(err, "qfx_amplitudes_backward: recompute step");
+    // reverse: gradient of step i's site from its input Lin and the incoming R, then R
+    // through the step
+    auto reverse_step = [&](int i, const char* Lin_raw) -> qfx_status {
+      const Step& sp = p->steps[i];
+      float2* gdst = sgrad + p->sites[sp.site].offset;
+      if (i == 0) {
+        cudaError_t e2 = cudaMemcpyAsync(gdst, Rcur, (size_t)sp.N * 8, cudaMemcpyDeviceToDevice, st);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "qfx_amplitudes_backward: site 0 gradient");
+        return QFX_OK;
       }
-      for (int j = std::min(L, n - i0) - 1; j >= 0; --j) {
-        const int i = i0 + j;
-        const Step& sp = p->steps[i];
-        float2* gdst = sgrad + p->sites[sp.site].offset;
-        if (i == 0) {
-          e = cudaMemcpyAsync(gdst, Rcur, (size_t)sp.N * 8, cudaMemcpyDeviceToDevice, st);
-          if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: site 0 gradient");
-          continue;
+      const float2* Lin = (const float2*)Lin_raw;
+      const int64_t J = sp.P * sp.Sd;
+      const GradsGeom gg = grads_geom(sp.K, sp.N, J);
+      float2* part = (float2*)(ws + Lw.gpart);
+      launch_grads(gg, Lin, Rcur, part, sp.P, sp.K, sp.N, sp.NL, sp.Sd, st);
+      const int64_t KN = sp.K * sp.N;
+      reduce_chunks_kernel<<<(unsigned)((KN * 32 + kT - 1) / kT), kT, 0, st>>>(part, gg.chunks, KN, gdst);
+      float2* Rnext = (float2*)rr(rsel ^ 1);
+      launch_rstep((const float2*)site_ptr(sp.site), Rcur, Rnext, sp.P, sp.K, sp.N, sp.NL, sp.Sd, st);
+      count_launch(3);
+      rsel ^= 1;
+      Rcur = Rnext;
+      cudaError_t e2 = cudaGetLastError();
+      if (e2 != cudaSuccess) return cuda_fail(e2, "qfx_amplitudes_backward: reverse step");
+      return QFX_OK;
+    };
+    if (full) {
+      // input of step i: site 0's tensor for i = 1, the stored output of step i - 1 after
+      for (int i = n - 1; i >= 0; --i) {
+        const char* in = i == 0 ? nullptr : i == 1 ? site_ptr(p->steps[0].site) : ckpt(i - 1);
+        qfx_status r = reverse_step(i, in);
+        if (r != QFX_OK) return r;
+      }
+    } else {
+      // line by line, recomputing each line's inputs from its checkpoint
+      for (int w = W - 1; w >= 0; --w) {
+        const int i0 = w * L;
+        // input of step i0 + j is lb(j) (j >= 1) or ckpt(w)
+        auto line_in = [&](int j) -> const char* {
+          if (j == 0) return w == 0 ? nullptr : ckpt(w);
+          if (w == 0 && j == 1) return site_ptr(p->steps[0].site);
+          return lb(j);
+        };
+        for (int j = 1; j < L && i0 + j < n; ++j) {
+          if (w == 0 && j == 1) continue;           // L_1 is site 0 itself
+          err = step_fwd(i0 + j - 1, line_in(j - 1), lb(j));
+          if (err) return cuda_fail(err, "qfx_amplitudes_backward: recompute step");
         }
-        const float2* Lin = (const float2*)line_in(j);
-        const int64_t J = sp.P * sp.Sd;
-        const GradsGeom gg = grads_geom(sp.K, sp.N, J);
-        float2* part = (float2*)(ws + Lw.gpart);
-        launch_grads(gg, Lin, Rcur, part, sp.P, sp.K, sp.N, sp.NL, sp.Sd, st);
-        const int64_t KN = sp.K * sp.N;
-        reduce_chunks_kernel<<<(unsigned)((KN * 32 + kT - 1) / kT), kT, 0, st>>>(part, gg.chunks, KN, gdst);
-        float2* Rnext = (float2*)rr(rsel ^ 1);
-        launch_rstep((const float2*)site_ptr(sp.site), Rcur, Rnext, sp.P, sp.K, sp.N, sp.NL, sp.Sd, st);
-        count_launch(3);
-        rsel ^= 1;
-        Rcur = Rnext;
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: reverse step");
+        for (int j = std::min(L, n - i0) - 1; j >= 0; --j) {
+          qfx_status r = reverse_step(i0 + j, line_in(j));
+          if (r != QFX_OK) return r;
+        }
       }
     }
     // back through every site's time fold

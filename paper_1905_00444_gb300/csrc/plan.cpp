@@ -142,6 +142,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     p->precision = o->precision;
     if (o->tc_flags & ~(QFX_TC_FAST_ACCUMULATION | QFX_TC_REGISTER_ROWS)) return qfx::fail(QFX_EINVAL, "unknown tc_flags bits");
     p->tc_flags = o->tc_flags;
+    if (o->adjoint_store_bytes) p->adjoint_store_bytes = o->adjoint_store_bytes;
     p->transposed = geo.transposed;
     for (int line = 0; line < geo.W; ++line)
       for (int pos = 0; pos < geo.L; ++pos) p->order.push_back(geo.qubit(line, pos));

@@ -109,6 +109,7 @@ struct qfx_plan {
   int lines = 0, line_len = 0;    // sweep geometry: steps [w*line_len, (w+1)*line_len) form line w
   int precision = 0;
   int tc_flags = 0;
+  uint64_t adjoint_store_bytes = 4ull << 30;  // backward keeps all step outputs up to this
   bool transposed = false;        // lines are grid rows instead of columns
   std::vector<int> order;         // qubits in sweep order
   std::vector<int> open_sites;    // user order (output bit i)

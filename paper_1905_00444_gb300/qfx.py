@@ -40,7 +40,7 @@ class PlanOpts(C.Structure):
                 ("n_open", C.c_int32), ("forced_cuts", C.POINTER(Cut)),
                 ("n_forced_cuts", C.c_int32), ("precision", C.c_int32),
                 ("plan_family", C.c_int32), ("tc_flags", C.c_int32),
-                ("autotune_cache", C.c_char_p)]
+                ("autotune_cache", C.c_char_p), ("adjoint_store_bytes", C.c_uint64)]
 
 
 class PlanStats(C.Structure):
@@ -182,7 +182,8 @@ class Plan:
     def __init__(self, circuit: Circuit, *, open_sites: Optional[Sequence[int]] = None,
                  n_open: int = 0, max_intermediate_bytes: int = 0,
                  cuts: Iterable = (), precision: str = "fp32", fast_accumulation: bool = False,
-                 autotune_cache: Optional[str] = None, tensor_maps: bool = True):
+                 autotune_cache: Optional[str] = None, tensor_maps: bool = True,
+                 adjoint_store_bytes: int = 0):
         opts = PlanOpts()
         opts.max_intermediate_bytes = int(max_intermediate_bytes)
         self._open_arr = None
@@ -199,6 +200,7 @@ class Plan:
         opts.precision = PRECISIONS[precision]
         opts.tc_flags = (1 if fast_accumulation else 0) | (0 if tensor_maps else 4)
         opts.autotune_cache = autotune_cache.encode() if autotune_cache else None
+        opts.adjoint_store_bytes = int(adjoint_store_bytes)
         h = C.c_void_p()
         _check(lib.qfx_plan_create(circuit._h, C.byref(opts), C.byref(h)))
         self._h = h
@@ -227,6 +229,10 @@ class Plan:
 
     def workspace_bytes(self, n_concurrent: int = 1) -> int:
         return int(lib.qfx_workspace_bytes(self._h, n_concurrent))
+
+    def backward_workspace_bytes(self) -> int:
+        """Workspace amplitudes_backward needs (all step outputs, or one per grid line)."""
+        return int(lib.qfx_backward_workspace_bytes(self._h))
 
     def upload(self):
         _check(lib.qfx_plan_upload(self._h))
@@ -268,7 +274,7 @@ def amplitudes_backward(plan: Plan, x1, grad_out, *, slice_begin: int = 0,
     if slice_end is None:
         slice_end = plan.n_slices
     if workspace is None:
-        workspace = torch.empty(int(lib.qfx_backward_workspace_bytes(plan._h)), dtype=torch.uint8,
+        workspace = torch.empty(plan.backward_workspace_bytes(), dtype=torch.uint8,
                                 device=x1.device)
     grad_out = grad_out.to(torch.complex128).contiguous()
     out = torch.empty((plan.stats_n_gates, 4), dtype=torch.complex128, device=x1.device)

@@ -113,6 +113,23 @@ def test_forced_cut_slices_and_cap():
     assert capped.n_slices > 1
 
 
+@pytest.mark.parametrize("shape", [(3, 4, 16), (5, 4, 16), (6, 6, 24)])
+def test_adjoint_boundary_storage_threshold(shape):
+    """The backward keeps all n step outputs when n x (one intermediate, 256-byte rounded)
+    fits adjoint_store_bytes, else one per line plus one line's worth: the workspaces differ
+    by exactly (n - lines - line_len) boundaries, lines + line_len = rows + cols."""
+    rows, cols, d = shape
+    c = qfx.Circuit(ri.rqc(rows, cols, d, seed=1))
+    base = qfx.Plan(c, n_open=3)
+    n = rows * cols
+    B = -(-base.stats["max_elements"] * 8 // 256) * 256
+    at = qfx.Plan(c, n_open=3, adjoint_store_bytes=n * B)
+    below = qfx.Plan(c, n_open=3, adjoint_store_bytes=n * B - 1)
+    assert base.backward_workspace_bytes() == at.backward_workspace_bytes()
+    assert at.backward_workspace_bytes() - below.backward_workspace_bytes() == \
+        (n - rows - cols) * B
+
+
 @pytest.mark.parametrize("cuts", [[(0, 5, 1)], [(1, 2, 3)], [(1, 2, 8)], [(1, 2, 1), (2, 1, 1)]])
 def test_bad_cuts_rejected(cuts):
     c = ri.rqc(4, 4, 16, seed=0)

@@ -22,8 +22,9 @@ def gates_tensor(c):
     return torch.tensor(np.stack(rows), dtype=torch.complex128)
 
 
-def gpu_grads(qfx, c, x1s, *, n_open=0, open_sites=None, cuts=(), gbar=None):
-    plan = qfx.Plan(qfx.Circuit(c), n_open=n_open, open_sites=open_sites, cuts=cuts)
+def gpu_grads(qfx, c, x1s, *, n_open=0, open_sites=None, cuts=(), gbar=None, store=0):
+    plan = qfx.Plan(qfx.Circuit(c), n_open=n_open, open_sites=open_sites, cuts=cuts,
+                    adjoint_store_bytes=store)
     x1 = torch.tensor(np.asarray(x1s, dtype=np.uint64).view(np.int64), device="cuda")
     ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device="cuda")
     amp = qfx.amplitudes(plan, x1, workspace=ws)
@@ -98,6 +99,23 @@ def test_gradients_sum_over_slices(qfx):
     _, _, g0 = gpu_grads(qfx, c, x1s, n_open=2)
     _, _, g1 = gpu_grads(qfx, c, x1s, n_open=2, cuts=[(5, 6, 1), (1, 5, 2)])
     assert np.linalg.norm(g1 - g0) / np.linalg.norm(g0) < 1e-5
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 16), (5, 4, 16)])
+def test_line_checkpoints_match_stored_boundaries(qfx, shape):
+    """Keeping every step's output and recomputing each line from its checkpoint run the
+    same kernels on the same inputs: the gradients are bit-identical, and the recomputing
+    run needs less workspace."""
+    rows, cols, d = shape
+    c = ri.rqc(rows, cols, d, seed=11, parametrised=True)
+    x1s = ri.random_bitstrings(rows * cols, 2, seed=5)
+    full, _, g_full = gpu_grads(qfx, c, x1s, n_open=3)
+    line, _, g_line = gpu_grads(qfx, c, x1s, n_open=3, store=1)
+    assert full.backward_workspace_bytes() > line.backward_workspace_bytes()
+    assert np.array_equal(g_full, g_line)
+    entries = all_entries(c)[:40]
+    want = oracle_grads(c, x1s, full.open_sites, entries)
+    compare(np.array([g_line[gi, e] for gi, e in entries]), want)
 
 
 def test_6x6x24_parametrised_128_bitstrings(qfx):
