@@ -9,9 +9,10 @@
 //   seed      R_n = upstream gradient of the amplitudes (scaled by 2^-m)
 //   fold      T[idx] = <x| O_M .. O_1 |0>:  dT/dG[a][b] = w_j[a] u_{j-1}[b] with
 //             u_{j-1} = O_{j-1}..O_1|0>, w_j = <x|O_M..O_{j+1}; grad G = sum Gbar_T conj(dT/dG).
-// Checkpointing: the forward sweep keeps the boundary at the start of every line; the
-// reverse sweep recomputes one line's boundaries from its checkpoint, then walks it
-// backwards.  Memory: (lines + line length + 2) boundary tensors instead of one per site.
+// Boundaries: the forward sweep keeps every step's output when they fit the plan's
+// adjoint_store_bytes; otherwise it keeps the boundary at the start of every line and the
+// reverse sweep recomputes one line's boundaries from its checkpoint before walking it
+// backwards ((lines + line length + 2) boundary tensors instead of one per site).
 // Scaling: sites were scaled by 2^-e_s and the amplitude by 2^E (E = sum e_s), so the
 // gradient of site s is 2^(E - e_s + m) times what the reverse sweep computes; that
 // factor is applied in FP64 when the per-event partials are reduced.
@@ -286,6 +287,48 @@ __global__ void __launch_bounds__(kT) reduce_chunks_kernel(const float2* __restr
 }
 
 // ---- fold adjoint: per-block partial gradients of every event's matrix ----------------
+// One thread per site-tensor element.  The per-element chains and the warp sums run in
+// FP32: the site gradient they consume is FP32 already, and nev FP32 roundings (relative
+// nev * 2^-24) stay far below its error, while this GPU's FP64 rate is 1/64 of FP32.  The
+// warp sums leave the registers as FP64 and every later sum is FP64.
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulcf(float2 a, float2 b) {   // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 mat_entry(const double* m, int i) {
+  return make_float2((float)m[2 * i], (float)m[2 * i + 1]);
+}
+
+// Sums v[0..7] over the warp by halving: after the exchanges at distance 16, 8 and 4 each
+// lane holds one entry, e = 4 * bit4 + 2 * bit3 + bit2 of its lane index, summed over the
+// lanes that differ in those bits; distances 2 and 1 finish it (9 shuffles instead of 40).
+__device__ __forceinline__ float warp_sum8(float v[8], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const float send = h16 ? v[t] : v[t + 4];
+    const float keep = h16 ? v[t + 4] : v[t];
+    v[t] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const float send = h8 ? v[t] : v[t + 2];
+    const float keep = h8 ? v[t + 2] : v[t];
+    v[t] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const float send = h4 ? v[0] : v[1];
+    const float keep = h4 ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  float x = v[0];
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  return x;
+}
+
 __global__ void __launch_bounds__(kT) fold_backward_kernel(
     const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events, const double* __restrict__ mats,
     const CutDev* __restrict__ cuts, int n_cuts, const uint64_t* __restrict__ x1, int64_t b, int64_t sid,
@@ -314,90 +357,75 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
   const uint64_t val0 = (uint64_t)(vu + off[0]), val1 = (uint64_t)(vl + off[1]);
   const uint64_t val2 = (uint64_t)(vr + off[2]), val3 = (uint64_t)(vd + off[3]);
   const int xv = st.x_open ? (int)vx : (int)((x1[b] >> st.qubit) & 1ull);
+  const float2 zero = make_float2(0.f, 0.f);
   // forward: states u_j before each event
-  double2 u0[kMaxEvents + 1], u1[kMaxEvents + 1];
-  u0[0] = make_double2(1.0, 0.0);
-  u1[0] = make_double2(0.0, 0.0);
+  float2 u0[kMaxEvents + 1], u1[kMaxEvents + 1];
+  u0[0] = make_float2(1.f, 0.f);
+  u1[0] = zero;
   for (int j = 0; j < nev; ++j) {
     const FoldEvent ev = events[st.ev_begin + j];
     const double* m = mats + 8 * (int64_t)ev.mat;
-    double2 a = u0[j], c = u1[j];
+    float2 a = u0[j], c = u1[j];
     if (ev.kind == EV_GATE) {
-      const double2 n0 = make_double2(m[0] * a.x - m[1] * a.y + m[2] * c.x - m[3] * c.y,
-                                      m[0] * a.y + m[1] * a.x + m[2] * c.y + m[3] * c.x);
-      const double2 n1 = make_double2(m[4] * a.x - m[5] * a.y + m[6] * c.x - m[7] * c.y,
-                                      m[4] * a.y + m[5] * a.x + m[6] * c.y + m[7] * c.x);
-      a = n0;
-      c = n1;
+      const float2 g00 = mat_entry(m, 0), g01 = mat_entry(m, 1), g10 = mat_entry(m, 2), g11 = mat_entry(m, 3);
+      const float2 p0 = cmulf(g00, a), q0 = cmulf(g01, c), p1 = cmulf(g10, a), q1 = cmulf(g11, c);
+      a = make_float2(p0.x + q0.x, p0.y + q0.y);
+      c = make_float2(p1.x + q1.x, p1.y + q1.y);
     } else {
       const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
       const int k = (int)((bv >> ev.bit) & 1ull);
       if (ev.kind == EV_PROJ) {
-        if (k) a = make_double2(0.0, 0.0);
-        else   c = make_double2(0.0, 0.0);
+        if (k) a = zero;
+        else   c = zero;
       } else {
-        a = cmul(a, make_double2(m[4 * k + 0], m[4 * k + 1]));
-        c = cmul(c, make_double2(m[4 * k + 2], m[4 * k + 3]));
+        a = cmulf(a, mat_entry(m, 2 * k));
+        c = cmulf(c, mat_entry(m, 2 * k + 1));
       }
     }
     u0[j + 1] = a;
     u1[j + 1] = c;
   }
-  double2 g = make_double2(0.0, 0.0);
-  if (active) {
-    const float2 gf = sgrad[st.offset + i];
-    g = make_double2(gf.x, gf.y);
-  }
+  const float2 g = active ? sgrad[st.offset + i] : zero;
   // backward: row vector w = <x| O_M .. O_{j+1}
-  double2 w0 = make_double2(xv == 0 ? 1.0 : 0.0, 0.0), w1 = make_double2(xv == 1 ? 1.0 : 0.0, 0.0);
+  float2 w0 = make_float2(xv == 0 ? 1.f : 0.f, 0.f), w1 = make_float2(xv == 1 ? 1.f : 0.f, 0.f);
   for (int j = nev - 1; j >= 0; --j) {
     const FoldEvent ev = events[st.ev_begin + j];
     const double* m = mats + 8 * (int64_t)ev.mat;
-    const double2 a = u0[j], c = u1[j];
-    double2 d[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
-                    make_double2(0.0, 0.0)};
+    const float2 a = u0[j], c = u1[j];
+    float2 d[4] = {zero, zero, zero, zero};
     int k = 0;
     if (ev.kind != EV_GATE) {
       const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
       k = (int)((bv >> ev.bit) & 1ull);
     }
     if (ev.kind == EV_GATE) {
-      d[0] = cmulc(g, cmul(w0, a));   // dG[0][0] = w0 u0
-      d[1] = cmulc(g, cmul(w0, c));   // dG[0][1] = w0 u1
-      d[2] = cmulc(g, cmul(w1, a));   // dG[1][0] = w1 u0
-      d[3] = cmulc(g, cmul(w1, c));   // dG[1][1] = w1 u1
+      d[0] = cmulcf(g, cmulf(w0, a));   // dG[0][0] = w0 u0
+      d[1] = cmulcf(g, cmulf(w0, c));   // dG[0][1] = w0 u1
+      d[2] = cmulcf(g, cmulf(w1, a));   // dG[1][0] = w1 u0
+      d[3] = cmulcf(g, cmulf(w1, c));   // dG[1][1] = w1 u1
     } else if (ev.kind == EV_DIAG) {
-      d[2 * k + 0] = cmulc(g, cmul(w0, a));
-      d[2 * k + 1] = cmulc(g, cmul(w1, c));
+      d[2 * k + 0] = cmulcf(g, cmulf(w0, a));
+      d[2 * k + 1] = cmulcf(g, cmulf(w1, c));
     }
-    // warp sums, one slot per warp (no atomics)
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      double re = d[t].x, im = d[t].y;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_down_sync(0xffffffffu, re, o);
-        im += __shfl_down_sync(0xffffffffu, im, o);
-      }
-      if (lane == 0) {
-        wpart[warp][j][2 * t] = re;
-        wpart[warp][j][2 * t + 1] = im;
-      }
+    if (ev.kind != EV_PROJ) {   // event-uniform: projections have no entries
+      float v[8] = {d[0].x, d[0].y, d[1].x, d[1].y, d[2].x, d[2].y, d[3].x, d[3].y};
+      const float sum = warp_sum8(v, lane);
+      if ((lane & 3) == 0) wpart[warp][j][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = sum;
+    } else if (lane < 8) {
+      wpart[warp][j][lane] = 0.0;
     }
     // w <- w O_j
     if (ev.kind == EV_GATE) {
-      const double2 g00 = make_double2(m[0], m[1]), g01 = make_double2(m[2], m[3]);
-      const double2 g10 = make_double2(m[4], m[5]), g11 = make_double2(m[6], m[7]);
-      const double2 n0 = make_double2(cmul(w0, g00).x + cmul(w1, g10).x, cmul(w0, g00).y + cmul(w1, g10).y);
-      const double2 n1 = make_double2(cmul(w0, g01).x + cmul(w1, g11).x, cmul(w0, g01).y + cmul(w1, g11).y);
-      w0 = n0;
-      w1 = n1;
+      const float2 g00 = mat_entry(m, 0), g01 = mat_entry(m, 1), g10 = mat_entry(m, 2), g11 = mat_entry(m, 3);
+      const float2 p0 = cmulf(w0, g00), q0 = cmulf(w1, g10), p1 = cmulf(w0, g01), q1 = cmulf(w1, g11);
+      w0 = make_float2(p0.x + q0.x, p0.y + q0.y);
+      w1 = make_float2(p1.x + q1.x, p1.y + q1.y);
     } else if (ev.kind == EV_PROJ) {
-      if (k) w0 = make_double2(0.0, 0.0);
-      else   w1 = make_double2(0.0, 0.0);
+      if (k) w0 = zero;
+      else   w1 = zero;
     } else {
-      w0 = cmul(w0, make_double2(m[4 * k + 0], m[4 * k + 1]));
-      w1 = cmul(w1, make_double2(m[4 * k + 2], m[4 * k + 3]));
+      w0 = cmulf(w0, mat_entry(m, 2 * k));
+      w1 = cmulf(w1, mat_entry(m, 2 * k + 1));
     }
   }
   __syncthreads();
