@@ -318,12 +318,35 @@ uint64_t qfx_step_scratch_bytes(int64_t K, int64_t N, int32_t precision);
 qfx_status qfx_permute(const void* in, void* out, int32_t rank, const int64_t* shape,
                        const int32_t* perm, void* stream);
 
+/* Fast sampling with frugal rejection (Sec. III.B): one sample per x1 batch.
+ *   x1         device uint64 [n_batch], the batches' x1 (as passed to qfx_amplitudes).
+ *   amps       device complex128 [n_batch][2^n_open], 16-byte aligned: qfx_amplitudes'
+ *              output for the same plan and x1 (any slice range: a fraction f of the
+ *              slices gives noisy sampling at fidelity about f, Sec. III.C).
+ *   u          device float64 [n_batch][2^n_open]: uniform variates in [0, 1), u[b][t] for
+ *              scan position t of batch b.
+ *   scan_mask  device uint64 [n_batch]: batch b examines x2 = t XOR scan_mask[b] (low
+ *              n_open bits used), t = 0, 1, ...
+ *   M          rejection constant (> 0): candidate t is accepted when
+ *              u[b][t] < 2^n |amp|^2 / M, evaluated in FP64 as p = re*re + im*im, then
+ *              p * (2^n / M), each operation rounded to nearest (no fused multiply-add).
+ *              With amplitudes of fidelity f pass M * f.
+ *   x2_out     device int64 [n_batch]: the first accepted x2 in scan order, -1 if none.
+ *   bits_out   device uint64 [n_batch] or NULL: x1 with bit open_sites[i] set to bit i of
+ *              x2 (x1 unchanged where x2_out is -1).
+ * One block per batch; asynchronous on `stream`; no allocation.
+ * Errors: QFX_EINVAL (NULL or misaligned pointers, M not finite and > 0), QFX_ECUDA. */
+qfx_status qfx_frugal_select(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                             const double* amps, const double* u, const uint64_t* scan_mask,
+                             double M, int64_t* x2_out, uint64_t* bits_out, void* stream);
+
 /* Kernel timing for measurement (not needed for computing): while enabled, each
  * contraction-step launch is bracketed by CUDA events on its own stream. */
 typedef struct {
   int32_t step;       /* plan step index, or -1 for qfx_contract_step */
   int32_t variant;
-  int32_t kind;       /* 0 = contraction step, 1 = fold, 2 = scale, 3 = accumulate */
+  int32_t kind;       /* 0 = contraction step, 1 = fold, 2 = scale, 3 = accumulate,
+                         4 = permute, 5 = frugal select */
   float ms;
   double flops;
   double bytes;

@@ -21,9 +21,12 @@ Independent routes, each pinned by ``tests/test_oracle_*.py``:
                       any grid size (pins full-size runs by a property);
 * ``gradient``     -- gate gradients by linearity of the amplitude in each gate;
 * ``primitives``   -- the single contraction step (TTGT, Sec. III.E), permutation and
-                      the flop count of Eq. 1, written as their definitions.
+                      the flop count of Eq. 1, written as their definitions;
+* ``sampling``     -- frugal rejection sampling over fast-sampling batches (Sec. III.B),
+                      the bitstring assembly x1 u x2 and the linear cross-entropy
+                      fidelity used to check noisy (path-fraction) sampling (Sec. III.C).
 
 Parity status: every function above is pinned by closed forms, brute force or an
 independent route; none is "parity unpinned".
 """
-from . import dense, statevector, network, stabilizer, gradient, primitives  # noqa: F401
+from . import dense, statevector, network, stabilizer, gradient, primitives, sampling  # noqa: F401

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["circuit.cpp", "plan.cpp", "runtime.cu", "fold.cu", "cgemm_simt.cu", "permute.cu",
            "static_scratch.cu", "cgemm_tc.cu",
-           "adjoint.cu", "batch.cu", "autotune.cu"]
+           "adjoint.cu", "batch.cu", "autotune.cu", "sampling.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

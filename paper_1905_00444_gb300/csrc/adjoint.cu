@@ -34,12 +34,6 @@ constexpr int64_t kGradsBlocks = 608;   // site-gradient grid target: 4 blocks p
 
 uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {   // a * conj(b)
-  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
 
 // ---- seed: R_n[f(o)] = gbar[o] * 2^-m ------------------------------------------------
 __global__ void __launch_bounds__(kT) seed_kernel(const double* __restrict__ gout, const int32_t* __restrict__ open_perm,

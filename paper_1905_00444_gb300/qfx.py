@@ -95,6 +95,7 @@ def _declare(lib):
         "qfx_tensor_peak": (st, [i32, i64, C.POINTER(C.c_double), vp]),
         "qfx_step_scratch_bytes": (u64, [i64, i64, i32]),
         "qfx_permute": (st, [vp, vp, i32, C.POINTER(i64), C.POINTER(i32), vp]),
+        "qfx_frugal_select": (st, [vp, vp, i64, vp, vp, vp, C.c_double, vp, vp, vp]),
         "qfx_profile_enable": (st, [i32]),
         "qfx_profile_collect": (st, [C.POINTER(KernelTime), i32, C.POINTER(i32)]),
         "qfx_autotune": (st, [vp, C.c_char_p, vp, C.c_size_t, vp]),
@@ -282,6 +283,43 @@ def amplitudes_backward(plan: Plan, x1, grad_out, *, slice_begin: int = 0,
                                        grad_out.data_ptr(), out.data_ptr(), workspace.data_ptr(),
                                        workspace.numel(), _stream_ptr(stream)))
     return out
+
+
+def frugal_select(plan: Plan, x1, amps, u, scan_mask, M: float = 10.0, *, stream=None):
+    """Frugal rejection sampling over fast-sampling batches (Sec. III.B), one sample per x1.
+
+    amps: complex128 [n_batch, 2^n_open] from amplitudes(plan, x1, ...); u: float64
+    [n_batch, 2^n_open] uniforms in [0, 1); scan_mask: int64/uint64 [n_batch].  Returns
+    (x2 int64 [n_batch], -1 where no candidate was accepted; bitstrings int64 [n_batch],
+    x1 with the open-site bits set from x2)."""
+    import torch
+    n_batch = x1.numel()
+    per = 1 << len(plan.open_sites)
+    if amps.dtype != torch.complex128 or tuple(amps.shape) != (n_batch, per) or not amps.is_contiguous():
+        raise ValueError("amps must be a contiguous complex128 [n_batch, 2^n_open] tensor")
+    if u.dtype != torch.float64 or tuple(u.shape) != (n_batch, per) or not u.is_contiguous():
+        raise ValueError("u must be a contiguous float64 [n_batch, 2^n_open] tensor")
+    if scan_mask.numel() != n_batch or scan_mask.element_size() != 8:
+        raise ValueError("scan_mask must hold n_batch 64-bit integers")
+    x2 = torch.empty(n_batch, dtype=torch.int64, device=x1.device)
+    bits = torch.empty(n_batch, dtype=torch.int64, device=x1.device)
+    _check(lib.qfx_frugal_select(plan._h, x1.data_ptr(), n_batch, amps.data_ptr(), u.data_ptr(),
+                                 scan_mask.data_ptr(), float(M), x2.data_ptr(), bits.data_ptr(),
+                                 _stream_ptr(stream)))
+    return x2, bits
+
+
+def frugal_sample(plan: Plan, x1, u, scan_mask, M: float = 10.0, *, slice_begin: int = 0,
+                  slice_end: Optional[int] = None, workspace=None, stream=None):
+    """Fast sampling (Sec. III.B): the 2^n_open amplitudes of every x1 batch in one
+    contraction call, then one frugal rejection pass per batch, all on the device.  A slice
+    range covering a fraction f of the slices samples at fidelity about f (Sec. III.C); the
+    caller then passes M * f.  Returns (x2, bitstrings, amps) as frugal_select does, plus
+    the amplitudes."""
+    amps = amplitudes(plan, x1, slice_begin=slice_begin, slice_end=slice_end,
+                      workspace=workspace, stream=stream)
+    x2, bits = frugal_select(plan, x1, amps, u, scan_mask, M, stream=stream)
+    return x2, bits, amps
 
 
 class Batch:

@@ -202,6 +202,17 @@ def random_bitstrings(n_qubits: int, count: int, seed: int) -> np.ndarray:
     return np.array([counter_draw(seed, 0xB17, i) & mask for i in range(count)], dtype=np.uint64)
 
 
+def sampling_draws(n_qubits: int, n_open: int, count: int, seed: int):
+    """Random inputs of `count` fast-sampling batches (one x1 each): x1 (uint64, low n_qubits
+    bits uniform), a scan mask (uint64, low n_open bits uniform) and one uniform variate in
+    [0, 1) per candidate (float64 [count, 2^n_open])."""
+    rng = np.random.default_rng(seed)
+    x1 = random_bitstrings(n_qubits, count, seed ^ 0x5A3)
+    mask = rng.integers(0, 1 << n_open, size=count, dtype=np.uint64)
+    u = rng.random((count, 1 << n_open))
+    return x1, mask, u
+
+
 def random_complex(shape, seed: int, dtype=np.complex64) -> np.ndarray:
     """Seeded complex array with iid N(0,1) real and imaginary parts."""
     rng = np.random.default_rng(seed)

@@ -167,6 +167,23 @@ def test_amplitudes_argument_checks_before_any_launch():
     assert qfx.launch_count() == 0
 
 
+def test_frugal_select_argument_checks_before_any_launch():
+    c = ri.rqc(2, 2, 8, seed=0)
+    p = qfx.Plan(qfx.Circuit(c), n_open=2)
+    f = q.lib.qfx_frugal_select
+    fake = C.c_void_p(1 << 20)
+    assert f(p._h, None, 0, None, None, None, 10.0, None, None, None) == q.QFX_OK   # empty
+    assert f(None, fake, 1, fake, fake, fake, 10.0, fake, None, None) == q.QFX_EINVAL
+    assert f(p._h, fake, -1, fake, fake, fake, 10.0, fake, None, None) == q.QFX_EINVAL
+    for M in (0.0, -1.0, math.inf, math.nan):
+        assert f(p._h, fake, 1, fake, fake, fake, M, fake, None, None) == q.QFX_EINVAL
+    assert f(p._h, fake, 1, None, fake, fake, 10.0, fake, None, None) == q.QFX_EINVAL
+    assert f(p._h, fake, 1, fake, fake, fake, 10.0, None, None, None) == q.QFX_EINVAL
+    assert f(p._h, fake, 1, C.c_void_p((1 << 20) + 8), fake, fake, 10.0, fake, None,
+             None) == q.QFX_EINVAL                                                  # alignment
+    assert qfx.launch_count() == 0
+
+
 def test_permute_and_step_argument_checks():
     fake = C.c_void_p(1 << 20)
     sh = (C.c_int64 * 3)(2, 3, 4)
