@@ -51,22 +51,32 @@ typedef enum {
   QFX_GATE_T = 3,
   QFX_GATE_CZ = 4,
   QFX_GATE_U1 = 5,  /* any single-qubit 2x2 matrix */
-  QFX_GATE_U2 = 6   /* any diagonal two-qubit gate */
+  QFX_GATE_U2 = 6,  /* any diagonal two-qubit gate */
+  QFX_GATE_U4 = 7   /* any two-qubit 4x4 matrix (fSim, iSWAP, CNOT, ...) */
 } qfx_gate_kind;
 
-/* One gate.  `kind` is a label only: the library always uses `mat`.
- *   single-qubit (q1 == -1): mat = 2x2 complex, row-major, (re, im) interleaved:
+/* One gate.  For single-qubit gates `kind` is a label only; for two-qubit gates it selects
+ * the form of `mat` (H .. U1 single-qubit, CZ and U2 diagonal, U4 general).
+ *   single-qubit (q1 == -1): mat[0..7] = 2x2 complex, row-major, (re, im) interleaved:
  *                            mat[2*(2*row + col)] + i*mat[2*(2*row + col) + 1].
- *   two-qubit (q1 >= 0):     a diagonal gate; mat = its 4 diagonal entries d[2*b0 + b1]
- *                            (b0 = value of q0, b1 = value of q1), interleaved.
- *                            q0 and q1 must be grid neighbours.
- * Gates of one layer must act on disjoint qubits; layers run in increasing order. */
+ *   CZ, U2 (q1 >= 0):        a diagonal gate; mat[0..7] = its 4 diagonal entries
+ *                            d[2*b0 + b1] (b0 = value of q0, b1 = value of q1), interleaved.
+ *                            Each such gate adds one bit (a leg of dimension 2) to its bond.
+ *   U4 (q1 >= 0):            mat[0..31] = 4x4 complex G[2*o0 + o1][2*i0 + i1], row-major,
+ *                            interleaved (o = output, i = input values of q0 and q1).  It is
+ *                            split exactly as G = sum_k E_k (x) B_k, k = 2*o0 + i0, with
+ *                            E_k = |o0><i0| on q0 and B_k[o1][i1] = G[2*o0 + o1][2*i0 + i1] on
+ *                            q1: one leg of dimension 4 (two bits) on its bond.
+ * The entries a kind does not use are ignored.  q0 and q1 must be grid neighbours.
+ * Gates of one layer must act on disjoint qubits; layers run in increasing order.  A bond
+ * holds at most 40 bits; its index reads the earliest gate's leg as the most significant
+ * bits. */
 typedef struct {
   int32_t layer;
   int32_t q0;
   int32_t q1;
   int32_t kind;
-  double mat[8];
+  double mat[32];
 } qfx_gate;
 
 typedef struct qfx_circuit qfx_circuit;
@@ -80,8 +90,9 @@ qfx_status qfx_circuit_create(int32_t rows, int32_t cols, const qfx_gate* gates,
                               int64_t n_gates, qfx_circuit** out);
 
 /* Same, from text: first line "grid R C", then one gate per line
- * "layer KIND q0 [q1] v0 v1 ... v7" with every gate's 8 matrix values written out
- * (KIND one of H SQRT_X SQRT_Y T CZ U1 U2; q1 present only for CZ and U2).
+ * "layer KIND q0 [q1] v0 v1 ... " with the gate's matrix values written out: 8 for every
+ * kind but U4, 32 for U4 (KIND one of H SQRT_X SQRT_Y T CZ U1 U2 U4; q1 present only for
+ * CZ, U2 and U4).
  * '#' starts a comment.  Errors: QFX_EINVAL with the line number. */
 qfx_status qfx_circuit_from_text(const char* text, qfx_circuit** out);
 
@@ -263,7 +274,8 @@ void qfx_batch_destroy(qfx_batch* b);
  * Runs the contraction in FP32 on the FMA path.  The forward sweep keeps every step's
  * output when they fit in the plan's adjoint_store_bytes; otherwise it keeps the boundary
  * at each line start and the reverse sweep recomputes one line at a time.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA,
- * QFX_EUNSUPPORTED (more than 64 events on one site's time line). */
+ * QFX_EUNSUPPORTED (more than 64 events on one site's time line, or a U4 gate: its 16
+ * entries do not fit the 4 per gate of grad_gates). */
 qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
                                    int64_t slice_begin, int64_t slice_end, const double* grad_out,
                                    double* grad_gates, void* workspace, size_t ws_bytes,

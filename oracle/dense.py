@@ -20,11 +20,21 @@ def gate_matrix(n: int, gate) -> np.ndarray:
         for q in range(n - 1, -1, -1):
             full = np.kron(full, gate.mat if q == gate.q0 else np.eye(2))
         return full
-    # diagonal two-qubit gate, entry d[2*bit(q0) + bit(q1)]
     idx = np.arange(dim)
     b0 = (idx >> gate.q0) & 1
     b1 = (idx >> gate.q1) & 1
-    return np.diag(np.asarray(gate.mat)[2 * b0 + b1])
+    g = np.asarray(gate.mat)
+    if g.size == 4:            # diagonal two-qubit gate, entry d[2*bit(q0) + bit(q1)]
+        return np.diag(g[2 * b0 + b1])
+    # general two-qubit gate g[2*o0 + o1, 2*i0 + i1]: column i maps to the four rows that
+    # differ from i only in bits q0 and q1
+    full = np.zeros((dim, dim), dtype=np.complex128)
+    base = idx & ~((1 << gate.q0) | (1 << gate.q1))
+    for o0 in range(2):
+        for o1 in range(2):
+            rows = base | (o0 << gate.q0) | (o1 << gate.q1)
+            full[rows, idx] = g.reshape(4, 4)[2 * o0 + o1, 2 * b0 + b1]
+    return full
 
 
 def unitary(circuit) -> np.ndarray:

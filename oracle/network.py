@@ -9,13 +9,20 @@ split used here is the identity
     D(b0, b1) = sum_k  delta(b0, k) * D(k, b1),
 
 i.e. the projector |k><k| on the gate's first qubit q0 and diag(D(k,0), D(k,1)) on
-its second qubit q1, with k the bond leg.  Every leg keeps its own label
-('cz', gate_index); a grid bond is the group of legs of the gates on that edge.
+its second qubit q1, with k the bond leg.  A general two-qubit gate G (4x4, entries
+G[2*o0 + o1, 2*i0 + i1]) has a leg of dimension 4: writing out its q0 indices,
+
+    G = sum_{o0, i0}  |o0><i0|  (x)  B_(o0,i0),   B_(o0,i0)[o1, i1] = G[2*o0 + o1, 2*i0 + i1],
+
+so q0 applies |o0><i0| and q1 applies B_k for leg value k = 2*o0 + i0 (two bits).
+Every leg keeps its own label ('cz', gate_index); a grid bond is the group of legs of
+the gates on that edge.
 
 Cuts (Sec. III.A): fixing a set of legs to values gives one slice ("path"); the
 amplitude is the sum over all slices.  A bond's index is read with the leg of its
-earliest gate as the most significant bit, so a sub-range cut of size 2^b at offset
-o fixes that bond's first (m - b) legs to the high bits of o.
+earliest gate as the most significant bits (a two-bit leg reads o0 as its high bit), so
+a sub-range cut of size 2^b at offset o fixes that bond's first (m - b) bits to the high
+bits of o -- which may fix only the high bit of a two-bit leg.
 
 The sweep absorbs sites in row-major order with ``np.tensordot`` over the labels
 they share -- a different order from any column sweep, and no layout tricks.
@@ -52,11 +59,17 @@ def bond_legs(circuit) -> Dict[Tuple[int, int], List[int]]:
     return out
 
 
-def site_tensor(circuit, q: int, x_bit: Optional[int], fixed: Dict[int, int]):
+def leg_bits(gate) -> int:
+    """Bits of a two-qubit gate's leg: 2 for a general 4x4 gate, 1 for a diagonal one."""
+    return 2 if np.asarray(gate.mat).size == 16 else 1
+
+
+def site_tensor(circuit, q: int, x_bit: Optional[int], fixed: Dict[int, object]):
     """Fold the time line of qubit q into one tensor.
 
     x_bit: output value of the qubit (None keeps the output leg open, labelled ('x', q)).
-    fixed: gate index -> leg value, for legs fixed by a cut.
+    fixed: gate index -> leg value for legs fixed by a cut: an int when the whole leg is
+    fixed, (value, b) when only its b high bits are.
     Returns (tensor, labels); labels are ('cz', gate_index) or ('x', q).
     """
     t = np.array([1.0, 0.0], dtype=np.complex128)   # |0>, physical leg last
@@ -66,16 +79,34 @@ def site_tensor(circuit, q: int, x_bit: Optional[int], fixed: Dict[int, int]):
         if g.q1 < 0:
             t = np.tensordot(t, g.mat, axes=([t.ndim - 1], [1]))
             continue
-        d = np.asarray(g.mat, dtype=np.complex128).reshape(2, 2)    # d[b0, b1]
-        op = np.zeros((2, 2, 2), dtype=np.complex128)                # op[k, out, in]
-        for k in range(2):
-            if q == g.q0:
-                op[k, k, k] = 1.0
-            else:
-                op[k, 0, 0] = d[k, 0]
-                op[k, 1, 1] = d[k, 1]
-        if gi in fixed:
-            t = np.tensordot(t, op[fixed[gi]], axes=([t.ndim - 1], [1]))
+        w = leg_bits(g)
+        op = np.zeros((1 << w, 2, 2), dtype=np.complex128)           # op[k, out, in]
+        if w == 1:
+            d = np.asarray(g.mat, dtype=np.complex128).reshape(2, 2)  # d[b0, b1]
+            for k in range(2):
+                if q == g.q0:
+                    op[k, k, k] = 1.0
+                else:
+                    op[k, 0, 0] = d[k, 0]
+                    op[k, 1, 1] = d[k, 1]
+        else:
+            G = np.asarray(g.mat, dtype=np.complex128).reshape(4, 4)
+            for o0 in range(2):
+                for i0 in range(2):
+                    k = 2 * o0 + i0
+                    if q == g.q0:
+                        op[k, o0, i0] = 1.0
+                    else:
+                        op[k] = G[2 * o0:2 * o0 + 2, 2 * i0:2 * i0 + 2]
+        f = fixed.get(gi)
+        if isinstance(f, tuple):                  # high bits fixed: other values drop out
+            val, b = f
+            for k in range(1 << w):
+                if k >> (w - b) != val:
+                    op[k] = 0
+            f = None
+        if f is not None:
+            t = np.tensordot(t, op[f], axes=([t.ndim - 1], [1]))
         else:
             t = np.tensordot(t, op, axes=([t.ndim - 1], [2]))        # (..., k, out)
             labels.append(("cz", gi))
@@ -97,7 +128,7 @@ def contract_network(tensors: Sequence[Tuple[np.ndarray, List[Label]]]):
     return acc, lab
 
 
-def slice_fixed_legs(circuit, cuts: Sequence[Tuple[int, int, int]], slice_id: int) -> Dict[int, int]:
+def slice_fixed_legs(circuit, cuts: Sequence[Tuple[int, int, int]], slice_id: int) -> Dict[int, object]:
     """Leg values fixed by slice `slice_id` of the cut list.
 
     cuts: (q_a, q_b, size) per cut bond; size is a power of two dividing the bond
@@ -105,9 +136,13 @@ def slice_fixed_legs(circuit, cuts: Sequence[Tuple[int, int, int]], slice_id: in
     the cuts with the first cut as the most significant digit.
     """
     legs = bond_legs(circuit)
+
+    def bits(gl):
+        return sum(leg_bits(circuit.gates[g]) for g in gl)
+
     radices = []
     for (a, b, size) in cuts:
-        m = len(legs[(min(a, b), max(a, b))])
+        m = bits(legs[(min(a, b), max(a, b))])
         assert size >= 1 and (size & (size - 1)) == 0 and size <= (1 << m)
         radices.append((1 << m) // size)
     digits = []
@@ -117,13 +152,19 @@ def slice_fixed_legs(circuit, cuts: Sequence[Tuple[int, int, int]], slice_id: in
         rem //= r
     assert rem == 0, "slice id out of range"
     digits.reverse()
-    fixed: Dict[int, int] = {}
+    fixed: Dict[int, object] = {}
     for (a, b, size), dgt in zip(cuts, digits):
         gl = legs[(min(a, b), max(a, b))]
-        m = len(gl)
-        nfix = m - (size.bit_length() - 1)
-        for j in range(nfix):                      # leg j is bit (m-1-j) of the bond index
-            fixed[gl[j]] = (dgt >> (nfix - 1 - j)) & 1
+        nfix = bits(gl) - (size.bit_length() - 1)
+        left = nfix                                # fixed bits still to hand out, MSB first
+        for g in gl:
+            if left <= 0:
+                break
+            w = leg_bits(circuit.gates[g])
+            take = min(w, left)
+            left -= take
+            val = (dgt >> left) & ((1 << take) - 1)
+            fixed[g] = val if take == w else (val, take)
     return fixed
 
 
@@ -131,7 +172,8 @@ def n_slices(circuit, cuts) -> int:
     legs = bond_legs(circuit)
     out = 1
     for (a, b, size) in cuts:
-        out *= (1 << len(legs[(min(a, b), max(a, b))])) // size
+        m = sum(leg_bits(circuit.gates[g]) for g in legs[(min(a, b), max(a, b))])
+        out *= (1 << m) // size
     return out
 
 

@@ -96,7 +96,7 @@ class Tableau:
 
 def _apply(tab: Tableau, g):
     if g.q1 >= 0:
-        if not np.allclose(np.asarray(g.mat).reshape(-1), ri.DIAG_CZ):
+        if np.asarray(g.mat).size != 4 or not np.allclose(np.asarray(g.mat).reshape(-1), ri.DIAG_CZ):
             raise ValueError("stabilizer oracle: only CZ among two-qubit gates")
         tab.cz(g.q0, g.q1)
         return

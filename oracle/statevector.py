@@ -19,6 +19,14 @@ def apply_diag_2q(psi: np.ndarray, n: int, q0: int, q1: int, d: np.ndarray) -> n
     return psi * np.asarray(d)[sel]
 
 
+def apply_2q(psi: np.ndarray, n: int, q0: int, q1: int, g: np.ndarray) -> np.ndarray:
+    """General two-qubit gate g[2*o0 + o1, 2*i0 + i1] on qubits (q0, q1)."""
+    t = psi.reshape([2] * n)                     # axis a holds qubit n - 1 - a
+    a0, a1 = n - 1 - q0, n - 1 - q1
+    out = np.tensordot(np.asarray(g).reshape(2, 2, 2, 2), t, axes=([2, 3], [a0, a1]))
+    return np.moveaxis(out, [0, 1], [a0, a1]).reshape(-1)
+
+
 def state(circuit) -> np.ndarray:
     n = circuit.n_qubits
     psi = np.zeros(1 << n, dtype=np.complex128)
@@ -28,6 +36,8 @@ def state(circuit) -> np.ndarray:
         g = circuit.gates[i]
         if g.q1 < 0:
             psi = apply_1q(psi, n, g.q0, g.mat)
+        elif np.asarray(g.mat).size == 16:
+            psi = apply_2q(psi, n, g.q0, g.q1, g.mat)
         else:
             psi = apply_diag_2q(psi, n, g.q0, g.q1, g.mat)
     return psi

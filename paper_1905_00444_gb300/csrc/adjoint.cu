@@ -523,6 +523,11 @@ extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t*
                                               int64_t slice_begin, int64_t slice_end,
                                               const double* grad_out, double* grad_gates,
                                               void* workspace, size_t ws_bytes, void* stream) {
+  if (p)
+    for (const auto& ev : p->events)
+      if (ev.kind == EV_ELEM || ev.kind == EV_BLOCK)
+        return fail(QFX_EUNSUPPORTED, "qfx_amplitudes_backward: general (U4) two-qubit gates have 16 "
+                                      "entries, more than the 4 per gate of grad_gates");
   qfx_status s = check_amplitudes_args(p, x1, n_batch, slice_begin, slice_end, grad_out);
   if (s != QFX_OK) return s;
   if (!grad_gates || !workspace) return fail(QFX_EINVAL, "qfx_amplitudes_backward: NULL argument");

@@ -11,6 +11,13 @@
 
 namespace {
 
+bool two_qubit_kind(int kind) {
+  return kind == QFX_GATE_CZ || kind == QFX_GATE_U2 || kind == QFX_GATE_U4;
+}
+
+// matrix values a kind carries: 32 for a general two-qubit gate, 8 otherwise
+int mat_values(int kind) { return kind == QFX_GATE_U4 ? 32 : 8; }
+
 bool neighbours(int rows, int cols, int a, int b) {
   int ra = a / cols, ca = a % cols, rb = b / cols, cb = b % cols;
   return (ra == rb && std::abs(ca - cb) == 1) || (ca == cb && std::abs(ra - rb) == 1);
@@ -42,17 +49,17 @@ qfx_status build(int32_t rows, int32_t cols, const qfx_gate* gates, int64_t n_ga
         return qfx::fail(QFX_EINVAL, where + "two-qubit gate between non-neighbours");
       }
     }
-    if (g.kind < QFX_GATE_H || g.kind > QFX_GATE_U2) {
+    if (g.kind < QFX_GATE_H || g.kind > QFX_GATE_U4) {
       delete c;
       return qfx::fail(QFX_EINVAL, where + "unknown kind");
     }
     bool two = g.q1 >= 0;
-    bool kind_two = (g.kind == QFX_GATE_CZ || g.kind == QFX_GATE_U2);
-    if (two != kind_two) { delete c; return qfx::fail(QFX_EINVAL, where + "kind does not match arity"); }
-    for (double v : g.mat)
-      if (!std::isfinite(v)) { delete c; return qfx::fail(QFX_EINVAL, where + "non-finite matrix entry"); }
+    if (two != two_qubit_kind(g.kind)) { delete c; return qfx::fail(QFX_EINVAL, where + "kind does not match arity"); }
+    const int nv = mat_values(g.kind);
+    for (int k = 0; k < nv; ++k)
+      if (!std::isfinite(g.mat[k])) { delete c; return qfx::fail(QFX_EINVAL, where + "non-finite matrix entry"); }
     qfx::Gate q{g.layer, g.q0, g.q1, g.kind, {}, (int)i};
-    std::memcpy(q.m, g.mat, sizeof(q.m));
+    std::memcpy(q.m, g.mat, sizeof(double) * nv);
     c->gates.push_back(q);
   }
   std::stable_sort(c->gates.begin(), c->gates.end(),
@@ -79,8 +86,8 @@ qfx_status build(int32_t rows, int32_t cols, const qfx_gate* gates, int64_t n_ga
 }
 
 int kind_from_name(const std::string& s) {
-  static const char* names[] = {"H", "SQRT_X", "SQRT_Y", "T", "CZ", "U1", "U2"};
-  for (int i = 0; i < 7; ++i)
+  static const char* names[] = {"H", "SQRT_X", "SQRT_Y", "T", "CZ", "U1", "U2", "U4"};
+  for (int i = 0; i < 8; ++i)
     if (s == names[i]) return i;
   return -1;
 }
@@ -126,12 +133,14 @@ extern "C" qfx_status qfx_circuit_from_text(const char* text, qfx_circuit** out)
       if (!(ls >> kname)) return qfx::fail(QFX_EINVAL, where + "missing kind");
       g.kind = kind_from_name(kname);
       if (g.kind < 0) return qfx::fail(QFX_EINVAL, where + "unknown kind " + kname);
-      bool two = (g.kind == QFX_GATE_CZ || g.kind == QFX_GATE_U2);
+      bool two = two_qubit_kind(g.kind);
       if (!(ls >> g.q0)) return qfx::fail(QFX_EINVAL, where + "missing q0");
       g.q1 = -1;
       if (two && !(ls >> g.q1)) return qfx::fail(QFX_EINVAL, where + "missing q1");
-      for (int k = 0; k < 8; ++k)
-        if (!(ls >> g.mat[k])) return qfx::fail(QFX_EINVAL, where + "need 8 matrix values");
+      const int nv = mat_values(g.kind);
+      for (int k = 0; k < nv; ++k)
+        if (!(ls >> g.mat[k]))
+          return qfx::fail(QFX_EINVAL, where + "need " + std::to_string(nv) + " matrix values");
       std::string extra;
       if (ls >> extra) return qfx::fail(QFX_EINVAL, where + "trailing text");
       gates.push_back(g);

@@ -16,7 +16,9 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
 }
 
 // Element i of site `st` for slice `sid` and output bits x1v: FP64 evolution of the
-// site's 2-vector through its time line, rounded once to complex64.
+// site's 2-vector through its time line, rounded once to complex64.  A diagonal two-qubit
+// gate reads one bit of the bond value (projector on q0, diagonal on q1); a general one
+// reads two, k = 2*o0 + i0 (|o0><i0| on q0, the 2x2 block B_k of the gate on q1).
 __device__ __forceinline__ float2 fold_element(const FoldSite& st, const FoldEvent* __restrict__ events,
                                                const double* __restrict__ mats,
                                                const CutDev* __restrict__ cuts, int n_cuts,
@@ -51,13 +53,28 @@ __device__ __forceinline__ float2 fold_element(const FoldSite& st, const FoldEve
       v1 = n1;
     } else {
       const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
-      const int k = (int)((bv >> ev.bit) & 1ull);
-      if (ev.kind == EV_PROJ) {
-        if (k) v0 = make_double2(0.0, 0.0);
-        else   v1 = make_double2(0.0, 0.0);
+      if (ev.kind == EV_PROJ || ev.kind == EV_DIAG) {
+        const int k = (int)((bv >> ev.bit) & 1ull);
+        if (ev.kind == EV_PROJ) {
+          if (k) v0 = make_double2(0.0, 0.0);
+          else   v1 = make_double2(0.0, 0.0);
+        } else {
+          v0 = cmul(v0, make_double2(m[4 * k + 0], m[4 * k + 1]));
+          v1 = cmul(v1, make_double2(m[4 * k + 2], m[4 * k + 3]));
+        }
       } else {
-        v0 = cmul(v0, make_double2(m[4 * k + 0], m[4 * k + 1]));
-        v1 = cmul(v1, make_double2(m[4 * k + 2], m[4 * k + 3]));
+        const int k = (int)((bv >> ev.bit) & 3ull);   // k = 2*o0 + i0
+        if (ev.kind == EV_ELEM) {                      // |o0><i0|
+          const double2 src = (k & 1) ? v1 : v0;
+          v0 = (k >> 1) ? make_double2(0.0, 0.0) : src;
+          v1 = (k >> 1) ? src : make_double2(0.0, 0.0);
+        } else {                                       // B_k
+          const double* b = m + 8 * k;
+          const double2 n0 = cadd(cmul(make_double2(b[0], b[1]), v0), cmul(make_double2(b[2], b[3]), v1));
+          const double2 n1 = cadd(cmul(make_double2(b[4], b[5]), v0), cmul(make_double2(b[6], b[7]), v1));
+          v0 = n0;
+          v1 = n1;
+        }
       }
     }
   }

@@ -162,12 +162,17 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       if (g.q1 < 0) continue;
       legs[eid.at({std::min(g.q0, g.q1), std::max(g.q0, g.q1)})].push_back((int)gi);
     }
+    // a diagonal gate's leg is one bit of its bond, a general gate's two (its operator
+    // Schmidt split has four terms); the earliest gate holds the most significant bits
+    auto leg_bits = [&](int gi) { return c->gates[gi].kind == QFX_GATE_U4 ? 2 : 1; };
     p->edge_legs.resize(E);
     std::vector<int64_t> full(E), edim(E);
     for (int e = 0; e < E; ++e) {
-      p->edge_legs[e] = (int)legs[e].size();
-      if (legs[e].size() > 40) return qfx::fail(QFX_EINVAL, "more than 40 two-qubit gates on one edge");
-      full[e] = int64_t(1) << legs[e].size();
+      int bits = 0;
+      for (int gi : legs[e]) bits += leg_bits(gi);
+      p->edge_legs[e] = bits;
+      if (bits > 40) return qfx::fail(QFX_EINVAL, "more than 40 bond bits on one edge");
+      full[e] = int64_t(1) << bits;
       edim[e] = full[e];
     }
     auto edge_of = [&](int a, int b) -> int {
@@ -307,10 +312,13 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     }
 
     // fold program
-    std::vector<int> gate_leg_bit(c->gates.size(), -1);
+    std::vector<int> gate_leg_bit(c->gates.size(), -1);   // lowest bit of each leg
     for (int e = 0; e < E; ++e) {
-      int m = (int)legs[e].size();
-      for (int j = 0; j < m; ++j) gate_leg_bit[legs[e][j]] = m - 1 - j;  // earliest = MSB
+      int top = p->edge_legs[e];
+      for (int gi : legs[e]) {   // time order: earliest = most significant
+        top -= leg_bits(gi);
+        gate_leg_bit[gi] = top;
+      }
     }
     p->sites.resize(n);
     int64_t offset = 0;
@@ -335,7 +343,19 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
         qfx::FoldEvent ev{};
         ev.gate = g.index;
         ev.mat = (int32_t)(p->mats.size() / 8);
-        p->mats.insert(p->mats.end(), g.m, g.m + 8);
+        const bool general = g.kind == QFX_GATE_U4;
+        if (general && q == g.q1) {
+          // B_k[o1][i1] = G[2*o0 + o1][2*i0 + i1], k = 2*o0 + i0: four 2x2 matrices in a row
+          for (int k = 0; k < 4; ++k)
+            for (int o1 = 0; o1 < 2; ++o1)
+              for (int i1 = 0; i1 < 2; ++i1) {
+                const int r = 2 * (k >> 1) + o1, col = 2 * (k & 1) + i1;
+                p->mats.push_back(g.m[2 * (4 * r + col)]);
+                p->mats.push_back(g.m[2 * (4 * r + col) + 1]);
+              }
+        } else {
+          p->mats.insert(p->mats.end(), g.m, g.m + 8);
+        }
         if (g.q1 < 0) {
           ev.kind = qfx::EV_GATE;
         } else {
@@ -344,7 +364,8 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
           for (int k = 0; k < 4; ++k)
             if (slots[q][k] == e) slot = k;
           if (slot < 0) return qfx::fail(QFX_EPLAN, "planner: gate edge not a site slot");
-          ev.kind = (q == g.q0) ? qfx::EV_PROJ : qfx::EV_DIAG;
+          if (general) ev.kind = (q == g.q0) ? qfx::EV_ELEM : qfx::EV_BLOCK;
+          else         ev.kind = (q == g.q0) ? qfx::EV_PROJ : qfx::EV_DIAG;
           ev.slot = slot;
           ev.bit = gate_leg_bit[gi];
         }

@@ -21,7 +21,7 @@ constexpr int kMaxCuts = 64;
 // ---------------------------------------------------------------------------
 struct Gate {
   int layer, q0, q1, kind;
-  double m[8];
+  double m[32];
   int index;   // position in the caller's gate list
 };
 
@@ -40,13 +40,15 @@ namespace qfx {
 enum EventKind : int32_t {
   EV_GATE = 0,   // v <- G v, G = 2x2 matrix `mat`
   EV_PROJ = 1,   // this site is q0 of a diagonal 2q gate: v <- |k><k| v, k = leg bit
-  EV_DIAG = 2    // this site is q1: v <- diag(D[k][0], D[k][1]) v, k = leg bit
+  EV_DIAG = 2,   // this site is q1: v <- diag(D[k][0], D[k][1]) v, k = leg bit
+  EV_ELEM = 3,   // q0 of a general 2q gate: v <- |k >> 1><k & 1| v, k = the 2-bit leg
+  EV_BLOCK = 4   // q1 of a general 2q gate: v <- B_k v, B_k = matrix `mat + k` (4 in a row)
 };
 
 struct FoldEvent {
   int32_t kind;
   int32_t slot;   // bond slot 0..3 (up, left, right, down) holding the leg
-  int32_t bit;    // bit of the bond value that is this leg
+  int32_t bit;    // lowest bit of the bond value that holds this leg
   int32_t mat;    // index into the matrix table (4 complex doubles each)
   int32_t gate;   // the gate's index in the caller's list (gradients are reported there)
 };

@@ -28,7 +28,7 @@ class QfxError(RuntimeError):
 
 class Gate(C.Structure):
     _fields_ = [("layer", C.c_int32), ("q0", C.c_int32), ("q1", C.c_int32), ("kind", C.c_int32),
-                ("mat", C.c_double * 8)]
+                ("mat", C.c_double * 32)]
 
 
 class Cut(C.Structure):
@@ -149,7 +149,8 @@ def _stream_ptr(stream) -> Optional[int]:
 
 class Circuit:
     """Validated circuit owned by the library.  `src` has .rows, .cols and .gates, each
-    gate with .layer, .q0, .q1, .kind and .mat (2x2 complex, or 4 diagonal entries)."""
+    gate with .layer, .q0, .q1, .kind and .mat (2x2 complex; 4 diagonal entries for CZ
+    and U2; 4x4 complex for U4)."""
 
     def __init__(self, src=None, *, text: Optional[str] = None):
         h = C.c_void_p()

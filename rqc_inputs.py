@@ -30,8 +30,9 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 # gate kinds (same numbering as the C ABI's qfx_gate_kind)
-H, SQRT_X, SQRT_Y, T, CZ, U1, U2 = 0, 1, 2, 3, 4, 5, 6
-KIND_NAMES = {H: "H", SQRT_X: "SQRT_X", SQRT_Y: "SQRT_Y", T: "T", CZ: "CZ", U1: "U1", U2: "U2"}
+H, SQRT_X, SQRT_Y, T, CZ, U1, U2, U4 = 0, 1, 2, 3, 4, 5, 6, 7
+KIND_NAMES = {H: "H", SQRT_X: "SQRT_X", SQRT_Y: "SQRT_Y", T: "T", CZ: "CZ", U1: "U1", U2: "U2",
+              U4: "U4"}
 
 _S2 = 1.0 / math.sqrt(2.0)
 # 2x2 matrices, row = output basis state, column = input basis state
@@ -53,7 +54,8 @@ class Gate:
     q0: int
     q1: int            # -1 for a single-qubit gate
     kind: int
-    mat: np.ndarray    # 2x2 complex for 1q gates; length-4 diagonal for 2q gates
+    mat: np.ndarray    # 2x2 complex for 1q gates; length-4 diagonal for CZ and U2;
+                       # 4x4 complex for U4, indexed [2*o0 + o1, 2*i0 + i1]
 
     @property
     def two_qubit(self) -> bool:
@@ -133,12 +135,24 @@ def grid_pattern_edges(rows: int, cols: int, pattern: int):
     return out
 
 
+def fsim(theta: float, phi: float) -> np.ndarray:
+    """The fermionic-simulation gate fSim(theta, phi) (a published two-qubit family: an
+    XX+YY rotation by theta and a controlled phase e^(-i phi)), 4x4, basis 2*b(q0) + b(q1)."""
+    c, s = math.cos(theta), math.sin(theta)
+    return np.array([[1, 0, 0, 0], [0, c, -1j * s, 0], [0, -1j * s, c, 0],
+                     [0, 0, 0, np.exp(-1j * phi)]], dtype=np.complex128)
+
+
 def rqc(rows: int, cols: int, depth: int, seed: int = 0,
-        gate_set: Sequence[int] = (SQRT_X, SQRT_Y, T), parametrised: bool = False) -> Circuit:
+        gate_set: Sequence[int] = (SQRT_X, SQRT_Y, T), parametrised: bool = False,
+        two_qubit: str = "cz") -> Circuit:
     """Random circuit of depth 1+depth+1 on a rows x cols grid (see module docstring).
 
     gate_set: kinds drawn for the single-qubit layers (uniform, counter-based).
     parametrised: draw G = Rz(a) Ry(b) Rz(c) with angles uniform in [0, 2pi) instead.
+    two_qubit: "cz" (diagonal, one bond bit per gate) or "fsim": every two-qubit gate is a
+    general (U4) fSim(theta, phi) with theta uniform in [0, pi) and phi in [0, 2pi) drawn
+    per gate (two bond bits per gate).
     """
     n = rows * cols
     gates: List[Gate] = []
@@ -147,7 +161,12 @@ def rqc(rows: int, cols: int, depth: int, seed: int = 0,
     layer = 1
     for t in range(depth):
         for (a, b) in grid_pattern_edges(rows, cols, t % 8):
-            gates.append(Gate(layer, a, b, CZ, DIAG_CZ.copy()))
+            if two_qubit == "fsim":
+                th = counter_draw(seed, 2000003 * t + a, 0x5F1) / 2.0 ** 64 * math.pi
+                ph = counter_draw(seed, 2000003 * t + a, 0x5F2) / 2.0 ** 64 * 2 * math.pi
+                gates.append(Gate(layer, a, b, U4, fsim(th, ph)))
+            else:
+                gates.append(Gate(layer, a, b, CZ, DIAG_CZ.copy()))
         layer += 1
         for q in range(n):
             if parametrised:
@@ -160,7 +179,7 @@ def rqc(rows: int, cols: int, depth: int, seed: int = 0,
         layer += 1
     for q in range(n):
         gates.append(Gate(layer, q, -1, H, MAT_H.copy()))
-    return Circuit(rows, cols, gates, name=f"rqc_{rows}x{cols}x(1+{depth}+1)_s{seed}")
+    return Circuit(rows, cols, gates, name=f"rqc_{rows}x{cols}x(1+{depth}+1)_s{seed}" + ("_fsim" if two_qubit == "fsim" else ""))
 
 
 def zyz(a: float, b: float, c: float) -> np.ndarray:
@@ -223,8 +242,9 @@ def random_complex(shape, seed: int, dtype=np.complex64) -> np.ndarray:
 
 def circuit_to_text(c: Circuit) -> str:
     """The project's text format: header 'grid R C', then one gate per line,
-    'layer KIND q0 [q1] v0 .. v7', with the gate's 8 matrix values (re, im interleaved:
-    the 2x2 matrix row-major, or the 4 diagonal entries of a two-qubit gate)."""
+    'layer KIND q0 [q1] v0 ..', with the gate's matrix values (re, im interleaved: the 2x2
+    matrix row-major, the 4 diagonal entries of a CZ or U2 gate, or the 4x4 matrix of a U4
+    gate row-major)."""
     lines = [f"grid {c.rows} {c.cols}"]
     for g in c.gates:
         vals = " ".join(f"{v.real:.17g} {v.imag:.17g}" for v in np.asarray(g.mat).reshape(-1))

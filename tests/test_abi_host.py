@@ -66,6 +66,52 @@ def test_text_format_errors_name_the_line():
         qfx.Circuit(text="grid 2 2\n0 FOO 0 1 0 0 0 0 0 0 0\n")
 
 
+def test_general_two_qubit_gates_validated():
+    c = ri.rqc(3, 3, 8, seed=0, two_qubit="fsim")
+    g = next(g for g in c.gates if g.kind == ri.U4)
+    g.q1 = -1                                        # U4 on one qubit
+    with pytest.raises(qfx.QfxError, match="arity"):
+        qfx.Circuit(c)
+    c = ri.rqc(3, 3, 8, seed=0, two_qubit="fsim")
+    g = next(g for g in c.gates if g.kind == ri.U4)
+    g.mat = g.mat.copy()
+    g.mat[3, 2] = np.nan
+    with pytest.raises(qfx.QfxError, match="non-finite"):
+        qfx.Circuit(c)
+    with pytest.raises(qfx.QfxError, match="need 32 matrix values"):
+        qfx.Circuit(text="grid 1 2\n0 U4 0 1 " + " ".join(["0"] * 8) + "\n")
+
+
+def test_general_gate_text_roundtrip_and_bond_bits():
+    c = ri.rqc(4, 4, 16, seed=2, two_qubit="fsim")
+    a = qfx.Plan(qfx.Circuit(c), n_open=3)
+    b = qfx.Plan(qfx.Circuit(text=ri.circuit_to_text(c)), n_open=3)
+    assert a.stats == b.stats and a.steps == b.steps
+    # every edge carries two fSim gates in 16 cycles: 2 x 2 bits, bond dimension 16, the
+    # same shapes as the CZ circuit of depth 32
+    cz = qfx.Plan(qfx.Circuit(ri.rqc(4, 4, 32, seed=2)), n_open=3)
+    assert [(s["P"], s["K"], s["N"], s["Sd"]) for s in a.steps] == \
+        [(s["P"], s["K"], s["N"], s["Sd"]) for s in cz.steps]
+    # a half cut of a 4-bit bond: 2 slices
+    h = qfx.Plan(qfx.Circuit(c), n_open=3, cuts=[(5, 6, 8)])
+    assert h.n_slices == 2
+
+
+def test_bond_bit_limit_counts_two_bits_per_general_gate():
+    gates = [ri.Gate(l, 0, 1, ri.U4, ri.fsim(0.3, 0.2)) for l in range(21)]   # 42 bits
+    with pytest.raises(qfx.QfxError, match="40 bond bits"):
+        qfx.Plan(qfx.Circuit(ri.Circuit(1, 2, gates)), n_open=1)
+    qfx.Plan(qfx.Circuit(ri.Circuit(1, 2, gates[:20])), n_open=1)          # 40 bits: fine
+
+
+def test_backward_rejects_general_gates_before_any_launch():
+    p = qfx.Plan(qfx.Circuit(ri.rqc(2, 2, 8, seed=0, two_qubit="fsim")), n_open=1)
+    fake = C.c_void_p(1 << 20)
+    st = q.lib.qfx_amplitudes_backward(p._h, fake, 1, 0, 1, fake, fake, fake, 1 << 30, None)
+    assert st == q.QFX_EUNSUPPORTED
+    assert qfx.launch_count() == 0
+
+
 @pytest.mark.parametrize("shape", [(4, 4, 16), (5, 5, 24), (6, 6, 24), (7, 7, 32), (8, 8, 32),
                                    (3, 5, 8), (5, 3, 8), (2, 7, 16), (1, 6, 8)])
 def test_plan_steps_obey_eq1(shape):
