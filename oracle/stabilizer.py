@@ -94,10 +94,29 @@ class Tableau:
         return 1.0 if int(self.r[sc]) == outcome else 0.0
 
 
+# fSim(pi/2, 0) (|01> -> -i|10>, |10> -> -i|01>) up to a global phase, as a word in the
+# tableau's H, S = diag(1, i) and CZ, applied left to right; 0 = the gate's q0, 1 = its q1.
+# Found by a breadth-first search over two-qubit Clifford words and checked against the
+# matrix by tests/test_oracle_general_gates.py.
+FSIM_PI2_WORD = (("h", 0), ("h", 1), ("s", 0), ("h", 0), ("cz",), ("h", 0), ("h", 1), ("s", 1),
+                 ("cz",), ("h", 0), ("cz",), ("h", 1))
+
+
 def _apply(tab: Tableau, g):
     if g.q1 >= 0:
-        if np.asarray(g.mat).size != 4 or not np.allclose(np.asarray(g.mat).reshape(-1), ri.DIAG_CZ):
-            raise ValueError("stabilizer oracle: only CZ among two-qubit gates")
+        m = np.asarray(g.mat)
+        if m.size == 16 and np.allclose(m, ri.fsim(np.pi / 2, 0.0)):
+            qs = (g.q0, g.q1)
+            for op in FSIM_PI2_WORD:
+                if op[0] == "cz":
+                    tab.cz(g.q0, g.q1)
+                elif op[0] == "h":
+                    tab.h(qs[op[1]])
+                else:
+                    tab.s(qs[op[1]])
+            return
+        if m.size != 4 or not np.allclose(m.reshape(-1), ri.DIAG_CZ):
+            raise ValueError("stabilizer oracle: only CZ and fSim(pi/2, 0) among two-qubit gates")
         tab.cz(g.q0, g.q1)
         return
     if g.kind == ri.H:

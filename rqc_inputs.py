@@ -152,7 +152,8 @@ def rqc(rows: int, cols: int, depth: int, seed: int = 0,
     parametrised: draw G = Rz(a) Ry(b) Rz(c) with angles uniform in [0, 2pi) instead.
     two_qubit: "cz" (diagonal, one bond bit per gate) or "fsim": every two-qubit gate is a
     general (U4) fSim(theta, phi) with theta uniform in [0, pi) and phi in [0, 2pi) drawn
-    per gate (two bond bits per gate).
+    per gate (two bond bits per gate); "fsim_pi2": every one is fSim(pi/2, 0), a Clifford
+    gate (with a Clifford gate_set the circuit has exact stabilizer probabilities).
     """
     n = rows * cols
     gates: List[Gate] = []
@@ -165,6 +166,8 @@ def rqc(rows: int, cols: int, depth: int, seed: int = 0,
                 th = counter_draw(seed, 2000003 * t + a, 0x5F1) / 2.0 ** 64 * math.pi
                 ph = counter_draw(seed, 2000003 * t + a, 0x5F2) / 2.0 ** 64 * 2 * math.pi
                 gates.append(Gate(layer, a, b, U4, fsim(th, ph)))
+            elif two_qubit == "fsim_pi2":
+                gates.append(Gate(layer, a, b, U4, fsim(math.pi / 2, 0.0)))
             else:
                 gates.append(Gate(layer, a, b, CZ, DIAG_CZ.copy()))
         layer += 1
@@ -179,7 +182,8 @@ def rqc(rows: int, cols: int, depth: int, seed: int = 0,
         layer += 1
     for q in range(n):
         gates.append(Gate(layer, q, -1, H, MAT_H.copy()))
-    return Circuit(rows, cols, gates, name=f"rqc_{rows}x{cols}x(1+{depth}+1)_s{seed}" + ("_fsim" if two_qubit == "fsim" else ""))
+    suffix = "" if two_qubit == "cz" else "_" + two_qubit
+    return Circuit(rows, cols, gates, name=f"rqc_{rows}x{cols}x(1+{depth}+1)_s{seed}{suffix}")
 
 
 def zyz(a: float, b: float, c: float) -> np.ndarray:

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import rqc_inputs as ri
-from oracle import network, statevector
+from oracle import network, stabilizer, statevector
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -99,3 +99,25 @@ def test_fsim_tensor_core_steps(qfx):
     assert any(s["variant"] >= 10 for s in plan.steps)
     want = np.array([[psi[expand(x1, plan.open_sites, j)] for j in range(16)] for x1 in x1s])
     check(out, want, n)
+
+
+def test_7x7x16_fsim_clifford_probabilities_exact(qfx):
+    """Full size with general gates: every two-qubit gate fSim(pi/2, 0) (Clifford, two bond
+    bits), sqrt(X) / sqrt(Y) layers, so chi = 16 and the largest intermediate is 2^32
+    elements as at 7x7x(1+32+1) with CZs; exact |amp|^2 per bitstring from the tableau."""
+    c = ri.rqc(7, 7, 16, seed=11, gate_set=(ri.SQRT_X, ri.SQRT_Y), two_qubit="fsim_pi2")
+    x1 = int(ri.random_bitstrings(49, 1, seed=12)[0])
+    plan = qfx.Plan(qfx.Circuit(c), n_open=6)
+    assert plan.stats["max_elements"] == 2 ** 32
+    xt = torch.tensor(np.array([x1], dtype=np.uint64).view(np.int64), device="cuda")
+    ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device="cuda")
+    out = qfx.amplitudes(plan, xt, workspace=ws)
+    qfx.sync()
+    got = np.abs(out[0].cpu().numpy())
+    del ws
+    tab = stabilizer.prepare(c)
+    probs = np.array([stabilizer.probability(c, expand(x1, plan.open_sites, j), tab)
+                      for j in range(64)])
+    assert np.count_nonzero(probs) > 0
+    floor = 2.0 ** (-49 / 2)
+    assert np.all(np.abs(got - np.sqrt(probs)) <= REL * np.maximum(np.sqrt(probs), floor))

@@ -11,6 +11,9 @@ G = sum_k |o0><i0| (x) B_k, B_k[o1, i1] = G[2*o0 + o1, 2*i0 + i1], k = 2*o0 + i0
   closed.
 - Slices over cuts that fix whole two-bit legs, or only their high bit, sum to the
   amplitude, and a half cut of a one-gate edge fixes that leg's high bit (o0).
+- The stabilizer oracle's word for the Clifford gate fSim(pi/2, 0), multiplied out from
+  textbook matrices, is that gate up to a phase; its probabilities on fSim(pi/2, 0)
+  circuits match the state vector.
 """
 import math
 
@@ -99,3 +102,31 @@ def test_half_cut_fixes_high_bit_of_a_two_bit_leg():
     assert network.n_slices(c, [(0, 1, 2)]) == 2
     assert network.slice_fixed_legs(c, [(0, 1, 2)], 1) == {legs[0]: (1, 1)}
     assert network.slice_fixed_legs(c, [(0, 1, 1)], 2) == {legs[0]: 2}
+
+
+def test_stabilizer_word_is_fsim_pi2():
+    """The tableau's gate word for fSim(pi/2, 0), multiplied out from the textbook H,
+    S = diag(1, i) and CZ matrices, equals the gate up to a global phase."""
+    from oracle import stabilizer
+    H, S, I = ri.MAT_H, np.diag([1, 1j]), np.eye(2)
+    one = {("h", 0): np.kron(H, I), ("h", 1): np.kron(I, H), ("s", 0): np.kron(S, I),
+           ("s", 1): np.kron(I, S), ("cz",): np.diag([1, 1, 1, -1])}   # q0 = high factor
+    m = np.eye(4, dtype=np.complex128)
+    for op in stabilizer.FSIM_PI2_WORD:
+        m = one[op] @ m
+    g = ri.fsim(np.pi / 2, 0.0)
+    phase = g[0, 0] / m[0, 0]
+    assert abs(abs(phase) - 1) < 1e-12
+    np.testing.assert_allclose(m * phase, g, atol=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 8), (4, 4, 12), (2, 5, 10)])
+def test_stabilizer_matches_statevector_fsim_pi2(shape):
+    from oracle import stabilizer
+    c = ri.rqc(*shape, seed=13, gate_set=(ri.SQRT_X, ri.SQRT_Y), two_qubit="fsim_pi2")
+    p = np.abs(statevector.amplitudes(c)) ** 2
+    tab = stabilizer.prepare(c)
+    xs = list(ri.random_bitstrings(c.n_qubits, 24, seed=5)) + [int(np.argmax(p))]
+    for x in xs:
+        assert abs(stabilizer.probability(c, int(x), tab) - p[int(x)]) < 1e-12
+    assert np.count_nonzero(p > 1e-12) > 1      # not a product of basis states
