@@ -274,12 +274,24 @@ void qfx_batch_destroy(qfx_batch* b);
  * Runs the contraction in FP32 on the FMA path.  The forward sweep keeps every step's
  * output when they fit in the plan's adjoint_store_bytes; otherwise it keeps the boundary
  * at each line start and the reverse sweep recomputes one line at a time.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA,
- * QFX_EUNSUPPORTED (more than 64 events on one site's time line, or a U4 gate: its 16
- * entries do not fit the 4 per gate of grad_gates). */
+ * QFX_EUNSUPPORTED (more than 64 time-line event slots on one site -- a U4 gate's q1
+ * event takes 4 -- or a U4 gate: its 16 entries do not fit the 4 per gate of grad_gates;
+ * qfx_amplitudes_backward_full takes them). */
 qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
                                    int64_t slice_begin, int64_t slice_end, const double* grad_out,
                                    double* grad_gates, void* workspace, size_t ws_bytes,
                                    void* stream);
+
+/* Same, for circuits with any gate kinds: grad_gates is device complex128 [n_gates][16],
+ * overwritten; entry j of gate g is the gradient with respect to the j-th complex value
+ * of its mat (a U4 gate's 16 entries G[r][c] at j = 4*r + c; other gates their 4 values,
+ * then zeros).  For a U4 gate G[2*o0 + o1][2*i0 + i1] is entry (o1, i1) of the block
+ * B_k, k = 2*o0 + i0, that its q1 event applies, so its gradient is that block's.  Same
+ * workspace and errors (without the U4 restriction). */
+qfx_status qfx_amplitudes_backward_full(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                        int64_t slice_begin, int64_t slice_end,
+                                        const double* grad_out, double* grad_gates,
+                                        void* workspace, size_t ws_bytes, void* stream);
 uint64_t qfx_backward_workspace_bytes(const qfx_plan* p);
 
 /* Autotuner: times every compatible FP32 tile variant of each distinct step shape of `p`

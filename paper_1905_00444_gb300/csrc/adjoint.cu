@@ -323,6 +323,11 @@ __device__ __forceinline__ float warp_sum8(float v[8], int lane) {
   return x;
 }
 
+// Partial slots of an event: a general gate's q1 block B_k has 4 x 4 entries, one set of 4
+// per leg value k (each element sees one k); every other event has one set of 4 (zero for
+// parameter-free events).  kMaxEvents bounds a site's slots.
+__host__ __device__ __forceinline__ int ev_slots(int kind) { return kind == EV_BLOCK ? 4 : 1; }
+
 __global__ void __launch_bounds__(kT) fold_backward_kernel(
     const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events, const double* __restrict__ mats,
     const CutDev* __restrict__ cuts, int n_cuts, const uint64_t* __restrict__ x1, int64_t b, int64_t sid,
@@ -352,22 +357,33 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
   const uint64_t val2 = (uint64_t)(vr + off[2]), val3 = (uint64_t)(vd + off[3]);
   const int xv = st.x_open ? (int)vx : (int)((x1[b] >> st.qubit) & 1ull);
   const float2 zero = make_float2(0.f, 0.f);
+  auto leg = [&](const FoldEvent& ev, uint64_t width_mask) {
+    const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
+    return (int)((bv >> ev.bit) & width_mask);
+  };
   // forward: states u_j before each event
   float2 u0[kMaxEvents + 1], u1[kMaxEvents + 1];
   u0[0] = make_float2(1.f, 0.f);
   u1[0] = zero;
+  int n_slots = 0;
   for (int j = 0; j < nev; ++j) {
     const FoldEvent ev = events[st.ev_begin + j];
+    n_slots += ev_slots(ev.kind);
     const double* m = mats + 8 * (int64_t)ev.mat;
     float2 a = u0[j], c = u1[j];
-    if (ev.kind == EV_GATE) {
-      const float2 g00 = mat_entry(m, 0), g01 = mat_entry(m, 1), g10 = mat_entry(m, 2), g11 = mat_entry(m, 3);
+    if (ev.kind == EV_GATE || ev.kind == EV_BLOCK) {
+      const double* g = ev.kind == EV_GATE ? m : m + 8 * leg(ev, 3);
+      const float2 g00 = mat_entry(g, 0), g01 = mat_entry(g, 1), g10 = mat_entry(g, 2), g11 = mat_entry(g, 3);
       const float2 p0 = cmulf(g00, a), q0 = cmulf(g01, c), p1 = cmulf(g10, a), q1 = cmulf(g11, c);
       a = make_float2(p0.x + q0.x, p0.y + q0.y);
       c = make_float2(p1.x + q1.x, p1.y + q1.y);
+    } else if (ev.kind == EV_ELEM) {                 // |o0><i0|, k = 2*o0 + i0
+      const int k = leg(ev, 3);
+      const float2 src = (k & 1) ? c : a;
+      a = (k >> 1) ? zero : src;
+      c = (k >> 1) ? src : zero;
     } else {
-      const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
-      const int k = (int)((bv >> ev.bit) & 1ull);
+      const int k = leg(ev, 1);
       if (ev.kind == EV_PROJ) {
         if (k) a = zero;
         else   c = zero;
@@ -382,17 +398,15 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
   const float2 g = active ? sgrad[st.offset + i] : zero;
   // backward: row vector w = <x| O_M .. O_{j+1}
   float2 w0 = make_float2(xv == 0 ? 1.f : 0.f, 0.f), w1 = make_float2(xv == 1 ? 1.f : 0.f, 0.f);
+  int sl = n_slots;
   for (int j = nev - 1; j >= 0; --j) {
     const FoldEvent ev = events[st.ev_begin + j];
     const double* m = mats + 8 * (int64_t)ev.mat;
     const float2 a = u0[j], c = u1[j];
+    sl -= ev_slots(ev.kind);
+    const int k = ev.kind == EV_GATE ? 0 : leg(ev, (ev.kind == EV_ELEM || ev.kind == EV_BLOCK) ? 3 : 1);
     float2 d[4] = {zero, zero, zero, zero};
-    int k = 0;
-    if (ev.kind != EV_GATE) {
-      const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
-      k = (int)((bv >> ev.bit) & 1ull);
-    }
-    if (ev.kind == EV_GATE) {
+    if (ev.kind == EV_GATE || ev.kind == EV_BLOCK) {
       d[0] = cmulcf(g, cmulf(w0, a));   // dG[0][0] = w0 u0
       d[1] = cmulcf(g, cmulf(w0, c));   // dG[0][1] = w0 u1
       d[2] = cmulcf(g, cmulf(w1, a));   // dG[1][0] = w1 u0
@@ -401,19 +415,30 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
       d[2 * k + 0] = cmulcf(g, cmulf(w0, a));
       d[2 * k + 1] = cmulcf(g, cmulf(w1, c));
     }
-    if (ev.kind != EV_PROJ) {   // event-uniform: projections have no entries
-      float v[8] = {d[0].x, d[0].y, d[1].x, d[1].y, d[2].x, d[2].y, d[3].x, d[3].y};
-      const float sum = warp_sum8(v, lane);
-      if ((lane & 3) == 0) wpart[warp][j][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = sum;
-    } else if (lane < 8) {
-      wpart[warp][j][lane] = 0.0;
+    // event-uniform branches: projections and elementary matrices have no entries
+    if (ev.kind == EV_PROJ || ev.kind == EV_ELEM) {
+      if (lane < 8) wpart[warp][sl][lane] = 0.0;
+    } else {
+      for (int kk = 0; kk < ev_slots(ev.kind); ++kk) {   // a block's sum goes to its k's slot
+        const bool mine = ev.kind != EV_BLOCK || kk == k;
+        float v[8] = {mine ? d[0].x : 0.f, mine ? d[0].y : 0.f, mine ? d[1].x : 0.f, mine ? d[1].y : 0.f,
+                      mine ? d[2].x : 0.f, mine ? d[2].y : 0.f, mine ? d[3].x : 0.f, mine ? d[3].y : 0.f};
+        const float sum = warp_sum8(v, lane);
+        if ((lane & 3) == 0)
+          wpart[warp][sl + kk][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = sum;
+      }
     }
     // w <- w O_j
-    if (ev.kind == EV_GATE) {
-      const float2 g00 = mat_entry(m, 0), g01 = mat_entry(m, 1), g10 = mat_entry(m, 2), g11 = mat_entry(m, 3);
+    if (ev.kind == EV_GATE || ev.kind == EV_BLOCK) {
+      const double* gm = ev.kind == EV_GATE ? m : m + 8 * k;
+      const float2 g00 = mat_entry(gm, 0), g01 = mat_entry(gm, 1), g10 = mat_entry(gm, 2), g11 = mat_entry(gm, 3);
       const float2 p0 = cmulf(w0, g00), q0 = cmulf(w1, g10), p1 = cmulf(w0, g01), q1 = cmulf(w1, g11);
       w0 = make_float2(p0.x + q0.x, p0.y + q0.y);
       w1 = make_float2(p1.x + q1.x, p1.y + q1.y);
+    } else if (ev.kind == EV_ELEM) {                 // (w |o0><i0|)[col] = w[o0] delta(col, i0)
+      const float2 src = (k >> 1) ? w1 : w0;
+      w0 = (k & 1) ? zero : src;
+      w1 = (k & 1) ? src : zero;
     } else if (ev.kind == EV_PROJ) {
       if (k) w0 = zero;
       else   w1 = zero;
@@ -423,8 +448,8 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
     }
   }
   __syncthreads();
-  double* outp = bpart + part_off[blockIdx.y] + (int64_t)blockIdx.x * nev * 8;
-  for (int t = threadIdx.x; t < nev * 8; t += kT) {
+  double* outp = bpart + part_off[blockIdx.y] + (int64_t)blockIdx.x * n_slots * 8;
+  for (int t = threadIdx.x; t < n_slots * 8; t += kT) {
     const int j = t / 8, e = t % 8;
     double s = 0.0;
     for (int w = 0; w < kT / 32; ++w) s += wpart[w][j][e];
@@ -432,38 +457,64 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
   }
 }
 
-// one thread per (event, entry): sum the site's blocks, apply 2^(E - e_s + m)
+// one thread per (event, double of its up to 4 slots): sum the site's blocks, apply
+// 2^(E - e_s + m); evgrad holds 32 doubles per event
 __global__ void __launch_bounds__(kT) event_reduce_kernel(const FoldSite* __restrict__ sites, int n_sites,
+                                                          const FoldEvent* __restrict__ events,
                                                           const double* __restrict__ bpart,
                                                           const int64_t* __restrict__ part_off,
                                                           const int* __restrict__ hdr_exps, const int* m_ptr,
                                                           int n_events, double* __restrict__ evgrad) {
   const int t = blockIdx.x * kT + threadIdx.x;
-  if (t >= n_events * 8) return;
-  const int e = t / 8, entry = t % 8;
+  if (t >= n_events * 32) return;
+  const int e = t / 32, entry = t % 32;
   int s = 0;
   for (int q = 0; q < n_sites; ++q)
     if (e >= sites[q].ev_begin && e < sites[q].ev_end) s = q;
   const FoldSite st = sites[s];
-  const int nev = st.ev_end - st.ev_begin, j = e - st.ev_begin;
+  int slot = 0, n_slots = 0;
+  for (int j = st.ev_begin; j < st.ev_end; ++j) {
+    if (j == e) slot = n_slots;
+    n_slots += ev_slots(events[j].kind);
+  }
+  if (entry >= 8 * ev_slots(events[e].kind)) {
+    evgrad[t] = 0.0;
+    return;
+  }
   const int64_t nblk = (st.size + kT - 1) / kT;
   double sum = 0.0;
-  for (int64_t bk = 0; bk < nblk; ++bk) sum += bpart[part_off[s] + bk * nev * 8 + j * 8 + entry];
+  for (int64_t bk = 0; bk < nblk; ++bk) sum += bpart[part_off[s] + bk * n_slots * 8 + slot * 8 + entry];
   int E = 0;
   for (int q = 0; q < n_sites; ++q) E += hdr_exps[q];
   evgrad[t] = ldexp(sum, E - hdr_exps[s] + *m_ptr);
 }
 
-// one thread per (gate, entry): add the gate's events into the output (item order)
-__global__ void __launch_bounds__(kT) gate_accum_kernel(const int32_t* __restrict__ gate_ev, int n_gates,
-                                                        const double* __restrict__ evgrad, double* grad) {
+// one thread per (gate, double of its `per_gate` complex entries): add the gate's events
+// into the output (item order).  A general gate's entry G[r][c] is entry (o1, i1) of the
+// block B_k of its q1 event, k = 2*o0 + i0 (r = 2*o0 + o1, c = 2*i0 + i1); other gates
+// fill their first 4 entries.
+__global__ void __launch_bounds__(kT) gate_accum_kernel(const int32_t* __restrict__ gate_ev,
+                                                        const FoldEvent* __restrict__ events, int n_gates,
+                                                        int per_gate, const double* __restrict__ evgrad,
+                                                        double* grad) {
   const int t = blockIdx.x * kT + threadIdx.x;
-  if (t >= n_gates * 8) return;
-  const int gte = t / 8, entry = t % 8;
-  double s = 0.0;
+  if (t >= n_gates * 2 * per_gate) return;
+  const int gte = t / (2 * per_gate), ent = t % (2 * per_gate), ce = ent / 2, ri = ent & 1;
+  int block = -1;
   for (int q = 0; q < 2; ++q) {
     const int e = gate_ev[2 * gte + q];
-    if (e >= 0) s += evgrad[e * 8 + entry];
+    if (e >= 0 && events[e].kind == EV_BLOCK) block = e;
+  }
+  double s = 0.0;
+  if (block >= 0) {
+    const int r = ce / 4, c = ce % 4;
+    const int k = 2 * (r >> 1) + (c >> 1), bi = 2 * (r & 1) + (c & 1);
+    s = evgrad[block * 32 + (k * 4 + bi) * 2 + ri];
+  } else if (ce < 4) {
+    for (int q = 0; q < 2; ++q) {
+      const int e = gate_ev[2 * gte + q];
+      if (e >= 0) s += evgrad[e * 32 + ce * 2 + ri];
+    }
   }
   grad[t] += s;
 }
@@ -476,6 +527,12 @@ struct BwdLayout {
 // the plan's adjoint_store_bytes; larger plans keep one checkpoint per line and recompute it.
 bool full_store(const qfx_plan* p) {
   return (uint64_t)p->n * a256((uint64_t)p->max_elements * 8) <= p->adjoint_store_bytes;
+}
+
+int64_t site_slots(const qfx_plan* p, const FoldSite& fs) {
+  int64_t n = 0;
+  for (int j = fs.ev_begin; j < fs.ev_end; ++j) n += ev_slots(p->events[j].kind);
+  return n;
 }
 
 BwdLayout bwd_layout(const qfx_plan* p) {
@@ -501,9 +558,9 @@ BwdLayout bwd_layout(const qfx_plan* p) {
   }
   L.gpart = o; o += a256(gp);
   uint64_t bp = 0;
-  for (const auto& fs : p->sites) bp += (uint64_t)((fs.size + kT - 1) / kT) * (fs.ev_end - fs.ev_begin) * 8;
+  for (const auto& fs : p->sites) bp += (uint64_t)((fs.size + kT - 1) / kT) * site_slots(p, fs) * 8;
   L.bpart = o; o += a256(bp * 8);
-  L.evgrad = o; o += a256((uint64_t)p->events.size() * 8 * 8);
+  L.evgrad = o; o += a256((uint64_t)p->events.size() * 32 * 8);
   L.partoff = o; o += a256((uint64_t)p->n * 8);
   L.total = o;
   return L;
@@ -519,23 +576,26 @@ extern "C" uint64_t qfx_backward_workspace_bytes(const qfx_plan* p) {
   return bwd_layout(p).total;
 }
 
-extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
-                                              int64_t slice_begin, int64_t slice_end,
-                                              const double* grad_out, double* grad_gates,
-                                              void* workspace, size_t ws_bytes, void* stream) {
-  if (p)
+namespace {
+
+qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int64_t slice_begin,
+                    int64_t slice_end, const double* grad_out, double* grad_gates, int per_gate,
+                    void* workspace, size_t ws_bytes, void* stream) {
+  if (p && per_gate == 4)
     for (const auto& ev : p->events)
       if (ev.kind == EV_ELEM || ev.kind == EV_BLOCK)
         return fail(QFX_EUNSUPPORTED, "qfx_amplitudes_backward: general (U4) two-qubit gates have 16 "
-                                      "entries, more than the 4 per gate of grad_gates");
+                                      "entries, more than the 4 per gate of grad_gates "
+                                      "(qfx_amplitudes_backward_full writes 16)");
   qfx_status s = check_amplitudes_args(p, x1, n_batch, slice_begin, slice_end, grad_out);
   if (s != QFX_OK) return s;
   if (!grad_gates || !workspace) return fail(QFX_EINVAL, "qfx_amplitudes_backward: NULL argument");
   if (((uintptr_t)workspace & 255) || ((uintptr_t)grad_gates & 15))
     return fail(QFX_EINVAL, "qfx_amplitudes_backward: misaligned workspace or grad_gates");
   for (const auto& fs : p->sites)
-    if (fs.ev_end - fs.ev_begin > kMaxEvents)
-      return fail(QFX_EUNSUPPORTED, "qfx_amplitudes_backward: a site has more than 64 time-line events");
+    if (site_slots(p, fs) > kMaxEvents)
+      return fail(QFX_EUNSUPPORTED, "qfx_amplitudes_backward: a site has more than 64 time-line event "
+                                    "slots (a general gate's block takes 4)");
   const BwdLayout Lw = bwd_layout(p);
   if (ws_bytes < Lw.total) return fail(QFX_ENOMEM, "qfx_amplitudes_backward: workspace smaller than qfx_backward_workspace_bytes()");
   const DeviceTables* tp = nullptr;
@@ -559,13 +619,13 @@ extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t*
     for (int q = 0; q < n; ++q) {
       partoff[q] = o;
       const auto& fs = p->sites[q];
-      o += ((fs.size + kT - 1) / kT) * (fs.ev_end - fs.ev_begin) * 8;
+      o += ((fs.size + kT - 1) / kT) * site_slots(p, fs) * 8;
     }
   }
   cudaError_t e = cudaMemcpyAsync(ws + Lw.partoff, partoff.data(), n * sizeof(int64_t),
                                   cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: partial offsets");
-  e = cudaMemsetAsync(grad_gates, 0, (size_t)p->n_gates * 8 * sizeof(double), st);
+  e = cudaMemsetAsync(grad_gates, 0, (size_t)p->n_gates * 2 * per_gate * sizeof(double), st);
   if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: clearing grad_gates");
 
   char* hdr = ws + Lw.hdr;
@@ -669,14 +729,34 @@ extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t*
                                             sid, sgrad, (double*)(ws + Lw.bpart),
                                             (const int64_t*)(ws + Lw.partoff));
     const int nev = (int)p->events.size();
-    event_reduce_kernel<<<(nev * 8 + kT - 1) / kT, kT, 0, st>>>(t.sites, n, (const double*)(ws + Lw.bpart),
-                                                               (const int64_t*)(ws + Lw.partoff), exps,
-                                                               m_ptr, nev, (double*)(ws + Lw.evgrad));
-    gate_accum_kernel<<<(p->n_gates * 8 + kT - 1) / kT, kT, 0, st>>>(t.gate_ev, p->n_gates,
-                                                                     (const double*)(ws + Lw.evgrad), grad_gates);
+    event_reduce_kernel<<<(nev * 32 + kT - 1) / kT, kT, 0, st>>>(t.sites, n, t.events,
+                                                                (const double*)(ws + Lw.bpart),
+                                                                (const int64_t*)(ws + Lw.partoff), exps,
+                                                                m_ptr, nev, (double*)(ws + Lw.evgrad));
+    gate_accum_kernel<<<(p->n_gates * 2 * per_gate + kT - 1) / kT, kT, 0, st>>>(
+        t.gate_ev, t.events, p->n_gates, per_gate, (const double*)(ws + Lw.evgrad), grad_gates);
     count_launch(3);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: fold adjoint");
   }
   return QFX_OK;
+}
+
+}  // namespace
+
+extern "C" qfx_status qfx_amplitudes_backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
+                                              int64_t slice_begin, int64_t slice_end,
+                                              const double* grad_out, double* grad_gates,
+                                              void* workspace, size_t ws_bytes, void* stream) {
+  return backward(p, x1, n_batch, slice_begin, slice_end, grad_out, grad_gates, 4, workspace,
+                  ws_bytes, stream);
+}
+
+extern "C" qfx_status qfx_amplitudes_backward_full(const qfx_plan* p, const uint64_t* x1,
+                                                   int64_t n_batch, int64_t slice_begin,
+                                                   int64_t slice_end, const double* grad_out,
+                                                   double* grad_gates, void* workspace,
+                                                   size_t ws_bytes, void* stream) {
+  return backward(p, x1, n_batch, slice_begin, slice_end, grad_out, grad_gates, 16, workspace,
+                  ws_bytes, stream);
 }

@@ -84,6 +84,7 @@ def _declare(lib):
         "qfx_amplitudes": (st, [vp, vp, i64, i64, i64, vp, C.c_size_t, vp, vp]),
         "qfx_amplitudes_static": (st, [vp, vp, i64, i64, i64, vp, vp]),
         "qfx_amplitudes_backward": (st, [vp, vp, i64, i64, i64, vp, vp, vp, C.c_size_t, vp]),
+        "qfx_amplitudes_backward_full": (st, [vp, vp, i64, i64, i64, vp, vp, vp, C.c_size_t, vp]),
         "qfx_backward_workspace_bytes": (u64, [vp]),
         "qfx_batch_workspace_bytes": (u64, [C.POINTER(BatchItem), i32, i64]),
         "qfx_batch_prepare": (st, [C.POINTER(BatchItem), i32, vp, C.c_size_t, C.POINTER(vp), vp]),
@@ -269,20 +270,25 @@ def amplitudes(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Optional[int]
 
 
 def amplitudes_backward(plan: Plan, x1, grad_out, *, slice_begin: int = 0,
-                        slice_end: Optional[int] = None, workspace=None, stream=None):
-    """Gradients [n_gates, 4] (complex128) of a real loss with respect to every gate's
-    matrix entries, given grad_out = dL/dRe(amp) + i dL/dIm(amp) [n_batch, 2^n_open]."""
+                        slice_end: Optional[int] = None, workspace=None, stream=None,
+                        entries: int = 4):
+    """Gradients [n_gates, entries] (complex128) of a real loss with respect to every gate's
+    matrix entries, given grad_out = dL/dRe(amp) + i dL/dIm(amp) [n_batch, 2^n_open].
+    entries = 4 (single-qubit and diagonal gates) or 16 (any gates, U4 included: entry
+    4*r + c of a U4 gate is G[r][c]; other gates fill their first 4)."""
     import torch
     if slice_end is None:
         slice_end = plan.n_slices
     if workspace is None:
         workspace = torch.empty(plan.backward_workspace_bytes(), dtype=torch.uint8,
                                 device=x1.device)
+    if entries not in (4, 16):
+        raise ValueError("entries must be 4 or 16")
     grad_out = grad_out.to(torch.complex128).contiguous()
-    out = torch.empty((plan.stats_n_gates, 4), dtype=torch.complex128, device=x1.device)
-    _check(lib.qfx_amplitudes_backward(plan._h, x1.data_ptr(), x1.numel(), slice_begin, slice_end,
-                                       grad_out.data_ptr(), out.data_ptr(), workspace.data_ptr(),
-                                       workspace.numel(), _stream_ptr(stream)))
+    out = torch.empty((plan.stats_n_gates, entries), dtype=torch.complex128, device=x1.device)
+    f = lib.qfx_amplitudes_backward if entries == 4 else lib.qfx_amplitudes_backward_full
+    _check(f(plan._h, x1.data_ptr(), x1.numel(), slice_begin, slice_end, grad_out.data_ptr(),
+             out.data_ptr(), workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)))
     return out
 
 

@@ -22,14 +22,14 @@ def gates_tensor(c):
     return torch.tensor(np.stack(rows), dtype=torch.complex128)
 
 
-def gpu_grads(qfx, c, x1s, *, n_open=0, open_sites=None, cuts=(), gbar=None, store=0):
+def gpu_grads(qfx, c, x1s, *, n_open=0, open_sites=None, cuts=(), gbar=None, store=0, entries=4):
     plan = qfx.Plan(qfx.Circuit(c), n_open=n_open, open_sites=open_sites, cuts=cuts,
                     adjoint_store_bytes=store)
     x1 = torch.tensor(np.asarray(x1s, dtype=np.uint64).view(np.int64), device="cuda")
     ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device="cuda")
     amp = qfx.amplitudes(plan, x1, workspace=ws)
     g = 2 * amp if gbar is None else torch.as_tensor(gbar, device="cuda")
-    out = qfx.amplitudes_backward(plan, x1, g)
+    out = qfx.amplitudes_backward(plan, x1, g, entries=entries)
     qfx.sync()
     return plan, amp.cpu().numpy(), out.cpu().numpy()
 
@@ -69,6 +69,29 @@ def test_all_gate_entries_small(qfx, shape):
     want = oracle_grads(c, x1s, plan.open_sites, entries)
     got = np.array([g[gi, e] for gi, e in entries])
     compare(got, want)
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 8), (2, 4, 12)])
+def test_general_two_qubit_gates_all_entries(qfx, shape):
+    """fSim (U4) gates: all 16 entries per gate, with the block of the gate's q1 event
+    mapped back to G[r][c]; single-qubit gates alongside."""
+    c = ri.rqc(*shape, seed=shape[2], parametrised=True, two_qubit="fsim")
+    x1s = ri.random_bitstrings(c.n_qubits, 2, seed=3)
+    plan, amp, g = gpu_grads(qfx, c, x1s, n_open=2, entries=16)
+    entries = all_entries(c)
+    assert sum(1 for gi, e in entries if e >= 4) > 0
+    want = oracle_grads(c, x1s, plan.open_sites, entries)
+    got = np.array([g[gi, e] for gi, e in entries])
+    compare(got, want)
+
+
+def test_sixteen_entries_extend_the_four_on_diagonal_gates(qfx):
+    c = ri.rqc(3, 4, 16, seed=4, parametrised=True)
+    x1s = ri.random_bitstrings(12, 2, seed=2)
+    _, _, g4 = gpu_grads(qfx, c, x1s, n_open=2)
+    _, _, g16 = gpu_grads(qfx, c, x1s, n_open=2, entries=16)
+    assert np.array_equal(g16[:, :4], g4)
+    assert not np.any(g16[:, 4:])
 
 
 def test_general_upstream_gradient(qfx):
