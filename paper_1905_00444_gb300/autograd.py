@@ -10,11 +10,21 @@ from . import qfx
 
 
 def _circuit_with(template, gates_host):
+    """The template with its gate matrices replaced by the rows of gates_host ([n, 4] or
+    [n, 16]): 2x2 for a single-qubit gate, 4 diagonal entries for a diagonal two-qubit
+    gate (its first 4 values), 4x4 for a general one (16 values, rows of width 16 only)."""
     c = copy.copy(template)
     c.gates = []
     for g, m in zip(template.gates, gates_host):
         g2 = copy.copy(g)
-        g2.mat = m.reshape(2, 2).copy() if g.q1 < 0 else m.reshape(4).copy()
+        if g.q1 < 0:
+            g2.mat = m[:4].reshape(2, 2).copy()
+        elif g.mat.size == 16:
+            if m.size != 16:
+                raise ValueError("a general (U4) gate needs gates rows of 16 entries")
+            g2.mat = m.reshape(4, 4).copy()
+        else:
+            g2.mat = m[:4].reshape(4).copy()
         c.gates.append(g2)
     return c
 
@@ -26,8 +36,10 @@ def _make():
         """amp = CircuitAmplitudes.apply(gates, template, x1, n_open, open_sites, cuts)
 
         gates: complex128 [n_gates, 4] (each gate's 2x2 matrix row-major, or the 4 diagonal
-        entries of a two-qubit gate), in the template circuit's gate order.  The backward
-        pass returns dL/dRe + i dL/dIm for every entry (PyTorch's convention)."""
+        entries of a diagonal two-qubit gate) or [n_gates, 16] (also a general gate's 4x4
+        matrix row-major; other gates in their first 4 entries), in the template circuit's
+        gate order.  The backward pass returns dL/dRe + i dL/dIm for every entry (PyTorch's
+        convention), in the same shape."""
 
         @staticmethod
         def forward(ctx, gates, template, x1, n_open: int = 0, open_sites=None, cuts=()):
@@ -36,6 +48,7 @@ def _make():
             ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=x1.device)
             amp = qfx.amplitudes(plan, x1, workspace=ws)
             ctx.plan = plan
+            ctx.entries = int(gates.shape[1])
             ctx.gates_device = gates.device
             ctx.save_for_backward(x1)
             return amp
@@ -43,7 +56,7 @@ def _make():
         @staticmethod
         def backward(ctx, grad_amp):
             (x1,) = ctx.saved_tensors
-            g = qfx.amplitudes_backward(ctx.plan, x1, grad_amp)
+            g = qfx.amplitudes_backward(ctx.plan, x1, grad_amp, entries=ctx.entries)
             return g.to(ctx.gates_device), None, None, None, None, None
 
     return CircuitAmplitudes

@@ -275,3 +275,26 @@ def test_autotune_cache_is_applied(tmp_path):
     # a missing or unreadable cache leaves the defaults
     p2 = qfx.Plan(qfx.Circuit(c), n_open=3, autotune_cache=str(tmp_path / "missing.json"))
     assert [st["variant"] for st in p2.steps] == [st["variant"] for st in base.steps]
+
+
+def test_autograd_circuit_rows_of_sixteen_entries():
+    """The autograd wrapper rebuilds the template from [n, 16] rows: 2x2 from the first 4
+    of a single-qubit gate, the diagonal from the first 4 of a CZ, the 4x4 of a U4 gate;
+    rows of 4 cannot carry a U4 gate.  The rebuilt circuit plans like the template."""
+    from paper_1905_00444_gb300.autograd import _circuit_with
+    c = ri.rqc(3, 3, 8, seed=2, two_qubit="fsim")
+    k = next(i for i, g in enumerate(c.gates) if g.kind == ri.U4)      # one CZ among the fSims
+    c.gates[k] = ri.Gate(c.gates[k].layer, c.gates[k].q0, c.gates[k].q1, ri.CZ, ri.DIAG_CZ.copy())
+    rows = np.zeros((len(c.gates), 16), dtype=np.complex128)
+    for i, g in enumerate(c.gates):
+        flat = np.asarray(g.mat).reshape(-1)
+        rows[i, :flat.size] = flat
+    c2 = _circuit_with(c, rows)
+    for a, b in zip(c.gates, c2.gates):
+        np.testing.assert_array_equal(np.asarray(a.mat).reshape(-1), np.asarray(b.mat).reshape(-1))
+        assert np.asarray(a.mat).shape == np.asarray(b.mat).shape
+    p1 = qfx.Plan(qfx.Circuit(c), n_open=2)
+    p2 = qfx.Plan(qfx.Circuit(c2), n_open=2)
+    assert p1.steps == p2.steps
+    with pytest.raises(ValueError):
+        _circuit_with(c, rows[:, :4])
