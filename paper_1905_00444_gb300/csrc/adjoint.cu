@@ -9,6 +9,9 @@
 //   seed      R_n = upstream gradient of the amplitudes (scaled by 2^-m)
 //   fold      T[idx] = <x| O_M .. O_1 |0>:  dT/dG[a][b] = w_j[a] u_{j-1}[b] with
 //             u_{j-1} = O_{j-1}..O_1|0>, w_j = <x|O_M..O_{j+1}; grad G = sum Gbar_T conj(dT/dG).
+//             A general two-qubit gate's q1 event applies the block B_k of its 2-bit leg k:
+//             the same formula per element, summed separately for each k, and entry
+//             (o1, i1) of B_k (k = 2*o0 + i0) is the gate's G[2*o0 + o1][2*i0 + i1].
 // Boundaries: the forward sweep keeps every step's output when they fit the plan's
 // adjoint_store_bytes; otherwise it keeps the boundary at the start of every line and the
 // reverse sweep recomputes one line's boundaries from its checkpoint before walking it
