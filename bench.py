@@ -8,7 +8,13 @@ one x1 batch through the whole path: fold, scale, 48 contraction steps, FP64 sum
 Counted work is Eq. 1 (F = 8 sqrt(v0 v1 v2) per contraction), 2.256e14 flop per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qfx|reference]
-                  [--workload full|small]
+                  [--workload full|small|kstep|batch|batch_small|permute|adjoint|sample]
+
+Workloads other than full/small print their own JSON line: kstep (the dominant step's
+kernel in one precision), batch / batch_small (the batch scheduler on a config mix or on
+small items), permute (tensor transposes against HBM bandwidth), adjoint (forward and
+backward at 6x6x(1+24+1)), sample (fast sampling with frugal rejection, ideal and at a
+quarter of the paths).
 
 Multi-GPU (torchrun): replicas -- each rank contracts its own x1 batches (no exchange on
 the data path); value is the sum over ranks, time the max over ranks ("weak" scaling).
