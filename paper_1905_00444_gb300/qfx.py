@@ -246,6 +246,26 @@ class Plan:
             self._h = None
 
 
+def _need(t, name, *, dtype=None, size=None, numel=None, device=None):
+    """Refuses what the library would read or write out of bounds: a host tensor, a
+    non-contiguous one, another dtype or element size, fewer elements than the call uses,
+    or another device than the call's."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+    if size is not None and t.element_size() != size:
+        raise ValueError(f"{name} must have {size}-byte elements")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements; the call needs {numel}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}; the call runs on {device}")
+    return t
+
+
 def amplitudes(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Optional[int] = None,
                workspace=None, out=None, stream=None):
     """Amplitudes [n_batch, 2^n_open] (torch complex128 on x1's device).
@@ -253,16 +273,18 @@ def amplitudes(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Optional[int]
     x1: torch int64/uint64 CUDA tensor of bitstrings.  workspace: torch uint8 CUDA tensor
     (default: room for one work item)."""
     import torch
-    if not x1.is_cuda:
-        raise ValueError("x1 must be a CUDA tensor")
+    _need(x1, "x1", size=8)
     n_batch = x1.numel()
     if slice_end is None:
         slice_end = plan.n_slices
     if workspace is None:
         workspace = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=x1.device)
+    _need(workspace, "workspace", dtype=torch.uint8, device=x1.device)
     if out is None:
         out = torch.empty((n_batch, 1 << len(plan.open_sites)), dtype=torch.complex128,
                           device=x1.device)
+    _need(out, "out", dtype=torch.complex128, numel=n_batch << len(plan.open_sites),
+          device=x1.device)
     _check(lib.qfx_amplitudes(plan._h, x1.data_ptr(), n_batch, slice_begin, slice_end,
                               workspace.data_ptr(), workspace.numel(), out.data_ptr(),
                               _stream_ptr(stream)))
@@ -277,14 +299,17 @@ def amplitudes_backward(plan: Plan, x1, grad_out, *, slice_begin: int = 0,
     entries = 4 (single-qubit and diagonal gates) or 16 (any gates, U4 included: entry
     4*r + c of a U4 gate is G[r][c]; other gates fill their first 4)."""
     import torch
+    _need(x1, "x1", size=8)
     if slice_end is None:
         slice_end = plan.n_slices
     if workspace is None:
         workspace = torch.empty(plan.backward_workspace_bytes(), dtype=torch.uint8,
                                 device=x1.device)
+    _need(workspace, "workspace", dtype=torch.uint8, device=x1.device)
     if entries not in (4, 16):
         raise ValueError("entries must be 4 or 16")
-    grad_out = grad_out.to(torch.complex128).contiguous()
+    grad_out = grad_out.to(device=x1.device, dtype=torch.complex128).contiguous()
+    _need(grad_out, "grad_out", numel=x1.numel() << len(plan.open_sites))
     out = torch.empty((plan.stats_n_gates, entries), dtype=torch.complex128, device=x1.device)
     f = lib.qfx_amplitudes_backward if entries == 4 else lib.qfx_amplitudes_backward_full
     _check(f(plan._h, x1.data_ptr(), x1.numel(), slice_begin, slice_end, grad_out.data_ptr(),
@@ -300,14 +325,14 @@ def frugal_select(plan: Plan, x1, amps, u, scan_mask, M: float = 10.0, *, stream
     (x2 int64 [n_batch], -1 where no candidate was accepted; bitstrings int64 [n_batch],
     x1 with the open-site bits set from x2)."""
     import torch
+    _need(x1, "x1", size=8)
     n_batch = x1.numel()
     per = 1 << len(plan.open_sites)
-    if amps.dtype != torch.complex128 or tuple(amps.shape) != (n_batch, per) or not amps.is_contiguous():
-        raise ValueError("amps must be a contiguous complex128 [n_batch, 2^n_open] tensor")
-    if u.dtype != torch.float64 or tuple(u.shape) != (n_batch, per) or not u.is_contiguous():
-        raise ValueError("u must be a contiguous float64 [n_batch, 2^n_open] tensor")
-    if scan_mask.numel() != n_batch or scan_mask.element_size() != 8:
-        raise ValueError("scan_mask must hold n_batch 64-bit integers")
+    _need(amps, "amps", dtype=torch.complex128, numel=n_batch * per, device=x1.device)
+    _need(u, "u", dtype=torch.float64, numel=n_batch * per, device=x1.device)
+    _need(scan_mask, "scan_mask", size=8, numel=n_batch, device=x1.device)
+    if tuple(amps.shape) != (n_batch, per) or tuple(u.shape) != (n_batch, per):
+        raise ValueError("amps and u must be [n_batch, 2^n_open]")
     x2 = torch.empty(n_batch, dtype=torch.int64, device=x1.device)
     bits = torch.empty(n_batch, dtype=torch.int64, device=x1.device)
     _check(lib.qfx_frugal_select(plan._h, x1.data_ptr(), n_batch, amps.data_ptr(), u.data_ptr(),
@@ -342,6 +367,7 @@ class Batch:
         arr = (BatchItem * len(items))()
         self.outs = []
         for i, (plan, x1, sb, se) in enumerate(items):
+            _need(x1, f"items[{i}] x1", size=8, device=items[0][1].device)
             out = torch.empty((x1.numel(), 1 << len(plan.open_sites)), dtype=torch.complex128,
                               device=x1.device)
             self.outs.append(out)
@@ -352,6 +378,7 @@ class Batch:
         if workspace is None:
             nbytes = int(lib.qfx_batch_workspace_bytes(arr, len(items), slots))
             workspace = torch.empty(nbytes, dtype=torch.uint8, device=items[0][1].device)
+        _need(workspace, "workspace", dtype=torch.uint8, device=items[0][1].device)
         self.workspace = workspace
         h = C.c_void_p()
         _check(lib.qfx_batch_prepare(arr, len(items), workspace.data_ptr(), workspace.numel(),
@@ -377,6 +404,7 @@ def autotune(plan: Plan, cache_path: str, *, workspace=None, stream=None):
     if workspace is None:
         workspace = torch.empty(min(plan.workspace_bytes(1), 4 << 30), dtype=torch.uint8,
                                 device="cuda")
+    _need(workspace, "workspace", dtype=torch.uint8)
     _check(lib.qfx_autotune(plan._h, cache_path.encode(), workspace.data_ptr(), workspace.numel(),
                             _stream_ptr(stream)))
 
@@ -390,14 +418,15 @@ def amplitudes_static(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Option
     caller's workspace (for callers that cannot allocate device memory; the output
     buffer is still the caller's).  Calls that overlap on the GPU race on that array."""
     import torch
-    if not x1.is_cuda:
-        raise ValueError("x1 must be a CUDA tensor")
+    _need(x1, "x1", size=8)
     n_batch = x1.numel()
     if slice_end is None:
         slice_end = plan.n_slices
     if out is None:
         out = torch.empty((n_batch, 1 << len(plan.open_sites)), dtype=torch.complex128,
                           device=x1.device)
+    _need(out, "out", dtype=torch.complex128, numel=n_batch << len(plan.open_sites),
+          device=x1.device)
     _check(lib.qfx_amplitudes_static(plan._h, x1.data_ptr(), n_batch, slice_begin, slice_end,
                                      out.data_ptr(), _stream_ptr(stream)))
     return out
@@ -422,11 +451,16 @@ def contract_step(S, B, P, K, N, NL, Sd, *, out=None, variant: int = -1, precisi
                   scratch=None, stream=None):
     """C[nh][p][nl][s] = sum_k S[k][nh*NL+nl] B[p][k][s] on complex64 CUDA tensors."""
     import torch
+    _need(S, "S", dtype=torch.complex64, numel=K * N)
+    _need(B, "B", dtype=torch.complex64, numel=P * K * Sd, device=S.device)
     if out is None:
         out = torch.empty(P * N * Sd, dtype=torch.complex64, device=S.device)
+    _need(out, "out", dtype=torch.complex64, numel=P * N * Sd, device=S.device)
     need = step_scratch_bytes(K, N, precision)
     if scratch is None and need:
         scratch = torch.empty(need, dtype=torch.uint8, device=S.device)
+    if scratch is not None:
+        _need(scratch, "scratch", dtype=torch.uint8, numel=need, device=S.device)
     sp, sb = (scratch.data_ptr(), scratch.numel()) if scratch is not None else (None, 0)
     _check(lib.qfx_contract_step(S.data_ptr(), B.data_ptr(), out.data_ptr(), P, K, N, NL, Sd,
                                  PRECISIONS[precision], variant, sp, sb, _stream_ptr(stream)))
@@ -436,8 +470,13 @@ def contract_step(S, B, P, K, N, NL, Sd, *, out=None, variant: int = -1, precisi
 def permute(x, shape: Sequence[int], perm: Sequence[int], *, out=None, stream=None):
     """out = x viewed with `shape`, axes reordered by `perm` (complex64 CUDA tensors)."""
     import torch
+    n = 1
+    for d in shape:
+        n *= int(d)
+    _need(x, "x", dtype=torch.complex64, numel=n)
     if out is None:
         out = torch.empty(x.numel(), dtype=torch.complex64, device=x.device)
+    _need(out, "out", dtype=torch.complex64, numel=n, device=x.device)
     r = len(shape)
     sh = (C.c_int64 * r)(*shape)
     pm = (C.c_int32 * r)(*perm)

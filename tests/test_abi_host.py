@@ -298,3 +298,27 @@ def test_autograd_circuit_rows_of_sixteen_entries():
     assert p1.steps == p2.steps
     with pytest.raises(ValueError):
         _circuit_with(c, rows[:, :4])
+
+
+def test_binding_refuses_host_and_short_tensors_before_any_launch():
+    """Host pointers or undersized buffers would reach the kernels as wild addresses: the
+    binding checks device, layout, dtype and size first (all on CPU here, so every call
+    must refuse)."""
+    torch = pytest.importorskip("torch")
+    p = qfx.Plan(qfx.Circuit(ri.rqc(2, 2, 8, seed=0)), n_open=1)
+    x1 = torch.zeros(2, dtype=torch.int64)
+    with pytest.raises(ValueError, match="CUDA"):
+        qfx.amplitudes(p, x1)
+    with pytest.raises(ValueError, match="CUDA"):
+        qfx.amplitudes_static(p, x1)
+    with pytest.raises(ValueError, match="CUDA"):
+        qfx.amplitudes_backward(p, x1, torch.zeros((2, 2), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="CUDA"):
+        qfx.frugal_select(p, x1, torch.zeros((2, 2), dtype=torch.complex128),
+                          torch.zeros((2, 2), dtype=torch.float64), torch.zeros(2, dtype=torch.int64))
+    S = torch.zeros(16, dtype=torch.complex64)
+    with pytest.raises(ValueError, match="CUDA"):
+        qfx.contract_step(S, S, 1, 4, 4, 4, 1)
+    with pytest.raises(ValueError, match="CUDA"):
+        qfx.permute(S, (4, 4), (1, 0))
+    assert qfx.launch_count() == 0
