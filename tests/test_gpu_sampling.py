@@ -46,7 +46,7 @@ def test_select_matches_oracle_bitwise(qfx, n_open, n_batch):
     amps = ri.random_complex((n_batch, per), seed=7 + n_open).astype(np.complex128)
     amps *= np.sqrt(0.5 / 2.0 ** n)
     if per > 256:
-        amps[0, [t ^ int(masks[0]) for t in range(300)]] = 0   # first acceptance past round 1
+        amps[0, [t ^ int(masks[0]) for t in range(300)]] = 0   # first acceptance past the first 256-candidate scan
     amps[-1, :] *= 1e-6                                          # (almost surely) no sample
     M = 10.0
     want_x2, want_bits = oracle_select(amps, x1s, masks, u, n, M, open_sites)
