@@ -7,8 +7,8 @@
 // fraction f of the slices is noisy sampling at fidelity about f (Sec. III.C); the caller
 // then passes M * f.
 //
-// One block per batch scans 256 candidates per round and stops at the first round with
-// an acceptance.  The acceptance is evaluated with explicit round-to-nearest operations
+// One block per batch scans 256 candidates per pass and stops at the first pass with an
+// acceptance.  The acceptance is evaluated with explicit round-to-nearest operations
 // (p = re*re + im*im, then p * (2^n / M), no fused multiply-add), so the decision is the
 // one an FP64 evaluation in that order makes.
 #include <cuda_runtime.h>
