@@ -38,6 +38,15 @@ struct Leg {
   int64_t dim;
 };
 
+// Tensor sizes are products of bond dimensions of up to 2^40 each, so they are formed with
+// a product that saturates at 2^62 instead of overflowing; a plan whose largest tensor
+// exceeds kMaxPlanElements is refused.
+constexpr int64_t kSat = int64_t(1) << 62;
+constexpr int64_t kMaxPlanElements = int64_t(1) << 50;
+int64_t smul(int64_t a, int64_t b) {   // a, b >= 1
+  return a > kSat / b ? kSat : std::min(a * b, kSat);
+}
+
 struct SimResult {
   bool ok = true;
   std::string err;
@@ -60,7 +69,7 @@ SimResult simulate(const Geometry& geo, const std::vector<int>& order, const Slo
     int q = order[si];
     const auto& s = slots[q];
     int64_t xd = is_open[q] ? 2 : 1;
-    int64_t site_size = d(s[0]) * d(s[1]) * xd * d(s[2]) * d(s[3]);
+    int64_t site_size = smul(smul(smul(smul(d(s[0]), d(s[1])), xd), d(s[2])), d(s[3]));
     r.peak = std::max(r.peak, site_size);
     std::vector<Leg> nlegs;
     if (is_open[q]) { nlegs.push_back({-(1 + q), 2}); r.intro.push_back(q); }
@@ -69,8 +78,8 @@ SimResult simulate(const Geometry& geo, const std::vector<int>& order, const Slo
     if (s[3] >= 0) rd.push_back({s[3], d(s[3])});
     qfx::Step st{};
     st.site = q;
-    st.N = xd * d(s[2]) * d(s[3]);
-    st.NL = d(s[2]) * d(s[3]);
+    st.N = smul(smul(xd, d(s[2])), d(s[3]));
+    st.NL = smul(d(s[2]), d(s[3]));
     if (si == 0) {
       if (s[0] >= 0 || s[1] >= 0) { r.ok = false; r.err = "first site has contracted bonds"; return r; }
       st.P = st.K = st.Sd = 1;
@@ -92,9 +101,9 @@ SimResult simulate(const Geometry& geo, const std::vector<int>& order, const Slo
     for (size_t j = 0; j < kids.size(); ++j)
       if (bnd[pos + j].id != kids[j]) { r.ok = false; r.err = "kink legs not adjacent"; return r; }
     int64_t P = 1, K = 1, Sd = 1;
-    for (size_t i = 0; i < pos; ++i) P *= bnd[i].dim;
-    for (size_t j = 0; j < kids.size(); ++j) K *= bnd[pos + j].dim;
-    for (size_t i = pos + kids.size(); i < bnd.size(); ++i) Sd *= bnd[i].dim;
+    for (size_t i = 0; i < pos; ++i) P = smul(P, bnd[i].dim);
+    for (size_t j = 0; j < kids.size(); ++j) K = smul(K, bnd[pos + j].dim);
+    for (size_t i = pos + kids.size(); i < bnd.size(); ++i) Sd = smul(Sd, bnd[i].dim);
     st.P = P; st.K = K; st.Sd = Sd;
     st.flops = 8.0 * (double)P * (double)K * (double)st.N * (double)Sd;
     st.bytes = 8.0 * ((double)P * K * Sd + (double)K * st.N + (double)P * st.N * Sd);
@@ -103,7 +112,7 @@ SimResult simulate(const Geometry& geo, const std::vector<int>& order, const Slo
     nb.insert(nb.end(), rd.begin(), rd.end());
     nb.insert(nb.end(), bnd.begin() + pos + kids.size(), bnd.end());
     bnd.swap(nb);
-    int64_t out_el = P * st.N * Sd;
+    int64_t out_el = smul(smul(P, st.N), Sd);
     if (out_el > r.peak) { r.peak = out_el; r.peak_count = 0; }
     if (out_el == r.peak) r.peak_count++;
     r.flops += st.flops;
@@ -233,7 +242,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       for (int e : cut_edges) s *= (double)full[e] / (double)dims[e];
       return s;
     };
-    while (cap > 0 && (uint64_t)sim.peak * 8ull > cap) {
+    while (cap > 0 && (uint64_t)sim.peak > cap / 8) {
       int best = -1;
       SimResult best_sim;
       double best_work = 0;
@@ -259,6 +268,12 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       if (std::find(cut_edges.begin(), cut_edges.end(), best) == cut_edges.end()) cut_edges.push_back(best);
       sim = best_sim;
     }
+    if (sim.peak > kMaxPlanElements)
+      return qfx::fail(QFX_EPLAN, "largest intermediate above 2^50 elements: cut bonds or set "
+                                  "max_intermediate_bytes");
+    for (int e = 0; e < E; ++e)
+      if (edim[e] > (int64_t(1) << 30))
+        return qfx::fail(QFX_EPLAN, "a bond keeps more than 2^30 values after its cuts: cut it");
     double nsl = slices_of(edim);
     if (nsl > 4.0e18) return qfx::fail(QFX_EPLAN, "too many slices");
 

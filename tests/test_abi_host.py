@@ -183,6 +183,24 @@ def test_bad_cuts_rejected(cuts):
         qfx.Plan(qfx.Circuit(c), cuts=cuts)
 
 
+def test_oversized_plans_refused_without_overflow():
+    """Deep circuits make tensor sizes (products of bond dimensions up to 2^40) exceed
+    int64; the planner saturates them and refuses plans above 2^50 elements, and bonds
+    that keep more than 2^30 values after their cuts."""
+    c = ri.rqc(8, 8, 128, seed=0)                   # bond 2^16 per edge: boundary 2^144
+    with pytest.raises(qfx.QfxError, match="2\\^50") as e:
+        qfx.Plan(qfx.Circuit(c), n_open=4)
+    assert e.value.status == q.QFX_EPLAN
+    with pytest.raises(qfx.QfxError) as e:
+        qfx.Plan(qfx.Circuit(c), n_open=4, max_intermediate_bytes=1 << 30)
+    assert e.value.status == q.QFX_EPLAN
+    wide = ri.Circuit(1, 2, [ri.Gate(l, 0, 1, ri.CZ, ri.DIAG_CZ.copy()) for l in range(33)])
+    with pytest.raises(qfx.QfxError, match="2\\^30"):
+        qfx.Plan(qfx.Circuit(wide), n_open=1)
+    p = qfx.Plan(qfx.Circuit(wide), n_open=1, cuts=[(0, 1, 1 << 20)])
+    assert p.n_slices == 1 << 13 and p.stats["max_elements"] <= 2 << 20
+
+
 def test_impossible_cap_is_eplan():
     c = ri.rqc(3, 3, 8, seed=0)
     with pytest.raises(qfx.QfxError) as e:
