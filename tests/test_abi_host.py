@@ -101,7 +101,8 @@ def test_bond_bit_limit_counts_two_bits_per_general_gate():
     gates = [ri.Gate(l, 0, 1, ri.U4, ri.fsim(0.3, 0.2)) for l in range(21)]   # 42 bits
     with pytest.raises(qfx.QfxError, match="40 bond bits"):
         qfx.Plan(qfx.Circuit(ri.Circuit(1, 2, gates)), n_open=1)
-    qfx.Plan(qfx.Circuit(ri.Circuit(1, 2, gates[:20])), n_open=1)          # 40 bits: fine
+    forty = qfx.Circuit(ri.Circuit(1, 2, gates[:20]))                        # 40 bits: fine,
+    qfx.Plan(forty, n_open=1, cuts=[(0, 1, 1 << 20)])                          # once cut
 
 
 def test_backward_rejects_general_gates_before_any_launch():
