@@ -151,7 +151,8 @@ typedef struct {
  * C[nh][p][nl][s] = sum_k S[k][nh*NL+nl] * B[p][k][s] with no tensor transpose; then it
  * adds cuts (greedily halving the bond that keeps the total work lowest) until the
  * largest intermediate fits the cap.
- * Errors: QFX_EINVAL (bad options), QFX_EPLAN (cap cannot be met). */
+ * Errors: QFX_EINVAL (bad options), QFX_EPLAN (cap cannot be met, largest tensor above
+ * 2^50 elements, or a bond that keeps more than 2^30 values after its cuts). */
 qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts* opts, qfx_plan** out);
 void qfx_plan_destroy(qfx_plan* p);
 
