@@ -130,3 +130,20 @@ def test_stabilizer_matches_statevector_fsim_pi2(shape):
     for x in xs:
         assert abs(stabilizer.probability(c, int(x), tab) - p[int(x)]) < 1e-12
     assert np.count_nonzero(p > 1e-12) > 1      # not a product of basis states
+
+
+def test_planted_swapped_leg_indices_are_caught(monkeypatch):
+    """o0 and i0 exchanged in the split (a plausible slip): the closed form fails."""
+    real = network.site_tensor
+
+    def wrong(circuit, q, x_bit, fixed):
+        c2 = circuit.copy()
+        for g in c2.gates:
+            m = np.asarray(g.mat)
+            if m.size == 16:
+                g.mat = m.reshape(2, 2, 2, 2).transpose(2, 1, 0, 3).reshape(4, 4)   # o0 <-> i0
+        return real(c2, q, x_bit, fixed)
+
+    monkeypatch.setattr(network, "site_tensor", wrong)
+    with pytest.raises(AssertionError):
+        test_single_general_gate_closed_form(True)

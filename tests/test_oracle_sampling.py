@@ -13,6 +13,8 @@ noisy sampling from a fraction of the paths).  CPU only.
   (64 paths) sample at fidelity about 1/4.  The paths come from state vectors of the
   circuit with each cut CZ replaced by one term of its split, and one of them is checked
   against the tensor-network oracle's slice.
+- Planted mistakes (a non-strict threshold, an ignored scan mask, a missing 2^n in the
+  acceptance) each fail one of these pins.
 """
 import copy
 
@@ -160,3 +162,35 @@ def test_quarter_of_the_paths_samples_at_fidelity_a_quarter(rqc_4x4x24):
     smp = sampling.frugal_sample(amp_fn, n, open_sites, x1s, masks, u, 10.0 * 0.25)
     got = sampling.linear_xeb(p[smp], n)
     assert abs(got - xeb_q) < 4 * _xeb_sigma(p[smp], n), (got, xeb_q)
+
+
+# --- planted mistakes: each must be caught by a pin above ---------------------------
+
+def _select_with(accept_cmp, use_mask=True):
+    def select(amps, n, M, u, mask):
+        for t in range(len(amps)):
+            x2 = t ^ int(mask) if use_mask else t
+            if accept_cmp(float(u[t]), sampling.acceptance(amps[x2], n, M)):
+                return x2
+        return -1
+    return select
+
+
+def test_planted_non_strict_threshold_is_caught(monkeypatch):
+    monkeypatch.setattr(sampling, "frugal_select", _select_with(lambda u, a: u <= a))
+    with pytest.raises(AssertionError):
+        test_threshold_is_strict_and_exact()
+
+
+def test_planted_ignored_scan_mask_is_caught(monkeypatch):
+    monkeypatch.setattr(sampling, "frugal_select", _select_with(lambda u, a: u < a, use_mask=False))
+    with pytest.raises(AssertionError):
+        test_zero_variates_accept_first_nonzero_candidate()
+
+
+def test_planted_missing_dimension_factor_is_caught(monkeypatch):
+    # acceptance |amp|^2 / M instead of 2^n |amp|^2 / M
+    monkeypatch.setattr(sampling, "acceptance",
+                        lambda amp, n, M: (amp.real ** 2 + amp.imag ** 2) / M)
+    with pytest.raises(AssertionError):
+        test_batch_distribution_matches_enumeration_over_masks()
