@@ -341,3 +341,58 @@ def test_binding_refuses_host_and_short_tensors_before_any_launch():
     with pytest.raises(ValueError, match="CUDA"):
         qfx.permute(S, (4, 4), (1, 0))
     assert qfx.launch_count() == 0
+
+
+def test_planner_invariants_on_random_circuits():
+    """Seeded random grids, depths, gate kinds, open sites, forced cuts and caps: every plan
+    chains its steps (each step reads exactly what the previous one wrote), ends with the
+    2^|x2| outputs, counts Eq. 1 per step, covers every site once, has as many slices as
+    its cuts' radices multiply to (2^bits per bond, two bits per U4 gate) and meets its
+    cap."""
+    rng = np.random.default_rng(2024)
+    for case in range(150):
+        rows, cols = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+        if rows * cols < 2:
+            cols = 2
+        depth = int(rng.choice([0, 4, 8, 12, 16]))
+        kind = "fsim" if rng.random() < 0.4 else "cz"
+        c = ri.rqc(rows, cols, depth, seed=case, two_qubit=kind)
+        n = rows * cols
+        n_open = int(rng.integers(0, min(6, n) + 1))
+        bits = {}
+        for g in c.gates:
+            if g.q1 >= 0:
+                e = (min(g.q0, g.q1), max(g.q0, g.q1))
+                bits[e] = bits.get(e, 0) + (2 if g.kind == ri.U4 else 1)
+        cuts = []
+        for e in rng.permutation(sorted(bits))[:int(rng.integers(0, 3))]:
+            m = bits[tuple(e)]
+            cuts.append((int(e[0]), int(e[1]), 1 << int(rng.integers(0, m + 1))))
+        base = qfx.Plan(qfx.Circuit(c), n_open=n_open, cuts=cuts)
+        cap = 0
+        if rng.random() < 0.3 and base.stats["max_elements"] > 64:
+            # a quarter of the uncapped peak, but not below the 2^|x2| outputs, which no
+            # cut can shrink
+            cap = max(base.stats["max_elements"] * 8 // 4, 8 << n_open)
+        p = qfx.Plan(qfx.Circuit(c), n_open=n_open, cuts=cuts, max_intermediate_bytes=cap)
+        st = p.steps
+        assert sorted(s["site"] for s in st) == list(range(n)), case
+        assert (st[0]["P"], st[0]["K"], st[0]["Sd"], st[0]["flops"]) == (1, 1, 1, 0), case
+        prev_out = st[0]["N"]
+        total = 0.0
+        for s in st[1:]:
+            assert s["P"] * s["K"] * s["Sd"] == prev_out, case
+            assert s["N"] % s["NL"] == 0 and s["N"] // s["NL"] in (1, 2), case
+            assert s["flops"] == 8.0 * s["P"] * s["K"] * s["N"] * s["Sd"], case
+            prev_out = s["P"] * s["N"] * s["Sd"]
+            total += s["flops"]
+        assert prev_out == 1 << n_open, case
+        assert p.stats["flops_per_item"] == pytest.approx(total, rel=1e-12), case
+        assert p.stats["max_elements"] == max(s["P"] * s["N"] * s["Sd"] for s in st[1:]), case
+        assert p.cuts[:len(cuts)] == cuts, case
+        want_slices = 1
+        for (a, b, size) in p.cuts:
+            want_slices *= (1 << bits[(min(a, b), max(a, b))]) // size
+        assert p.n_slices == want_slices, case
+        if cap:
+            assert p.stats["max_elements"] * 8 <= cap, case
