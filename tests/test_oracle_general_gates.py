@@ -147,3 +147,35 @@ def test_planted_swapped_leg_indices_are_caught(monkeypatch):
     monkeypatch.setattr(network, "site_tensor", wrong)
     with pytest.raises(AssertionError):
         test_single_general_gate_closed_form(True)
+
+
+def test_random_circuits_network_slices_match_statevector():
+    """Seeded random small grids (CZ or fSim), open sites and cuts (whole bonds or their
+    high bits, which may split a 2-bit leg): the network route's slices sum to the state
+    vector's amplitudes."""
+    rng = np.random.default_rng(77)
+    for case in range(30):
+        rows, cols = int(rng.integers(1, 4)), int(rng.integers(2, 5))
+        depth = int(rng.choice([4, 8, 12]))
+        c = ri.rqc(rows, cols, depth, seed=100 + case,
+                   two_qubit="fsim" if rng.random() < 0.5 else "cz")
+        n = c.n_qubits
+        psi = statevector.amplitudes(c)
+        legs = network.bond_legs(c)
+        edges = sorted(legs)
+        cuts = []
+        for k in rng.permutation(len(edges))[:int(rng.integers(0, 3))]:
+            e = edges[k]
+            m = sum(network.leg_bits(c.gates[g]) for g in legs[e])
+            cuts.append((e[0], e[1], 1 << int(rng.integers(0, m))))
+        open_sites = sorted(int(q) for q in rng.permutation(n)[:int(rng.integers(0, min(4, n) + 1))])
+        x1 = int(ri.random_bitstrings(n, 1, seed=case)[0])
+        S = network.n_slices(c, cuts)
+        got = network.amplitudes_sliced(c, x1, open_sites, cuts, range(S))
+        idx = []
+        for j in range(1 << len(open_sites)):
+            x = x1
+            for i, q in enumerate(open_sites):
+                x = (x & ~(1 << q)) | (((j >> i) & 1) << q)
+            idx.append(x)
+        np.testing.assert_allclose(got, psi[idx], atol=1e-12, err_msg=f"case {case}")
