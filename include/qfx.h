@@ -17,11 +17,15 @@
  *   - Every call returns a qfx_status.  On failure, qfx_last_error() (thread-local) holds
  *     a message.  No exception crosses the ABI and nothing aborts the process.
  *   - Host objects (qfx_circuit, qfx_plan) are opaque, owned by the library, created by
- *     *_create and freed by *_destroy.  They are immutable after creation (the plan's
- *     device tables are uploaded once per device under a lock) and may be shared
- *     between threads.
+ *     *_create and freed by *_destroy.  They are immutable after creation and may be
+ *     shared between threads.  A plan holds a host image of its tables (fold program,
+ *     gate matrices, cuts, output order; a few hundred KB at most for the paper's
+ *     shapes); the first compute call with a plan page-locks that image (under a lock;
+ *     qfx_plan_upload does it explicitly).
  *   - All device buffers (inputs, outputs, workspace) are owned by the caller.  The
- *     compute entry points allocate no device memory, so they can run on any stream.
+ *     compute entry points allocate no device memory: every call copies the plan's table
+ *     image into the first bytes of the caller's workspace (an asynchronous copy on the
+ *     call's stream) and keeps all other scratch there too.
  *   - `stream` arguments are cudaStream_t values passed as void* (NULL = legacy stream).
  */
 #ifndef QFX_H
@@ -189,8 +193,11 @@ qfx_status qfx_plan_cut(const qfx_plan* p, int32_t i, qfx_cut* out);
 /* The plan's x2 qubits, in output-bit order (out must hold n_open entries). */
 qfx_status qfx_plan_open_sites(const qfx_plan* p, int32_t* out);
 
-/* Uploads the plan's tables to the current device (done implicitly by the first compute
- * call on a device, which is then synchronous; call this first before stream capture). */
+/* Page-locks the plan's host table image so that the copy every compute call makes from
+ * it is asynchronous and can be recorded into a CUDA graph.  The first compute call with
+ * the plan does this implicitly; make that call, or this one, before any stream capture.
+ * If the system refuses to page-lock the image, it stays pageable (the copies stay
+ * correct but may make the host wait for the stream).  Allocates no device memory. */
 qfx_status qfx_plan_upload(const qfx_plan* p);
 
 /* Amplitudes (Sec. III.A-III.B; the sum over paths of Sec. III.A and III.C).
@@ -198,7 +205,9 @@ qfx_status qfx_plan_upload(const qfx_plan* p);
  *   slices    [slice_begin, slice_end) of the plan's n_slices; a sub-range gives that
  *             range's contribution (sharding, or a fraction of paths).
  *   workspace device, ws_bytes >= qfx_plan_stats.workspace_min, 256-byte aligned; more
- *             workspace lets more (slice, x1) items run concurrently.
+ *             workspace lets more (slice, x1) items run concurrently.  Its first bytes
+ *             receive the plan's tables (copied on `stream` by every call), the rest the
+ *             per-item headers, boundary tensors and site tensors.
  *   out       device complex128 [n_batch][2^n_open], overwritten with
  *             2^(sum of per-site scale exponents) * sum over slices (in slice order, FP64).
  * Asynchronous on `stream`.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA. */
@@ -219,7 +228,10 @@ qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int64_t n_batch
  *   fit in it, else QFX_ENOMEM with both sizes in the message.
  *   Allocates nothing.  The first call on a device looks up the array's device address
  *   (make it before any stream capture).  All calls share the array: calls that overlap
- *   on the GPU race, and each call rewrites what it reads. */
+ *   on the GPU race, and each call rewrites what it reads.  The plan's tables are copied
+ *   into the array from the plan's own host image; this entry point does not page-lock
+ *   that image, so unless qfx_plan_upload or another call has, the copy is from pageable
+ *   memory and may make the host wait for work already queued on the stream. */
 qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
                                  int64_t slice_begin, int64_t slice_end, double* out,
                                  void* stream);
@@ -248,8 +260,8 @@ typedef struct qfx_batch qfx_batch;
 /* Workspace that lets `slots` work items be in flight at once (an upper bound). */
 uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32_t n_items, int64_t slots);
 
-/* Builds the schedule and uploads it into `workspace` (synchronously on `stream`; also
- * uploads plan tables).  The workspace, items' x1 and out buffers must stay valid while
+/* Builds the schedule and uploads it into `workspace` (synchronously on `stream`),
+ * together with one copy of each distinct plan's tables at the workspace's start.  The workspace, items' x1 and out buffers must stay valid while
  * the batch is used.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA. */
 qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_items, void* workspace,
                              size_t ws_bytes, qfx_batch** out, void* stream);
@@ -381,6 +393,21 @@ qfx_status qfx_profile_enable(int32_t on);
 /* Waits for the recorded events; copies up to `max` records; returns the count in *n
  * and clears the record list. */
 qfx_status qfx_profile_collect(qfx_kernel_time* out, int32_t max, int32_t* n);
+
+/* Test hooks (not needed for computing).  Each makes one bounded device wait run out on
+ * purpose, so that the error path -- the waiting kernel records QFX_ETIMEOUT in its status
+ * word, every CTA returns, the context stays usable -- can be tested without faulting or
+ * hanging the GPU.  The paper has no counterpart.
+ *   qfx_debug_permute_withhold: the calling thread's next qfx_permute that takes the
+ *     tensor-map path issues none of its copies and waits at most wait_ns (1e3..1e9) for
+ *     them; the output is left unwritten and qfx_sync reports QFX_ETIMEOUT.
+ *   qfx_debug_batch_stall: one dependency of a persistent-kernel batch's schedule is made
+ *     unreachable and every dependency wait is limited to wait_ns (1e3..5e9); the next
+ *     qfx_batch_run gives up after wait_ns and qfx_sync reports QFX_ETIMEOUT.  The batch
+ *     is broken for good (destroy it).  QFX_EUNSUPPORTED for graph batches.
+ * Errors: QFX_EINVAL (bad argument), QFX_ECUDA. */
+qfx_status qfx_debug_permute_withhold(int64_t wait_ns);
+qfx_status qfx_debug_batch_stall(qfx_batch* b, int64_t wait_ns);
 
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t qfx_launch_count(void);

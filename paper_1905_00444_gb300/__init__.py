@@ -11,7 +11,7 @@ _build()
 from .qfx import (  # noqa: E402,F401
     Batch, Circuit, Plan, QfxError, amplitudes, amplitudes_backward, amplitudes_static, contract_step, header_symbols, launch_count, lib,
     autotune, frugal_sample, frugal_select, permute, profile_collect, profile_enable, sync,
-    tensor_peak, version,
+    tensor_peak, version, debug_permute_withhold,
 )
 from .sharding import partition_slices, reduce_partials  # noqa: E402,F401
 from .autograd import CircuitAmplitudes, circuit_amplitudes  # noqa: E402,F401

@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kT) gate_accum_kernel(const int32_t* __restric
 }
 
 struct BwdLayout {
-  uint64_t hdr, sites, sgrad, ckpt, lb, rr, gpart, bpart, evgrad, partoff, total;
+  uint64_t tab, hdr, sites, sgrad, ckpt, lb, rr, gpart, bpart, evgrad, total;
 };
 
 // Every step output is kept (no recomputation in the reverse sweep) when all of them fit in
@@ -542,6 +542,7 @@ BwdLayout bwd_layout(const qfx_plan* p) {
   BwdLayout L{};
   const uint64_t B = a256((uint64_t)p->max_elements * 8);
   uint64_t o = 0;
+  L.tab = o; o += table_bytes(p);   // the plan's tables, copied in by every call
   L.hdr = o; o += a256((uint64_t)p->n * 8 + 16);
   L.sites = o; o += a256((uint64_t)p->site_total * 8);
   L.sgrad = o; o += a256((uint64_t)p->site_total * 8);
@@ -564,12 +565,17 @@ BwdLayout bwd_layout(const qfx_plan* p) {
   for (const auto& fs : p->sites) bp += (uint64_t)((fs.size + kT - 1) / kT) * site_slots(p, fs) * 8;
   L.bpart = o; o += a256(bp * 8);
   L.evgrad = o; o += a256((uint64_t)p->events.size() * 32 * 8);
-  L.partoff = o; o += a256((uint64_t)p->n * 8);
   L.total = o;
   return L;
 }
 
 }  // namespace
+
+// Fold-adjoint partials of one site: one slot per event slot for each 256-element block.
+int64_t adjoint_site_partials(const qfx_plan* p, const FoldSite& fs) {
+  return ((fs.size + kT - 1) / kT) * site_slots(p, fs) * 8;
+}
+
 }  // namespace qfx
 
 using namespace qfx;
@@ -601,12 +607,11 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
                                     "slots (a general gate's block takes 4)");
   const BwdLayout Lw = bwd_layout(p);
   if (ws_bytes < Lw.total) return fail(QFX_ENOMEM, "qfx_amplitudes_backward: workspace smaller than qfx_backward_workspace_bytes()");
-  const DeviceTables* tp = nullptr;
-  s = ensure_tables(p, &tp);
-  if (s != QFX_OK) return s;
-  const DeviceTables& t = *tp;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
+  DeviceTables t;
+  s = stage_tables(p, ws + Lw.tab, stream, &t);
+  if (s != QFX_OK) return s;
   const uint64_t B = a256((uint64_t)p->max_elements * 8);
   const int n = p->n, L = p->line_len, W = p->lines;
   const bool full = full_store(p);
@@ -614,20 +619,7 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
   const int64_t per = int64_t(1) << n_open;
   int64_t max_site = 1;
   for (const auto& fs : p->sites) max_site = std::max(max_site, fs.size);
-
-  // per-site offsets of the fold-adjoint partials (host -> workspace, once per call)
-  std::vector<int64_t> partoff(n);
-  {
-    int64_t o = 0;
-    for (int q = 0; q < n; ++q) {
-      partoff[q] = o;
-      const auto& fs = p->sites[q];
-      o += ((fs.size + kT - 1) / kT) * site_slots(p, fs) * 8;
-    }
-  }
-  cudaError_t e = cudaMemcpyAsync(ws + Lw.partoff, partoff.data(), n * sizeof(int64_t),
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: partial offsets");
+  cudaError_t e;
   e = cudaMemsetAsync(grad_gates, 0, (size_t)p->n_gates * 2 * per_gate * sizeof(double), st);
   if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: clearing grad_gates");
 
@@ -730,11 +722,11 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
     dim3 fg((unsigned)((max_site + kT - 1) / kT), n);
     fold_backward_kernel<<<fg, kT, 0, st>>>(t.sites, t.events, t.mats, t.cuts, (int)p->cut_dev.size(), x1, b,
                                             sid, sgrad, (double*)(ws + Lw.bpart),
-                                            (const int64_t*)(ws + Lw.partoff));
+                                            t.partoff);
     const int nev = (int)p->events.size();
     event_reduce_kernel<<<(nev * 32 + kT - 1) / kT, kT, 0, st>>>(t.sites, n, t.events,
                                                                 (const double*)(ws + Lw.bpart),
-                                                                (const int64_t*)(ws + Lw.partoff), exps,
+                                                                t.partoff, exps,
                                                                 m_ptr, nev, (double*)(ws + Lw.evgrad));
     gate_accum_kernel<<<(p->n_gates * 2 * per_gate + kT - 1) / kT, kT, 0, st>>>(
         t.gate_ev, t.events, p->n_gates, per_gate, (const double*)(ws + Lw.evgrad), grad_gates);

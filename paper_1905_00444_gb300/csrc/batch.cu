@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -81,6 +82,7 @@ struct BatchArgs {
   char* hdrs;             // slot headers: maxabs[64] (u32) + exps[64] (i32) each
   char* blocks;           // slot item blocks
   uint64_t hdr_bytes, block_bytes;
+  unsigned long long wait_ns;   // limit of each dependency wait
 };
 
 __device__ __forceinline__ int ld_acquire(const int32_t* p) {
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(kT, 1) batch_kernel(const BatchArgs a) {
         for (int d = 0; d < 2 && s_go; ++d) {
           if (sg.dep[d] < 0) continue;
           if (ld_acquire(a.done + sg.dep[d]) >= sg.need[d]) continue;
-          const unsigned long long deadline = gtimer() + kDepWaitNs;
+          const unsigned long long deadline = gtimer() + a.wait_ns;
           while (ld_acquire(a.done + sg.dep[d]) < sg.need[d]) {
             if (*(volatile int32_t*)a.abort) { s_go = 0; break; }
             if (gtimer() > deadline) {
@@ -397,9 +399,13 @@ static qfx_status prepare_graph(const qfx_batch_item* items, int32_t n_items,
 extern "C" uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32_t n_items,
                                               int64_t slots) {
   if (!items || n_items < 1 || slots < 1) return 0;
-  for (int i = 0; i < n_items; ++i)
+  std::set<const qfx_plan*> distinct;
+  uint64_t tab = 0;   // one copy of each distinct plan's tables
+  for (int i = 0; i < n_items; ++i) {
     if (!items[i].plan) return 0;
-  if (qfx::batch_has_tc(items, n_items)) return (uint64_t)slots * qfx::graph_lane_bytes(items, n_items);
+    if (distinct.insert(items[i].plan).second) tab += qfx::table_bytes(items[i].plan);
+  }
+  if (qfx::batch_has_tc(items, n_items)) return tab + (uint64_t)slots * qfx::graph_lane_bytes(items, n_items);
   uint64_t block = 0;
   int64_t segs_est = 0, work = 0;
   for (int i = 0; i < n_items; ++i) {
@@ -413,7 +419,7 @@ extern "C" uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32
   const uint64_t tables = a256((uint64_t)segs_est * sizeof(SegDev)) + a256((uint64_t)work * sizeof(WorkDev)) +
                           (uint64_t)n_items * (64 * 1024) + (1u << 20);
   const uint64_t control = a256(64 + (uint64_t)segs_est * 4);
-  return control + tables + (uint64_t)slots * (a256(kMaxSites * 8) + a256(block));
+  return tab + control + tables + (uint64_t)slots * (a256(kMaxSites * 8) + a256(block));
 }
 
 extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_items, void* workspace,
@@ -433,13 +439,24 @@ extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_i
         plans.push_back(it.plan);
       }
     }
-    // plan tables on the device (uploads happen here, before any capture)
+    // plan tables: one copy per distinct plan at the start of the workspace, uploaded
+    // here (synchronously, before any capture); the schedule lives after them
+    std::vector<DeviceTables> tab_store(plans.size());
     std::vector<const DeviceTables*> tabs;
-    for (auto* p : plans) {
-      const DeviceTables* t = nullptr;
-      qfx_status s = ensure_tables(p, &t);
-      if (s != QFX_OK) return s;
-      tabs.push_back(t);
+    {
+      uint64_t o = 0;
+      cudaStream_t st = (cudaStream_t)stream;
+      for (size_t k = 0; k < plans.size(); ++k) {
+        if (o + table_bytes(plans[k]) > ws_bytes) return fail(QFX_ENOMEM, "qfx_batch_prepare: workspace smaller than the plans' tables");
+        qfx_status s = stage_tables(plans[k], (char*)workspace + o, stream, &tab_store[k]);
+        if (s != QFX_OK) return s;
+        tabs.push_back(&tab_store[k]);
+        o += table_bytes(plans[k]);
+      }
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_prepare: plan tables");
+      workspace = (char*)workspace + o;
+      ws_bytes -= o;
     }
     if (batch_has_tc(items, n_items))
       return prepare_graph(items, n_items, tabs, plan_ix, workspace, ws_bytes, out);
@@ -607,6 +624,7 @@ extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_i
     A.blocks = dev + o_blocks;
     A.hdr_bytes = hdr_b;
     A.block_bytes = blk_b;
+    A.wait_ns = kDepWaitNs;
     B->control = dev;
     B->control_bytes = control_bytes;
     B->hdrs_bytes = (uint64_t)G * hdr_b;
@@ -672,3 +690,29 @@ extern "C" qfx_status qfx_batch_info(const qfx_batch* b, int64_t* n_work, int64_
 }
 
 extern "C" void qfx_batch_destroy(qfx_batch* b) { delete b; }
+
+// Test hook: one dependency of the schedule becomes unreachable (its count is raised
+// above the tasks that feed it) and every dependency wait is limited to wait_ns, so the
+// next qfx_batch_run gives up after wait_ns and qfx_sync reports QFX_ETIMEOUT.
+extern "C" qfx_status qfx_debug_batch_stall(qfx_batch* b, int64_t wait_ns) {
+  if (!b) return fail(QFX_EINVAL, "qfx_debug_batch_stall: NULL batch");
+  if (b->exec) return fail(QFX_EUNSUPPORTED, "qfx_debug_batch_stall: graph batches have no device queue");
+  if (wait_ns < 1000 || wait_ns > 5000000000ll)
+    return fail(QFX_EINVAL, "qfx_debug_batch_stall: wait_ns must be in [1e3, 5e9]");
+  const SegDev* dsegs = b->args.segs;
+  for (int32_t i = 0; i < b->args.n_segs; ++i) {
+    SegDev sg;
+    cudaError_t e = cudaMemcpy(&sg, dsegs + i, sizeof(sg), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_debug_batch_stall");
+    if (sg.dep[0] < 0) continue;
+    SegDev feed;
+    e = cudaMemcpy(&feed, dsegs + sg.dep[0], sizeof(feed), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_debug_batch_stall");
+    sg.need[0] = feed.tiles + 1;
+    e = cudaMemcpy(const_cast<SegDev*>(dsegs + i), &sg, sizeof(sg), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_debug_batch_stall");
+    b->args.wait_ns = (unsigned long long)wait_ns;
+    return QFX_OK;
+  }
+  return fail(QFX_EINVAL, "qfx_debug_batch_stall: the schedule has no dependency");
+}

@@ -163,8 +163,13 @@ struct PermTma {
   int BZ;                   // box extent along run 0 (divides its innermost axis)
   int64_t tiles_z;          // segE[0] / BZ (1 if there is no run)
   int64_t ostr_z;           // output stride of run 0's innermost axis
+  unsigned long long wait_ns;   // limit of every bounded wait
+  int withhold;             // test hook: issue no copies (every consumer's wait runs out)
 };
 constexpr unsigned long long kPermWaitNs = 1000000000ull;   // 1 s per wait
+// test hook (qfx_debug_permute_withhold): the next tensor-map permute of this thread
+// issues no copies and waits at most this long
+thread_local unsigned long long g_perm_withhold_ns = 0;
 
 struct TileMeta {
   int64_t obase;
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(160) permute_tma_kernel(const PermTma a, float
   volatile int* abort = &abort_flag;
   auto wait = [&](uint32_t bar, uint32_t parity) -> bool {
     if (mbar_try(bar, parity)) return true;
-    const unsigned long long deadline = globaltimer() + kPermWaitNs;
+    const unsigned long long deadline = globaltimer() + a.wait_ns;
     while (!mbar_try(bar, parity)) {
       if (*abort) return false;
       if (globaltimer() > deadline) {
@@ -248,6 +253,7 @@ __global__ void __launch_bounds__(160) permute_tma_kernel(const PermTma a, float
       int64_t k = 0, issued = 0;
       for (int64_t t = blockIdx.x; t < a.total; t += stride, ++k) {
         const int b = (int)(k % NB);
+        if (a.withhold) break;
         if (k >= NB && !wait(smem_u32(&empty[b]), (uint32_t)((k / NB - 1) & 1))) break;
         perm_issue<TA>(a, &map, t, smem_u32(buf + b * TILE), smem_u32(&full[b]), &meta[b]);
         issued = k + 1;
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(160) permute_tma_kernel(const PermTma a, float
       // copies still in flight must land before the block exits
       for (int64_t i = (issued > NB ? issued - NB : 0); i < issued; ++i) {
         const int b = (int)(i % NB);
-        const unsigned long long deadline = globaltimer() + kPermWaitNs;
+        const unsigned long long deadline = globaltimer() + a.wait_ns;
         while (!mbar_try(smem_u32(&full[b]), (uint32_t)((i / NB) & 1)) && globaltimer() < deadline) {
         }
       }
@@ -341,6 +347,8 @@ bool perm_tma_plan(const PermArgs& f, const void* in, PermTma* t, CUtensorMap* m
   for (int g = 1; g < a.nseg; ++g) a.nbatch *= a.segE[g];
   if (a.nseg > 0) a.nbatch *= a.segE[0] / a.BZ;
   a.total = a.tiles_a * a.tiles_b * a.nbatch;
+  a.wait_ns = kPermWaitNs;
+  a.withhold = 0;
   int64_t total_el = 1;
   for (int i = 0; i < fr; ++i) total_el *= f.dim[i];
   const cuuint64_t pad_stride = (cuuint64_t)((total_el * 8 + 15) / 16 * 16);
@@ -438,6 +446,11 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
     std::memset(&map, 0, sizeof(map));
     int TA = 0;
     if (perm_tma_plan(a, in, &tp, &map, &TA)) {
+      if (g_perm_withhold_ns) {   // test hook, one call only
+        tp.withhold = 1;
+        tp.wait_ns = g_perm_withhold_ns;
+        g_perm_withhold_ns = 0;
+      }
       const int err = TA == 64 ? launch_perm_tma<64, 4>(tp, map, dst, st)
                     : TA == 32 ? launch_perm_tma<32, 4>(tp, map, dst, st)
                                : launch_perm_tma<16, 4>(tp, map, dst, st);
@@ -466,3 +479,10 @@ int perm_take_status() {
 }
 
 }  // namespace qfx
+
+extern "C" qfx_status qfx_debug_permute_withhold(int64_t wait_ns) {
+  if (wait_ns < 1000 || wait_ns > 1000000000)
+    return qfx::fail(QFX_EINVAL, "qfx_debug_permute_withhold: wait_ns must be in [1e3, 1e9]");
+  qfx::g_perm_withhold_ns = (unsigned long long)wait_ns;
+  return QFX_OK;
+}

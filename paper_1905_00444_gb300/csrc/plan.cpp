@@ -405,7 +405,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     L.sites = L.buf1 + align256((uint64_t)p->max_elements * 8);
     L.simage = L.sites + align256((uint64_t)p->site_total * 8);
     L.item_bytes = L.simage + align256(simage);
-    p->dev.resize(0);
+    qfx::build_table_image(p);
     *out = guard.release();
     return QFX_OK;
   } catch (const std::exception& e) {
@@ -433,7 +433,7 @@ extern "C" qfx_status qfx_plan_info(const qfx_plan* p, qfx_plan_stats* s) {
 
 extern "C" uint64_t qfx_workspace_bytes(const qfx_plan* p, int64_t n_concurrent) {
   if (!p || n_concurrent < 1) return 0;
-  return align256((uint64_t)n_concurrent * p->layout.header_per_item) +
+  return qfx::table_bytes(p) + align256((uint64_t)n_concurrent * p->layout.header_per_item) +
          (uint64_t)n_concurrent * p->layout.item_bytes;
 }
 
@@ -464,7 +464,6 @@ extern "C" qfx_status qfx_plan_open_sites(const qfx_plan* p, int32_t* out) {
 
 extern "C" void qfx_plan_destroy(qfx_plan* p) {
   if (!p) return;
-  for (auto& t : p->dev)
-    if (t.base) qfx::free_tables(t);
+  qfx::free_table_image(p);
   delete p;
 }

@@ -93,14 +93,17 @@ struct Layout {
   uint64_t simage;            // pre-split site image for tensor-core steps (0 bytes if none)
 };
 
+// A plan's tables as the kernels see them: regions of one image that every compute call
+// copies from the plan's host image into the caller's workspace (nothing is allocated).
 struct DeviceTables {
-  void* base = nullptr;          // one cudaMalloc holding everything below
+  void* base = nullptr;          // start of the image in device memory
   const FoldSite* sites = nullptr;
   const FoldEvent* events = nullptr;
   const double* mats = nullptr;  // [n_mats][8]
   const CutDev* cuts = nullptr;
   const int32_t* open_perm = nullptr;  // output bit i -> bit of the final tensor index
   const int32_t* gate_ev = nullptr;    // per caller gate: its (up to 2) fold events, -1 if none
+  const int64_t* partoff = nullptr;    // per site: first fold-adjoint partial of the site
 };
 
 }  // namespace qfx
@@ -131,9 +134,16 @@ struct qfx_plan {
   double flops_per_item = 0, bytes_per_item = 0;
   int largest_step = 0;
   qfx::Layout layout{};
-  // device tables, one set per device
+  // host image of the tables (page-aligned, built once at creation), copied into the
+  // caller's workspace by every compute call; page-locked on first use so that the copy
+  // is asynchronous and can be recorded into a CUDA graph
+  char* timg = nullptr;
+  uint64_t timg_bytes = 0;        // image size, multiple of 256 (the workspace region)
+  uint64_t timg_alloc = 0;        // allocation size, multiple of the page size
+  size_t toffs[7] = {0};          // region offsets (qfx::kTableRegions)
   mutable std::mutex mu;
-  mutable std::vector<qfx::DeviceTables> dev;   // index = device ordinal
+  mutable bool timg_pinned = false;
+  mutable bool timg_tried = false;
 };
 
 namespace qfx {
@@ -184,13 +194,19 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
 void apply_autotune_cache(qfx_plan* p, const char* path);
 int tc_variant_of(int precision);   // plan-step variant marking a tensor-core step
 
-// device tables of a plan (uploaded once per device)
-qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out);
-void free_tables(DeviceTables& t);
-// host image of a plan's tables; offs[] = byte offsets of sites, events, mats, cuts, perm
-constexpr int kTableRegions = 6;
-size_t pack_tables(const qfx_plan* p, std::vector<char>& host, size_t offs[kTableRegions]);
+// A plan's tables: regions sites, events, mats, cuts, open_perm, gate_ev, partoff of one
+// image.  build_table_image packs the host image at plan creation; stage_tables copies it
+// (asynchronously on `stream`) to `dst`, a 256-byte aligned region of table_bytes(p) bytes
+// of the caller's workspace, and returns the kernels' view of it.
+constexpr int kTableRegions = 7;
+void build_table_image(qfx_plan* p);
+void free_table_image(qfx_plan* p);
+inline uint64_t table_bytes(const qfx_plan* p) { return p->timg_bytes; }
+qfx_status pin_tables(const qfx_plan* p);   // page-locks the host image (once; see qfx_plan_upload)
+qfx_status stage_tables(const qfx_plan* p, void* dst, void* stream, DeviceTables* out);
 DeviceTables tables_at(void* base, const size_t offs[kTableRegions]);
+// fold-adjoint partial entries of one site (the adjoint's per-site partial offsets)
+int64_t adjoint_site_partials(const qfx_plan* p, const FoldSite& fs);
 
 // the executor behind qfx_amplitudes (argument checks, items in flight, run)
 qfx_status check_amplitudes_args(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,

@@ -6,10 +6,13 @@
 // the caller's workspace holds run together: fold + scale their site tensors, run every
 // contraction step once for all of them (the item index is the GEMM's batch index), and
 // add each item's result into out in FP64, in slice order.  No device memory is
-// allocated here; all scratch lives in the caller's workspace.
+// allocated here; all scratch lives in the caller's workspace, whose first
+// table_bytes(p) bytes receive a copy of the plan's tables on every call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <new>
 #include <atomic>
 #include <cstring>
 #include <string>
@@ -91,26 +94,67 @@ void profile_end(void* stream, int slot, int step, int variant, int kind, double
   r.bytes = bytes;
 }
 
-void free_tables(DeviceTables& t) {
-  if (t.base) cudaFree(t.base);
-  t = DeviceTables{};
-}
-
-size_t pack_tables(const qfx_plan* p, std::vector<char>& host, size_t offs[kTableRegions]) {
+void build_table_image(qfx_plan* p) {
+  std::vector<int64_t> partoff(p->sites.size());
+  int64_t o = 0;
+  for (size_t q = 0; q < p->sites.size(); ++q) {
+    partoff[q] = o;
+    o += adjoint_site_partials(p, p->sites[q]);
+  }
   const void* src[kTableRegions] = {p->sites.data(), p->events.data(), p->mats.data(),
-                                    p->cut_dev.data(), p->open_perm.data(), p->gate_ev.data()};
+                                    p->cut_dev.data(), p->open_perm.data(), p->gate_ev.data(),
+                                    partoff.data()};
   const size_t len[kTableRegions] = {p->sites.size() * sizeof(FoldSite), p->events.size() * sizeof(FoldEvent),
                                      p->mats.size() * sizeof(double), p->cut_dev.size() * sizeof(CutDev),
-                                     p->open_perm.size() * sizeof(int32_t), p->gate_ev.size() * sizeof(int32_t)};
+                                     p->open_perm.size() * sizeof(int32_t), p->gate_ev.size() * sizeof(int32_t),
+                                     partoff.size() * sizeof(int64_t)};
   size_t total = 0;
   for (int r = 0; r < kTableRegions; ++r) {
-    offs[r] = total;
+    p->toffs[r] = total;
     total += align256(std::max<size_t>(1, len[r]));
   }
-  host.assign(total, 0);
+  // its own pages, so that page-locking it never touches another object's pages
+  const uint64_t page = 4096;
+  p->timg_bytes = total;
+  p->timg_alloc = (total + page - 1) / page * page;
+  void* mem = nullptr;
+  if (posix_memalign(&mem, page, p->timg_alloc) != 0) throw std::bad_alloc();
+  p->timg = (char*)mem;
+  std::memset(p->timg, 0, p->timg_alloc);
   for (int r = 0; r < kTableRegions; ++r)
-    if (len[r]) std::memcpy(host.data() + offs[r], src[r], len[r]);
-  return total;
+    if (len[r]) std::memcpy(p->timg + p->toffs[r], src[r], len[r]);
+}
+
+void free_table_image(qfx_plan* p) {
+  if (!p->timg) return;
+  if (p->timg_pinned) cudaHostUnregister(p->timg);
+  free(p->timg);
+  p->timg = nullptr;
+}
+
+qfx_status pin_tables(const qfx_plan* p) {
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (p->timg_tried) return QFX_OK;
+  p->timg_tried = true;
+  cudaError_t e = cudaHostRegister(p->timg, p->timg_alloc, cudaHostRegisterPortable);
+  if (e == cudaSuccess || e == cudaErrorHostMemoryAlreadyRegistered) {
+    p->timg_pinned = e == cudaSuccess;
+  } else {
+    // the image stays pageable: copies from it remain correct (it lives as long as the
+    // plan) but may make the host wait for the stream's earlier work
+    (void)cudaGetLastError();
+  }
+  return QFX_OK;
+}
+
+qfx_status stage_tables(const qfx_plan* p, void* dst, void* stream, DeviceTables* out) {
+  qfx_status s = pin_tables(p);
+  if (s != QFX_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(dst, p->timg, p->timg_bytes, cudaMemcpyHostToDevice,
+                                  (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "plan tables -> workspace copy");
+  *out = tables_at(dst, p->toffs);
+  return QFX_OK;
 }
 
 DeviceTables tables_at(void* base, const size_t offs[kTableRegions]) {
@@ -123,29 +167,8 @@ DeviceTables tables_at(void* base, const size_t offs[kTableRegions]) {
   t.cuts = (const CutDev*)(b + offs[3]);
   t.open_perm = (const int32_t*)(b + offs[4]);
   t.gate_ev = (const int32_t*)(b + offs[5]);
+  t.partoff = (const int64_t*)(b + offs[6]);
   return t;
-}
-
-qfx_status ensure_tables(const qfx_plan* p, const DeviceTables** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  std::lock_guard<std::mutex> lk(p->mu);
-  if ((int)p->dev.size() <= dev) p->dev.resize(dev + 1);
-  DeviceTables& t = p->dev[dev];
-  if (!t.base) {
-    std::vector<char> host;
-    size_t offs[kTableRegions];
-    const size_t total = pack_tables(p, host, offs);
-    void* d = nullptr;
-    e = cudaMalloc(&d, total);
-    if (e != cudaSuccess) return cuda_fail(e, "plan table upload (cudaMalloc)");
-    e = cudaMemcpy(d, host.data(), total, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "plan table upload (cudaMemcpy)"); }
-    t = tables_at(d, offs);
-  }
-  *out = &t;
-  return QFX_OK;
 }
 
 qfx_status check_amplitudes_args(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
@@ -226,8 +249,7 @@ using namespace qfx;
 
 extern "C" qfx_status qfx_plan_upload(const qfx_plan* p) {
   if (!p) return fail(QFX_EINVAL, "qfx_plan_upload: NULL plan");
-  const DeviceTables* t = nullptr;
-  return ensure_tables(p, &t);
+  return pin_tables(p);
 }
 
 extern "C" qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,
@@ -237,12 +259,14 @@ extern "C" qfx_status qfx_amplitudes(const qfx_plan* p, const uint64_t* x1, int6
   if (s != QFX_OK) return s;
   if (!workspace) return fail(QFX_EINVAL, "qfx_amplitudes: NULL argument");
   if (((uintptr_t)workspace & 255) != 0) return fail(QFX_EINVAL, "qfx_amplitudes: workspace not 256-byte aligned");
-  const int64_t G = items_in_flight(p, ws_bytes);
+  const uint64_t tb = table_bytes(p);
+  const int64_t G = ws_bytes > tb ? items_in_flight(p, ws_bytes - tb) : 0;
   if (G < 1) return fail(QFX_ENOMEM, "qfx_amplitudes: workspace smaller than qfx_plan_stats.workspace_min");
-  const DeviceTables* tp = nullptr;
-  s = ensure_tables(p, &tp);
+  DeviceTables t;
+  s = stage_tables(p, workspace, stream, &t);
   if (s != QFX_OK) return s;
-  return exec_amplitudes(p, *tp, x1, n_batch, slice_begin, slice_end, workspace, G, out, stream);
+  return exec_amplitudes(p, t, x1, n_batch, slice_begin, slice_end, (char*)workspace + tb, G, out,
+                         stream);
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up at run time (the library links only

@@ -17,11 +17,15 @@
 // plan's tables into it and clears the per-item header and the output before use, and
 // every other byte a call reads it has written first.  Calls that overlap on the GPU
 // (for example on two streams) race on the array.
+//
+// The tables are copied from the plan's own host image, which lives as long as the plan.
+// This entry point does not page-lock that image; unless another call (qfx_plan_upload,
+// qfx_amplitudes) has done so, the copy is from pageable memory and may make the host
+// wait for work already queued on the stream.
 #include <cuda_runtime.h>
 
 #include <mutex>
 #include <string>
-#include <vector>
 
 #include "qfx_internal.h"
 
@@ -58,10 +62,8 @@ extern "C" qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x
                                             int64_t slice_end, double* out, void* stream) {
   qfx_status s = qfx::check_amplitudes_args(p, x1, n_batch, slice_begin, slice_end, out);
   if (s != QFX_OK) return s;
-  std::vector<char> host;
-  size_t offs[qfx::kTableRegions];
-  const uint64_t tables = align256(qfx::pack_tables(p, host, offs));
-  const uint64_t need = tables + qfx_workspace_bytes(p, 1);
+  const uint64_t tables = qfx::table_bytes(p);
+  const uint64_t need = qfx_workspace_bytes(p, 1);   // the tables plus one work item
   if (need > (uint64_t)QFX_STATIC_SCRATCH_BYTES)
     return qfx::fail(QFX_ENOMEM, "qfx_amplitudes_static: plan needs " + std::to_string(need) +
                                      " bytes of scratch, the static array holds " +
@@ -71,9 +73,10 @@ extern "C" qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x
   s = scratch_address(&base);
   if (s != QFX_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+  // the source is the plan's own host image, which lives as long as the plan
+  cudaError_t e = cudaMemcpyAsync(base, p->timg, tables, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return qfx::cuda_fail(e, "qfx_amplitudes_static: table copy");
-  const qfx::DeviceTables t = qfx::tables_at(base, offs);
+  const qfx::DeviceTables t = qfx::tables_at(base, p->toffs);
   char* ws = (char*)base + tables;
   const int64_t G = qfx::items_in_flight(p, (size_t)(QFX_STATIC_SCRATCH_BYTES - tables));
   return qfx::exec_amplitudes(p, t, x1, n_batch, slice_begin, slice_end, ws, G, out, stream);

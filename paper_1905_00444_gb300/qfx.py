@@ -101,6 +101,8 @@ def _declare(lib):
         "qfx_profile_collect": (st, [C.POINTER(KernelTime), i32, C.POINTER(i32)]),
         "qfx_autotune": (st, [vp, C.c_char_p, vp, C.c_size_t, vp]),
         "qfx_launch_count": (u64, []),
+        "qfx_debug_permute_withhold": (st, [i64]),
+        "qfx_debug_batch_stall": (st, [vp, i64]),
         "qfx_last_error": (C.c_char_p, []),
         "qfx_version": (C.c_char_p, []),
     }
@@ -392,6 +394,11 @@ class Batch:
         _check(lib.qfx_batch_run(self._h, _stream_ptr(stream)))
         return self.outs
 
+    def debug_stall(self, wait_ns: int):
+        """Test hook: makes one dependency unreachable and limits every wait to wait_ns,
+        so the next run() gives up and sync() raises QFX_ETIMEOUT (the batch stays broken)."""
+        _check(lib.qfx_debug_batch_stall(self._h, int(wait_ns)))
+
     def __del__(self):
         if getattr(self, "_h", None):
             lib.qfx_batch_destroy(self._h)
@@ -430,6 +437,12 @@ def amplitudes_static(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Option
     _check(lib.qfx_amplitudes_static(plan._h, x1.data_ptr(), n_batch, slice_begin, slice_end,
                                      out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+def debug_permute_withhold(wait_ns: int):
+    """Test hook: the calling thread's next tensor-map permute issues no copies and gives up
+    after wait_ns; sync() then raises QFX_ETIMEOUT."""
+    _check(lib.qfx_debug_permute_withhold(int(wait_ns)))
 
 
 def sync(stream=None):
