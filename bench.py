@@ -10,11 +10,15 @@ Counted work is Eq. 1 (F = 8 sqrt(v0 v1 v2) per contraction), 2.256e14 flop per 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qfx|reference]
                   [--workload full|small|kstep|batch|batch_small|permute|adjoint|sample]
 
-Workloads other than full/small print their own JSON line: kstep (the dominant step's
-kernel in one precision), batch / batch_small (the batch scheduler on a config mix or on
-small items), permute (tensor transposes against HBM bandwidth), adjoint (forward and
-backward at 6x6x(1+24+1)), sample (fast sampling with frugal rejection, ideal and at a
-quarter of the paths).
+The default line also carries, each with its own clock record and roofline: every
+split-precision mode on the same workload (precision_modes), the adjoint at 6x6x(1+24+1)
+(adjoint), the permute kernel against HBM bandwidth (permute), a 128-item subset of the
+uneven-shape batch mix (batch: one persistent launch vs per-item launches, FP32 and
+BF16x3), the FP64 oracle on the host cores (cpu_baseline) and, last, a compact summary of
+all of them.  Workloads other than full/small print their own JSON line: kstep (the
+dominant step's kernel in one precision), batch / batch_small (the full 512-item mix or
+4096 small items), permute, adjoint, sample (fast sampling with frugal rejection, ideal
+and at a quarter of the paths).
 
 Multi-GPU (torchrun): replicas -- each rank contracts its own x1 batches (no exchange on
 the data path); value is the sum over ranks, time the max over ranks ("weak" scaling).
@@ -43,9 +47,11 @@ WORKLOADS = {
     "full": dict(rows=7, cols=7, depth=32, n_open=6, seed=0),
     "small": dict(rows=7, cols=7, depth=24, n_open=6, seed=0),   # profiling case (128 MiB boundary)
 }
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the
-# same kernel build on the small case (2^18 columns, 1.028e9 B) scaled by the columns of a
-# full launch (2^24): profiles/cgemm_step_simt_dominant_step_ncu_full.md.
+# DRAM bytes (read + write) per launch of the dominant kernel: dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the same kernel on the kernel case
+# (K = N = 256, 2^18 columns: 1.0291e9 B), scaled by the columns of a full launch
+# (2^24 / 2^18 = 64); the traffic grows in proportion to the columns (B read once, C
+# written once).
 TRAFFIC = {"full": 1.0291e9 * 64, "small": None}
 
 
@@ -131,20 +137,61 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_oracle_sample(seconds: float = 12.0):
-    """The oracle's contraction step (complex128 definition, oracle.primitives) on a
-    bounded sample of the dominant step of the workload: K = N = 256, 2^14 of its 2^24
-    columns, repeated for about `seconds`."""
-    from oracle import primitives
+def blas_threads():
+    """Threads of the BLAS numpy calls (threadpoolctl when installed, else the OpenBLAS
+    default, one per core)."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i["num_threads"] for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(n[0])
+    except ImportError:
+        pass
+    return int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+
+
+# Eq. 1 work of one x1 batch (|x2| = 6) of 7x7x(1+24+1), seed 0, in the line-sweep plan
+# (qfx_plan_info's flops_per_item; tests/test_abi_host.py checks the value): the unit the
+# full-route CPU figure is counted in.
+FLOPS_7x7x24 = 226265202688.0
+OPEN_7x7 = [13, 20, 27, 34, 41, 48]    # the planner's six open sites on a 7x7 grid
+
+
+def cpu_full_route():
+    """The oracle as it stands, end to end: oracle.network.amplitudes_open (time fold,
+    row-major sweep of np.tensordot in complex128, BLAS on every core) on one x1 batch of
+    7x7x(1+24+1) -- the largest shape of the benchmark's family the oracle finishes uncut
+    in seconds (7x7x(1+32+1) needs 2^32 complex128 values per tensor and more host memory
+    than the benchmark host has)."""
+    from oracle import network
+    circ = ri.rqc(7, 7, 24, seed=0)
+    x1 = int(ri.random_bitstrings(49, 1, seed=1000)[0])
+    t0 = time.perf_counter()
+    network.amplitudes_open(circ, x1, OPEN_7x7)
+    dt = time.perf_counter() - t0
+    return {"value": FLOPS_7x7x24 / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+            "blas_threads": blas_threads(), "kind": "oracle",
+            "sample": f"oracle.network.amplitudes_open, one x1 batch (64 amplitudes) of "
+                      f"7x7x(1+24+1) in {dt:.1f} s; Eq. 1 flops of that batch / time; host "
+                      f"{cpu_model()}", "amplitudes_per_s": 64.0 / dt, "seconds": dt}
+
+
+def cpu_step_sample(seconds: float = 4.0, cols: int = 1 << 16):
+    """The oracle's contraction routine (oracle.network.contract_network: labelled
+    np.tensordot, BLAS threads) on a bounded sample of the benchmark's dominant step,
+    K = N = 256 (two bond legs of 4 bits each), `cols` of its 2^24 columns, repeated for
+    about `seconds`.  Returns (TFLOP/s, repetitions, seconds)."""
+    from oracle import network
     K = N = 256
-    cols = 1 << 14
-    S = ri.random_complex((K, N), seed=1).astype(np.complex128)
-    B = ri.random_complex((1, K, cols), seed=2).astype(np.complex128)
+    S = ri.random_complex((16, 16, 16, 16), seed=1).astype(np.complex128)      # [up][left][right][down]
+    B = ri.random_complex((cols, 16, 16), seed=2).astype(np.complex128)         # [s][v][h]
+    sl = ["u", "l", "r", "d"]
+    bl = ["s", "u", "l"]
     flops = 8.0 * K * N * cols
     t0 = time.perf_counter()
     reps = 0
     while True:
-        primitives.contract_step(S, B, 1, K, N, cols)
+        network.contract_network([(B, bl), (S, sl)])
         reps += 1
         if time.perf_counter() - t0 >= seconds:
             break
@@ -152,40 +199,55 @@ def cpu_oracle_sample(seconds: float = 12.0):
     return flops * reps / dt / 1e12, reps, dt
 
 
+def shared_config(w):
+    """The config object both arms print for the default workload."""
+    return {"workload": workload_desc(w), "grid": [w["rows"], w["cols"]], "depth": w["depth"],
+            "n_open": w["n_open"], "l2": "inputs larger than L2 (each big step reads and writes 32 GiB)",
+            "precision": "fp32_simt"}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The FP64 oracle on the host cores: each step is the oracle's contraction routine on a
+    bounded sample (2^16 of 2^24 columns) of the workload's dominant step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     w = WORKLOADS[args.workload]
     times, tf = [], []
+    reps_total = 0
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        rate, reps, dt = cpu_oracle_sample(seconds=4.0)
+        rate, reps, dt = cpu_step_sample(seconds=1.0)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
             tf.append(rate)
+            reps_total += reps
     value = float(np.mean(tf))
-    flops_step = 2.2558e14 if args.workload == "full" else None
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": workload_desc(w), "l2": "host CPU run"},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": "oracle.primitives.contract_step (numpy complex128 einsum, one "
-                                   "thread) on 2^14 of the 2^24 columns of the dominant step "
-                                   "(K=N=256), repeated ~4 s per step"},
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": shared_config(w),
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                         "blas_threads": blas_threads(), "kind": "oracle",
+                         "sample": f"oracle.network.contract_network (np.tensordot, complex128) on "
+                                   f"2^16 of the 2^24 columns of the dominant step (K = N = 256), "
+                                   f"{reps_total} contractions over {args.steps} steps of ~1 s; "
+                                   f"host {cpu_model()}"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    if flops_step:
-        line["amplitudes_per_s"] = value * 1e12 / flops_step * (1 << w["n_open"])
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ----------------------------------------------------------------------------- our arm
+def fp32_peak(torch, dev, sm_max):
+    """FP32 FMA-pipe peak, TFLOP/s: SMs x 128 lanes x 2 flop x clock (recipe unit counts)."""
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return n_sm * 128 * 2 * sm_max * 1e6 / 1e12, n_sm
+
+
 def run_qfx(args):
     import torch
     import torch.distributed as dist
@@ -246,11 +308,12 @@ def run_qfx(args):
     elapsed = float(amax.item())
 
     # ---- end to end through the public API with host buffers ----------------------
+    e2e_steps = min(args.steps, 5)
     pin_x1 = torch.tensor(x1_host.view(np.int64)).pin_memory()
     pin_out = torch.empty((1, amps_step), dtype=torch.complex128).pin_memory()
     barrier()
     e0 = time.perf_counter()
-    for i in range(args.warmup, total):
+    for i in range(args.warmup, args.warmup + e2e_steps):
         d = pin_x1[i:i + 1].to(dev, non_blocking=True)
         qfx.amplitudes(plan, d, workspace=ws, out=out, stream=stream)
         pin_out.copy_(out, non_blocking=True)
@@ -270,10 +333,8 @@ def run_qfx(args):
     big = plan.steps[plan.stats["largest_step"]]
     dom = [r for r in recs if r["kind"] == 0 and r["flops"] == big["flops"]]
     dom_ms = float(np.mean([r["ms"] for r in dom])) if dom else float("nan")
-    props = torch.cuda.get_device_properties(dev)
-    n_sm = props.multi_processor_count
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12          # FP32 FMA pipes, TFLOP/s
+    peak, n_sm = fp32_peak(torch, dev, sm_max)
     achieved = big["flops"] / (dom_ms / 1e3) / 1e12
     kern_total = sum(r["ms"] for r in recs)
     share = {}
@@ -282,46 +343,84 @@ def run_qfx(args):
         share[key] = share.get(key, 0.0) + r["ms"]
 
     value = flops_step * args.steps * world / elapsed / 1e12
+    cfg = shared_config(w)
+    cfg.update({"n_slices": plan.n_slices, "flops_per_step": flops_step,
+                "max_intermediate_bytes": plan.stats["max_elements"] * 8, "plan_s": plan_s})
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
-        "data": "synthetic",
-        "config": {"workload": workload_desc(w), "grid": [w["rows"], w["cols"]],
-                   "depth": w["depth"], "n_open": w["n_open"], "n_slices": plan.n_slices,
-                   "flops_per_step": flops_step, "max_intermediate_bytes": plan.stats["max_elements"] * 8,
-                   "l2": "inputs larger than L2 (each big step reads and writes 32 GiB)",
-                   "plan_s": plan_s, "precision": "fp32_simt"},
+        "data": "synthetic", "config": cfg,
         "amplitudes_per_s": amps_step * args.steps * world / elapsed,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": TRAFFIC.get(args.workload),
                      "kernel": f"cgemm_step variant {big['variant']} (P,K,N,Sd)="
                                f"({big['P']},{big['K']},{big['N']},{big['Sd']})",
                      "launches_timed": len(dom),
-                     "peak_note": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
-                                  "(FMA pipes; recipe unit counts)"},
+                     "peak_note": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"},
         "kernel_share": {k: v / kern_total for k, v in share.items()} if kern_total else {},
-        "e2e": {"value": flops_step * args.steps * world / e_el / 1e12, "unit": "TFLOP/s",
-                "amplitudes_per_s": amps_step * args.steps * world / e_el,
+        "e2e": {"value": flops_step * e2e_steps * world / e_el / 1e12, "unit": "TFLOP/s",
+                "amplitudes_per_s": amps_step * e2e_steps * world / e_el, "steps": e2e_steps,
                 "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 16 * amps_step},
         "clocks": clk,
         "gpu_launches": int(launches),
     }
-    if not args.no_modes:
-        line["precision_modes"] = {m: run_mode(qfx, torch, circ, w, m, x1_dev, args, dev, stream)
+    sub_steps = max(1, min(args.steps, 5))
+    sub_warm = max(1, min(args.warmup, 2))
+    if not args.no_modes and world == 1:
+        line["precision_modes"] = {m: run_mode(qfx, torch, circ, w, m, x1_dev, sub_steps, sub_warm,
+                                               dev, stream)
                                    for m in ("bf16x3", "tf32x3", "bf16x2", "bf16x3_fast")}
+    del ws
+    torch.cuda.empty_cache()
+    if not args.no_configs and world == 1:
+        line["adjoint"] = measure_adjoint(qfx, torch, steps=sub_steps, warmup=sub_warm)
+        line["permute"] = measure_permute(qfx, torch, steps=sub_steps, warmup=sub_warm)
+        line["batch"] = measure_batch(qfx, torch, BATCH_MIX_SUBSET, 8, steps=1, warmup=1,
+                                      tc=True, autotune=not args.no_autotune)
     if world == 1 and not args.no_cpu:
-        rate, reps, dt = cpu_oracle_sample(seconds=args.cpu_seconds)
-        line["cpu_baseline"] = {
-            "value": rate, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle.primitives.contract_step (numpy complex128 einsum, one thread) on "
-                      f"2^14 of the 2^24 columns of the dominant step (K=N=256), {reps} reps in "
-                      f"{dt:.1f} s; host has {os.cpu_count()} cores ({cpu_model()})",
-            "amplitudes_per_s": rate * 1e12 / flops_step * amps_step}
+        cpu = cpu_full_route()
+        rate, reps, dt = cpu_step_sample(seconds=4.0)
+        cpu["step_sample"] = {"value": rate, "unit": "TFLOP/s",
+                              "what": f"oracle.network.contract_network on 2^16 of the 2^24 columns "
+                                      f"of the dominant step, {reps} reps in {dt:.1f} s"}
+        line["cpu_baseline"] = cpu
+    line["summary"] = summarize(line)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _r(x, nd=3):
+    return None if x is None else float(f"{x:.{nd}g}")
+
+
+def summarize(line):
+    """Compact figures of every part of the line, printed last (the end of the line is
+    what a truncated log keeps)."""
+    s = {"fp32": {"tflops": _r(line["value"]), "frac": _r(line["roofline"]["frac"]),
+                  "e2e": _r(line["e2e"]["value"]), "mhz": line["clocks"].get("sm_mhz")}}
+    for m, d in line.get("precision_modes", {}).items():
+        s[m] = {"tflops": _r(d["value"]), "frac_probe": _r(d["roofline"]["tensor_probe"]["frac"]),
+                "err_vs_fp32": _r(d["max_rel_diff_vs_fp32"], 2), "mhz": d["clocks"].get("sm_mhz")}
+    if "adjoint" in line:
+        a = line["adjoint"]
+        s["adjoint"] = {"fwd_ms": _r(a["forward_ms"]), "bwd_ms": _r(a["backward_ms"]),
+                        "bwd_frac": _r(a["roofline"]["frac"])}
+    if "permute" in line:
+        s["permute_frac"] = [_r(c["frac"], 2) for c in line["permute"]["cases"]]
+    if "batch" in line:
+        b = line["batch"]
+        s["batch_tflops"] = {"persistent": _r(b["fp32_persistent"]["value"]),
+                             "per_item": _r(b["fp32_per_item"]["value"]),
+                             "bf16x3_graph": _r(b["bf16x3_graph"]["value"]) if b.get("bf16x3_graph") else None,
+                             "bf16x3_per_item": _r(b["bf16x3_per_item"]["value"]) if b.get("bf16x3_per_item") else None}
+    if "cpu_baseline" in line:
+        c = line["cpu_baseline"]
+        s["cpu"] = {"tflops": _r(c["value"]), "cores": c["cores"],
+                    "step_sample": _r(c["step_sample"]["value"])}
+    return s
 
 
 # Tensor-pipe work per counted complex multiply-add (8 counted flops): 4 real products,
@@ -339,15 +438,17 @@ def measured_peaks():
         return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}, "fallback"
 
 
-def run_mode(qfx, torch, circ, w, mode, x1_dev, args, dev, stream):
-    """The same workload with the contraction steps on tcgen05 in a split precision."""
+def run_mode(qfx, torch, circ, w, mode, x1_dev, steps, warmup, dev, stream):
+    """The same workload with the contraction steps on tcgen05 in a split precision, and
+    the largest per-amplitude difference to the FP32 path (floor 2^(-n/2))."""
     fast = mode.endswith("_fast")
     mode = mode.replace("_fast", "")
+    plan32 = qfx.Plan(qfx.Circuit(circ), n_open=w["n_open"])
     plan = qfx.Plan(qfx.Circuit(circ), n_open=w["n_open"], precision=mode, fast_accumulation=fast)
     plan.upload()
     ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
     out = torch.empty((1, 1 << w["n_open"]), dtype=torch.complex128, device=dev)
-    for i in range(args.warmup):
+    for i in range(warmup):
         qfx.amplitudes(plan, x1_dev[i:i + 1], workspace=ws, out=out, stream=stream)
     torch.cuda.synchronize(dev)
     qfx.profile_enable(True)
@@ -355,7 +456,7 @@ def run_mode(qfx, torch, circ, w, mode, x1_dev, args, dev, stream):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i in range(args.warmup, args.warmup + args.steps):
+    for i in range(warmup, warmup + steps):
         qfx.amplitudes(plan, x1_dev[i:i + 1], workspace=ws, out=out, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
@@ -364,6 +465,12 @@ def run_mode(qfx, torch, circ, w, mode, x1_dev, args, dev, stream):
     qfx.profile_enable(False)
     recs = qfx.profile_collect()
     el = e0.elapsed_time(e1) / 1e3
+    got = out.clone()
+    ref = qfx.amplitudes(plan32, x1_dev[warmup + steps - 1:warmup + steps], workspace=ws, stream=stream)
+    qfx.sync()
+    floor = 2.0 ** (-w["rows"] * w["cols"] / 2)
+    diff = float((torch.abs(got - ref) / torch.clamp(torch.abs(ref), min=floor)).max())
+    del ws
     flops = plan.stats["flops_per_item"] * plan.n_slices
     big = plan.steps[plan.stats["largest_step"]]
     dom = [r["ms"] for r in recs if r["kind"] == 0 and r["flops"] == big["flops"]]
@@ -374,21 +481,91 @@ def run_mode(qfx, torch, circ, w, mode, x1_dev, args, dev, stream):
     burst = peaks["bf16_tflops"] * TENSOR_PEAK_RATIO[mode]
     achieved = counted * TENSOR_FACTOR[mode]
     probe = qfx.tensor_peak(mode, 1 << 16)   # this kind's MMA rate, measured here
-    return {"value": flops * args.steps / el / 1e12, "unit": "TFLOP/s",
-            "amplitudes_per_s": (1 << w["n_open"]) * args.steps / el,
-            "ms_per_step": 1e3 * el / args.steps,
-            "largest_step_counted_tflops": counted,
+    return {"value": flops * steps / el / 1e12, "unit": "TFLOP/s",
+            "amplitudes_per_s": (1 << w["n_open"]) * steps / el,
+            "ms_per_step": 1e3 * el / steps, "steps": steps,
+            "largest_step_counted_tflops": counted, "max_rel_diff_vs_fp32": diff,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "frac_of_burst": achieved / burst, "traffic": None,
-                         "tensor_probe": {"tflops": probe, "frac": achieved / probe,
-                                          "what": "qfx_tensor_peak: back-to-back 128x256 MMAs of "
-                                                  "this operand kind from shared memory, one CTA "
-                                                  "per SM"},
-                         "note": f"tensor-pipe flops = {TENSOR_FACTOR[mode]:g} x counted; peak = "
-                                 f"{src} bf16 sustained x {TENSOR_PEAK_RATIO[mode]} (the sustained "
-                                 f"GEMM ran power-capped; this kernel is bound by shared-memory "
-                                 f"bandwidth and keeps its clocks, see clocks)"},
+                         "tensor_probe": {"tflops": probe, "frac": achieved / probe},
+                         "peak_source": f"{src} bf16 sustained x {TENSOR_PEAK_RATIO[mode]}; tensor-pipe "
+                                        f"flops = {TENSOR_FACTOR[mode]:g} x counted"},
             "clocks": clk}
+
+
+def measure_adjoint(qfx, torch, steps, warmup):
+    """6x6x(1+24+1) parametrised RQC, 128 bitstrings, L = sum |amp|^2: forward amplitudes
+    and the adjoint's gradients of every gate tensor (every step output stored), CUDA
+    events; backward work model = 3 forward-equivalents (forward, reverse step, site-
+    gradient GEMM)."""
+    circ = ri.rqc(6, 6, 24, seed=0, parametrised=True)
+    x1 = torch.tensor(ri.random_bitstrings(36, 1, seed=9).view(np.int64), device="cuda")
+    out = torch.empty((1, 128), dtype=torch.complex128, device="cuda")
+    plan = qfx.Plan(qfx.Circuit(circ), n_open=7)
+    ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device="cuda")
+    bws = torch.empty(plan.backward_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
+        qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f_ms, b_ms = [], []
+    for _ in range(max(steps, 3)):
+        ev[0].record()
+        amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
+        ev[1].record()
+        qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
+        ev[2].record()
+        torch.cuda.synchronize()
+        f_ms.append(ev[0].elapsed_time(ev[1]))
+        b_ms.append(ev[1].elapsed_time(ev[2]))
+    clk = clocks.stop()
+    qfx.sync()
+    flops = plan.stats["flops_per_item"]
+    fwd, bwd = float(np.median(f_ms)), float(np.median(b_ms))
+    peak, _ = fp32_peak(torch, torch.device("cuda", 0), clk.get("sm_max_mhz") or 2070.0)
+    bt = 3 * flops / (bwd / 1e3) / 1e12
+    return {"workload": f"6x6x(1+24+1) parametrised RQC, 128 bitstrings, {len(circ.gates)} gate "
+                        f"tensors, every step output stored",
+            "forward_ms": fwd, "backward_ms": bwd, "forward_tflops": flops / (fwd / 1e3) / 1e12,
+            "backward_tflops": bt,
+            "roofline": {"bound": "alu", "achieved": bt, "peak": peak, "unit": "TFLOP/s",
+                         "frac": bt / peak, "what": "backward, 3 x forward flops / time, FP32 FMA peak"},
+            "clocks": clk}
+
+
+def measure_permute(qfx, torch, steps, warmup):
+    """qfx_permute on 2^28-element complex64 tensors (2 GiB in, 2 GiB out): HBM bandwidth
+    (16 B per element) against the measured copy bandwidth."""
+    peaks, src = measured_peaks()
+    out = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    for shape, perm in PERMUTES:
+        n = int(np.prod(shape))
+        x = torch.randn(n, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(warmup):
+            qfx.permute(x, shape, perm, out=y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            qfx.permute(x, shape, perm, out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        gbs = 16.0 * n / (ms / 1e3) / 1e9
+        out.append({"shape": list(shape), "perm": list(perm), "ms": ms, "GB/s": gbs,
+                    "frac": gbs / peaks["hbm_gbs"]})
+        del x, y
+    clk = clocks.stop()
+    qfx.sync()
+    return {"workload": "permute, 2^28 complex64 elements", "roofline": {
+        "bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src},
+        "cases": out, "clocks": clk}
 
 
 # ----------------------------------------------------------------------------- batch case
@@ -405,25 +582,29 @@ BATCH_MIX = [  # (rows, cols, depth, per-item cap bytes, items, kind)
 ]
 
 
-def run_batch(args):
-    """512 work items of uneven shapes from mixed grids, |x2| = 8 (256 amplitudes per
-    item): one persistent launch replayed from a CUDA graph vs one qfx_amplitudes call
-    per item (each its own fold, step and accumulate launches).  The 512-item mix costs
-    ~1.4e15 flop per batch, so it times at most 2 batches after 1 warm-up."""
-    import torch
-    import paper_1905_00444_gb300 as qfx
+BATCH_MIX_SUBSET = [  # a quarter of BATCH_MIX, same proportions (the default line's batch)
+    (6, 6, 24, 1 << 30, 43, "x1"),
+    (7, 7, 32, 1 << 30, 43, "slice"),
+    (8, 8, 32, 2 << 30, 41, "slice"),
+    (7, 7, 40, 8 << 30, 1, "slice"),
+]
+
+
+def measure_batch(qfx, torch, mix, n_open, steps, warmup, tc, autotune):
+    """Work items of uneven shapes from mixed grids: one persistent launch replayed from a
+    CUDA graph vs one qfx_amplitudes call per item; with tc, the same items with BF16x3
+    plans as one batch (a CUDA graph of per-item launch sequences over parallel lanes) and
+    per item.  Results of the batched and per-item runs must be bit-identical."""
     dev = torch.device("cuda", 0)
     items, flops = [], 0.0
     rng = np.random.default_rng(7)
     cache = os.path.join("/tmp", "qfx_autotune_batch.json")
-    mix = BATCH_MIX_SMALL if args.workload == "batch_small" else BATCH_MIX
-    n_open = 4 if args.workload == "batch_small" else 8
     tc_plan, nq = {}, []   # split-precision twin of each plan; qubits per item
     for (r, c, d, cap, count, kind) in mix:
         n0 = len(items)
         circ = qfx.Circuit(ri.rqc(r, c, d, seed=r * 10 + d))
         plan = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap)
-        if not args.no_autotune:
+        if autotune:
             qfx.autotune(plan, cache)
             plan = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap, autotune_cache=cache)
         if kind == "x1":
@@ -435,23 +616,23 @@ def run_batch(args):
             for sl in sorted(set(int(v) for v in rng.integers(0, plan.n_slices, size=count))):
                 items.append((plan, x1, sl, sl + 1))
         flops += plan.stats["flops_per_item"] * (len(items) - n0)
-        if args.workload == "batch":
+        if tc:
             tp = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap, precision="bf16x3")
-            if not args.no_autotune:   # tensor cores or FP32 tiles, per step shape, by timing
+            if autotune:   # tensor cores or FP32 tiles, per step shape, by timing
                 qfx.autotune(tp, cache)
                 tp = qfx.Plan(circ, n_open=n_open, max_intermediate_bytes=cap, precision="bf16x3",
                               autotune_cache=cache)
             tc_plan[id(plan)] = tp
         nq += [r * c] * (len(items) - n0)
-    if args.workload == "batch":
-        args.steps, args.warmup = min(args.steps, 2), 1
     # slots hold the largest item; keep the batch workspace under ~96 GiB
     block = max(p.workspace_bytes(1) for p, _, _, _ in items)
     slots = int(max(2, min(16, (96 << 30) // block)))
+    clocks = ClockSampler(0)
+    clocks.start()
     batch = qfx.Batch(items, slots=slots)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, warmup)):
             batch.run(stream=stream)
     torch.cuda.synchronize(dev)
     graph = torch.cuda.CUDAGraph()
@@ -461,94 +642,107 @@ def run_batch(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):      # replay() launches on the current stream
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             graph.replay()
         e1.record(stream)
     torch.cuda.synchronize(dev)
     qfx.sync()
-    t_graph = e0.elapsed_time(e1) / 1e3 / args.steps
+    t_graph = e0.elapsed_time(e1) / 1e3 / steps
     ref = [o.clone() for o in batch.outs]
+    n_tasks_fp32, slots_fp32 = batch.n_tasks, batch.slots
+    del graph, batch
+    torch.cuda.empty_cache()
     # per-item launches on one shared workspace
     ws = torch.empty(max(p.workspace_bytes(1) for p, _, _, _ in items), dtype=torch.uint8, device=dev)
     outs = [torch.empty_like(o) for o in ref]
-    for (plan, x1, sb, se), o in zip(items, outs):
-        qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws, out=o)
+    for _ in range(max(1, warmup)):
+        for (plan, x1, sb, se), o in zip(items, outs):
+            qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws, out=o)
     torch.cuda.synchronize(dev)
     l1 = qfx.launch_count()
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         for (plan, x1, sb, se), o in zip(items, outs):
             qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws, out=o)
     e1.record()
     torch.cuda.synchronize(dev)
-    t_items = e0.elapsed_time(e1) / 1e3 / args.steps
-    per_item_launches = (qfx.launch_count() - l1) // args.steps
+    t_items = e0.elapsed_time(e1) / 1e3 / steps
+    per_item_launches = (qfx.launch_count() - l1) // steps
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
-    n_tasks_fp32, slots_fp32 = batch.n_tasks, batch.slots
-    tc_line = None
-    if args.workload == "batch":
-        # free the FP32 batch's workspaces before the split-precision runs
-        del graph, batch, ws
-        torch.cuda.empty_cache()
-        # the same items with the steps on the tensor cores (BF16x3, default accumulation)
+    res = {"n_items": len(items), "flops_per_batch": flops,
+           "fp32_persistent": {"value": flops / t_graph / 1e12, "ms_per_batch": 1e3 * t_graph,
+                               "items_per_s": len(items) / t_graph, "kernel_launches": 1,
+                               "tasks": n_tasks_fp32, "slots": slots_fp32},
+           "fp32_per_item": {"value": flops / t_items / 1e12, "ms_per_batch": 1e3 * t_items,
+                             "items_per_s": len(items) / t_items, "kernel_launches": per_item_launches},
+           "fp32_identical": bool(same), "autotuned": bool(autotune)}
+    del ws
+    torch.cuda.empty_cache()
+    if tc:
         tc_items = [(tc_plan[id(p)], x1, sb, se) for p, x1, sb, se in items]
         ws_tc = torch.empty(max(p.workspace_bytes(1) for p, _, _, _ in tc_items), dtype=torch.uint8, device=dev)
         outs_tc = [torch.empty_like(o) for o in ref]
-        for (plan, x1, sb, se), o in zip(tc_items, outs_tc):
-            qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws_tc, out=o)
+        for _ in range(max(1, warmup)):
+            for (plan, x1, sb, se), o in zip(tc_items, outs_tc):
+                qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws_tc, out=o)
         torch.cuda.synchronize(dev)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             for (plan, x1, sb, se), o in zip(tc_items, outs_tc):
                 qfx.amplitudes(plan, x1, slice_begin=sb, slice_end=se, workspace=ws_tc, out=o)
         e1.record()
         torch.cuda.synchronize(dev)
         qfx.sync()
-        t_tc = e0.elapsed_time(e1) / 1e3 / args.steps
+        t_tc = e0.elapsed_time(e1) / 1e3 / steps
         worst = 0.0
         for a, b, n in zip(outs_tc, ref, nq):
             fl = 2.0 ** (-n / 2)
             worst = max(worst, float((torch.abs(a - b) / torch.clamp(torch.abs(b), min=fl)).max()))
-        # the same items as one batch: one CUDA graph of per-item launch sequences over
-        # parallel lanes (each lane one workspace slot; slots sized like the FP32 batch's)
+        del ws_tc
+        torch.cuda.empty_cache()
         lane = max(p.workspace_bytes(1) for p, _, _, _ in tc_items)
         gb = qfx.Batch(tc_items, slots=int(max(1, min(16, (96 << 30) // lane))))
         with torch.cuda.stream(stream):
-            gb.run(stream=stream)
+            for _ in range(max(1, warmup)):
+                gb.run(stream=stream)
             torch.cuda.synchronize(dev)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 gb.run(stream=stream)
             e1.record(stream)
         torch.cuda.synchronize(dev)
         qfx.sync()
-        t_gb = e0.elapsed_time(e1) / 1e3 / args.steps
+        t_gb = e0.elapsed_time(e1) / 1e3 / steps
         same_tc = all(torch.equal(a, b) for a, b in zip(gb.outs, outs_tc))
-        tc_line = {"value": flops / t_tc / 1e12, "ms_per_batch": 1e3 * t_tc,
-                   "graph_batch": {"value": flops / t_gb / 1e12, "ms_per_batch": 1e3 * t_gb,
-                                   "lanes": gb.slots, "graph_nodes": gb.n_tasks,
-                                   "identical_to_per_item": bool(same_tc)},
-                   "max_rel_diff_vs_fp32": worst,
-                   "note": "per-item qfx_amplitudes launches with BF16x3 plans (autotuned: "
-                           "tensor cores or FP32 tiles per step shape); per-amplitude "
-                           "difference to the FP32 results, floor 2^(-n/2)"}
+        res["bf16x3_per_item"] = {"value": flops / t_tc / 1e12, "ms_per_batch": 1e3 * t_tc}
+        res["bf16x3_graph"] = {"value": flops / t_gb / 1e12, "ms_per_batch": 1e3 * t_gb,
+                               "lanes": gb.slots, "graph_nodes": gb.n_tasks}
+        res["bf16x3_identical"] = bool(same_tc)
+        res["bf16x3_max_rel_diff_vs_fp32"] = worst
+        del gb
+        torch.cuda.empty_cache()
+    res["clocks"] = clocks.stop()
+    return res
+
+
+def run_batch(args):
+    """The 512-item mix (batch) or 4096 small items (batch_small); |x2| = 8 (256 amplitudes
+    per item) or 4.  The 512-item mix costs ~1.4e15 flop per batch, so it times at most 2
+    batches after 1 warm-up."""
+    import torch
+    import paper_1905_00444_gb300 as qfx
+    big = args.workload == "batch"
+    mix = BATCH_MIX if big else BATCH_MIX_SMALL
+    steps, warmup = (min(args.steps, 2), 1) if big else (args.steps, args.warmup)
+    res = measure_batch(qfx, torch, mix, 8 if big else 4, steps, warmup, tc=big,
+                        autotune=not args.no_autotune)
     desc = ("batch of 512 work items: 171 x 6x6x(1+24+1) x1 batches (bond dim 2^3); sampled "
             "slices: 171 of 7x7x(1+32+1) (1 GiB cap), 166 of 8x8x(1+32+1) (2 GiB cap), both "
-            "bond dim 2^4, and 4 of 7x7x(1+40+1) (8 GiB cap, bond dim 2^5); |x2| = 8; "
-            "FP32 SIMT tiles") if args.workload == "batch" else (
+            "bond dim 2^4, and 4 of 7x7x(1+40+1) (8 GiB cap, bond dim 2^5); |x2| = 8") if big else (
             "batch of 4096 small work items: 2048 x 4x4x(1+16+1), 1024 x 4x5x(1+16+1), "
             "1024 x 5x5x(1+24+1) x1 batches; |x2| = 4; FP32 SIMT tiles")
-    print(json.dumps({
-        "workload": desc,
-        "metric": "contraction TFLOP/s", "unit": "TFLOP/s",
-        "graph_persistent": {"value": flops / t_graph / 1e12, "ms_per_batch": 1e3 * t_graph,
-                             "items_per_s": len(items) / t_graph, "kernel_launches": 1,
-                             "tasks": n_tasks_fp32, "slots": slots_fp32},
-        "per_item_launches": {"value": flops / t_items / 1e12, "ms_per_batch": 1e3 * t_items,
-                              "items_per_s": len(items) / t_items, "kernel_launches": per_item_launches},
-        "identical_results": bool(same), "flops_per_batch": flops, "n_items": len(items),
-        "bf16x3_per_item_launches": tc_line,
-        "autotuned": not args.no_autotune}), flush=True)
+    print(json.dumps({"workload": desc, "metric": "contraction TFLOP/s", "unit": "TFLOP/s", **res}),
+          flush=True)
     return 0
 
 
@@ -685,33 +879,9 @@ PERMUTES = [  # (shape, perm): bond-tensor transposes of the kind region plans n
 
 
 def run_permute(args):
-    """qfx_permute on 2^28-element complex64 tensors (2 GiB in, 2 GiB out): achieved HBM
-    bandwidth (16 B per element) against the measured copy bandwidth."""
     import torch
     import paper_1905_00444_gb300 as qfx
-    peaks, src = measured_peaks()
-    out = []
-    for shape, perm in PERMUTES:
-        n = int(np.prod(shape))
-        x = torch.randn(n, dtype=torch.complex64, device="cuda")
-        y = torch.empty_like(x)
-        for _ in range(args.warmup):
-            qfx.permute(x, shape, perm, out=y)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            qfx.permute(x, shape, perm, out=y)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        gbs = 16.0 * n / (ms / 1e3) / 1e9
-        out.append({"shape": list(shape), "perm": list(perm), "ms": ms, "GB/s": gbs,
-                    "frac": gbs / peaks["hbm_gbs"]})
-        del x, y
-    print(json.dumps({"workload": "permute, 2^28 complex64 elements", "roofline": {
-        "bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src},
-        "cases": out}), flush=True)
+    print(json.dumps(measure_permute(qfx, torch, args.steps, args.warmup)), flush=True)
     return 0
 
 
@@ -778,6 +948,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "bf16x2", "bf16x3_fast"],
                     help="kernel case only; the amplitude run reports every mode")
     ap.add_argument("--no-modes", action="store_true", help="skip the split-precision runs")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the adjoint, permute and batch parts of the default line")
     ap.add_argument("--no-autotune", action="store_true", help="batch case: planner's default tiles")
     args = ap.parse_args()
     if args.impl == "reference":
