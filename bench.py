@@ -8,7 +8,7 @@ one x1 batch through the whole path: fold, scale, 48 contraction steps, FP64 sum
 Counted work is Eq. 1 (F = 8 sqrt(v0 v1 v2) per contraction), 2.256e14 flop per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qfx|reference]
-                  [--workload full|small|kstep|batch|batch_small|permute|adjoint|sample]
+                  [--workload full|small|kstep|batch|batch_small|permute|adjoint|sample|wide]
 
 The default line also carries, each with its own clock record and roofline: every
 split-precision mode on the same workload (precision_modes), the adjoint at 6x6x(1+24+1)
@@ -18,7 +18,7 @@ BF16x3), the FP64 oracle on the host cores (cpu_baseline) and, last, a compact s
 all of them.  Workloads other than full/small print their own JSON line: kstep (the
 dominant step's kernel in one precision), batch / batch_small (the full 512-item mix or
 4096 small items), permute, adjoint, sample (fast sampling with frugal rejection, ideal
-and at a quarter of the paths).
+and at a quarter of the paths), wide (slices of the 121-qubit 11x11x(1+24+1) shape).
 
 Multi-GPU (torchrun): replicas -- each rank contracts its own x1 batches (no exchange on
 the data path); value is the sum over ranks, time the max over ranks ("weak" scaling).
@@ -885,6 +885,70 @@ def run_permute(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- 121 qubits
+def run_wide(args):
+    """The paper's 11x11x(1+24+1) shape (121 qubits, two-word bitstrings, mean |amp|^2 =
+    2^-121) under a 64 GiB cap on the largest intermediate: 2^31 slices (paths, Sec. III.A)
+    of 2.5e14 flop each.  Each timed step contracts one seeded slice of one x1 batch
+    (|x2| = 6), in FP32 and in BF16x3; the slice sum of a fraction f of the paths gives
+    amplitudes of fidelity about f (Sec. III.C)."""
+    import torch
+    import paper_1905_00444_gb300 as qfx
+    dev = torch.device("cuda", 0)
+    circ = qfx.Circuit(ri.rqc(11, 11, 24, seed=0))
+    words = ri.random_bitstring_words(121, 1, seed=11)
+    x1 = torch.tensor(words.view(np.int64), device=dev)
+    peaks, src = measured_peaks()
+    res = {}
+    for prec in ("fp32", "bf16x3"):
+        plan = qfx.Plan(circ, n_open=6, max_intermediate_bytes=64 << 30, precision=prec)
+        plan.upload()
+        sids = [int(v) for v in np.random.default_rng(3).integers(0, plan.n_slices, args.warmup + args.steps)]
+        ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
+        out = torch.empty((1, 64), dtype=torch.complex128, device=dev)
+        for s in sids[:args.warmup]:
+            qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(0)
+        clocks.start()
+        qfx.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in sids[args.warmup:]:
+            qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        qfx.profile_enable(False)
+        recs = qfx.profile_collect()
+        clk = clocks.stop()
+        qfx.sync()
+        el = e0.elapsed_time(e1) / 1e3
+        flops = plan.stats["flops_per_item"]
+        big = plan.steps[plan.stats["largest_step"]]
+        dom = [r["ms"] for r in recs if r["kind"] == 0 and r["flops"] == big["flops"]]
+        counted = big["flops"] / (float(np.mean(dom)) / 1e3) / 1e12 if dom else float("nan")
+        if prec == "fp32":
+            peak, _ = fp32_peak(torch, dev, clk.get("sm_max_mhz") or 2070.0)
+            roof = {"bound": "alu", "achieved": counted, "peak": peak, "unit": "TFLOP/s",
+                    "frac": counted / peak}
+        else:
+            probe = qfx.tensor_peak("bf16x3", 1 << 16)
+            roof = {"bound": "tensor", "achieved": counted * TENSOR_FACTOR["bf16x3"], "unit": "TFLOP/s",
+                    "peak": peaks["bf16_tflops"], "frac_of_burst": counted * TENSOR_FACTOR["bf16x3"] / peaks["bf16_tflops"],
+                    "tensor_probe": {"tflops": probe, "frac": counted * TENSOR_FACTOR["bf16x3"] / probe}}
+        res[prec] = {"value": flops * args.steps / el / 1e12, "unit": "TFLOP/s",
+                     "ms_per_slice": 1e3 * el / args.steps, "slices": args.steps,
+                     "dominant_step": f"(P,K,N,Sd)=({big['P']},{big['K']},{big['N']},{big['Sd']})",
+                     "roofline": roof, "clocks": clk}
+        del ws
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "11x11x(1+24+1) RQC seed 0 (121 qubits), |x2| = 6, 64 GiB cap: "
+                                  f"{plan.n_slices} slices of {plan.stats['flops_per_item']:.3g} flop; "
+                                  "one seeded slice per step", "metric": "contraction TFLOP/s",
+                      **res}), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- kernel case
 def run_kstep(args):
     """The dominant contraction step alone (K = N = 256 as in the 7x7x32 interior steps)
@@ -942,7 +1006,7 @@ def main():
     ap.add_argument("--impl", default="qfx", choices=["qfx", "reference"])
     ap.add_argument("--workload", default="full",
                     choices=sorted(WORKLOADS) + ["kstep", "batch", "batch_small", "permute", "adjoint",
-                                                 "sample"])
+                                                 "sample", "wide"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "bf16x2", "bf16x3_fast"],
@@ -964,6 +1028,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "sample":
         return run_sample(args)
+    if args.workload == "wide":
+        return run_wide(args)
     return run_qfx(args)
 
 

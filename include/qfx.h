@@ -12,7 +12,9 @@
  *   the TTGT form of Sec. III.E, with counted work F = 8 sqrt(v0 v1 v2) (Eq. 1).
  *
  * Conventions
- *   - qubit q = r * cols + c; bit q of a uint64 bitstring is the value of qubit q (n <= 64).
+ *   - qubit q = r * cols + c.  A bitstring of n qubits is ceil(n / 64) uint64 words (the
+ *     plan's x1_words; one word up to 64 qubits): qubit q is bit q % 64 of word q / 64.
+ *     Grids hold up to 144 qubits.
  *   - complex numbers are (re, im) pairs; complex64 = 2 x float, complex128 = 2 x double.
  *   - Every call returns a qfx_status.  On failure, qfx_last_error() (thread-local) holds
  *     a message.  No exception crosses the ABI and nothing aborts the process.
@@ -88,7 +90,7 @@ typedef struct qfx_plan qfx_plan;
 
 /* Sec. III (RQC class on a planar grid; Table I's "1+d+1" circuits).
  * Validates and copies the gate list (a1): qubit ranges, two-qubit gates only between
- * grid neighbours, disjoint qubits within a layer, layers >= 0, rows*cols <= 64.
+ * grid neighbours, disjoint qubits within a layer, layers >= 0, rows*cols <= 144.
  * Errors: QFX_EINVAL with the offending gate index in qfx_last_error(). */
 qfx_status qfx_circuit_create(int32_t rows, int32_t cols, const qfx_gate* gates,
                               int64_t n_gates, qfx_circuit** out);
@@ -173,6 +175,7 @@ typedef struct {
   uint64_t workspace_min;      /* workspace for one item plus the shared header */
   int32_t largest_step;        /* index of the step with the most flops */
   int32_t precision;
+  int32_t x1_words;            /* uint64 words per bitstring, ceil(n / 64) */
 } qfx_plan_stats;
 
 qfx_status qfx_plan_info(const qfx_plan* p, qfx_plan_stats* out);
@@ -201,7 +204,8 @@ qfx_status qfx_plan_open_sites(const qfx_plan* p, int32_t* out);
 qfx_status qfx_plan_upload(const qfx_plan* p);
 
 /* Amplitudes (Sec. III.A-III.B; the sum over paths of Sec. III.A and III.C).
- *   x1        device, [n_batch] uint64 bitstrings; the bits of the open sites are ignored.
+ *   x1        device, [n_batch][x1_words] uint64 bitstrings (x1_words = ceil(n / 64) from
+ *             qfx_plan_info, 1 up to 64 qubits); the bits of the open sites are ignored.
  *   slices    [slice_begin, slice_end) of the plan's n_slices; a sub-range gives that
  *             range's contribution (sharding, or a fraction of paths).
  *   workspace device, ws_bytes >= qfx_plan_stats.workspace_min, 256-byte aligned; more
@@ -249,7 +253,7 @@ qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x1, int64_t 
  * Each batch item's `out` rows get the same values qfx_amplitudes would produce. */
 typedef struct {
   const qfx_plan* plan;
-  const uint64_t* x1;      /* device [n_batch] */
+  const uint64_t* x1;      /* device [n_batch][x1_words] */
   int64_t n_batch;
   int64_t slice_begin, slice_end;
   double* out;             /* device complex128 [n_batch][2^n_open], overwritten */
@@ -261,7 +265,8 @@ typedef struct qfx_batch qfx_batch;
 uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32_t n_items, int64_t slots);
 
 /* Builds the schedule and uploads it into `workspace` (synchronously on `stream`),
- * together with one copy of each distinct plan's tables at the workspace's start.  The workspace, items' x1 and out buffers must stay valid while
+ * together with one copy of each distinct plan's tables at the workspace's start.  The
+ * workspace, items' x1 and out buffers must stay valid while
  * the batch is used.  Errors: QFX_EINVAL, QFX_ENOMEM, QFX_ECUDA. */
 qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_items, void* workspace,
                              size_t ws_bytes, qfx_batch** out, void* stream);
@@ -356,7 +361,7 @@ qfx_status qfx_permute(const void* in, void* out, int32_t rank, const int64_t* s
                        const int32_t* perm, void* stream);
 
 /* Fast sampling with frugal rejection (Sec. III.B): one sample per x1 batch.
- *   x1         device uint64 [n_batch], the batches' x1 (as passed to qfx_amplitudes).
+ *   x1         device uint64 [n_batch][x1_words], the batches' x1 (as passed to qfx_amplitudes).
  *   amps       device complex128 [n_batch][2^n_open], 16-byte aligned: qfx_amplitudes'
  *              output for the same plan and x1 (any slice range: a fraction f of the
  *              slices gives noisy sampling at fidelity about f, Sec. III.C).
@@ -369,8 +374,8 @@ qfx_status qfx_permute(const void* in, void* out, int32_t rank, const int64_t* s
  *              p * (2^n / M), each operation rounded to nearest (no fused multiply-add).
  *              With amplitudes of fidelity f pass M * f.
  *   x2_out     device int64 [n_batch]: the first accepted x2 in scan order, -1 if none.
- *   bits_out   device uint64 [n_batch] or NULL: x1 with bit open_sites[i] set to bit i of
- *              x2 (x1 unchanged where x2_out is -1).
+ *   bits_out   device uint64 [n_batch][x1_words] or NULL: x1 with the bit of open_sites[i]
+ *              set to bit i of x2 (x1 unchanged where x2_out is -1).
  * One block per batch; asynchronous on `stream`; no allocation.
  * Errors: QFX_EINVAL (NULL or misaligned pointers, M not finite and > 0), QFX_ECUDA. */
 qfx_status qfx_frugal_select(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,

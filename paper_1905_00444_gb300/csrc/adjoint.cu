@@ -333,7 +333,7 @@ __host__ __device__ __forceinline__ int ev_slots(int kind) { return kind == EV_B
 
 __global__ void __launch_bounds__(kT) fold_backward_kernel(
     const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events, const double* __restrict__ mats,
-    const CutDev* __restrict__ cuts, int n_cuts, const uint64_t* __restrict__ x1, int64_t b, int64_t sid,
+    const CutDev* __restrict__ cuts, int n_cuts, const uint64_t* __restrict__ x1w, int64_t sid,
     const float2* __restrict__ sgrad, double* __restrict__ bpart, const int64_t* __restrict__ part_off) {
   __shared__ double wpart[kT / 32][kMaxEvents][8];
   const FoldSite st = sites[blockIdx.y];
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
   const int64_t vu = r;
   const uint64_t val0 = (uint64_t)(vu + off[0]), val1 = (uint64_t)(vl + off[1]);
   const uint64_t val2 = (uint64_t)(vr + off[2]), val3 = (uint64_t)(vd + off[3]);
-  const int xv = st.x_open ? (int)vx : (int)((x1[b] >> st.qubit) & 1ull);
+  const int xv = st.x_open ? (int)vx : (int)((x1w[st.qubit >> 6] >> (st.qubit & 63)) & 1ull);
   const float2 zero = make_float2(0.f, 0.f);
   auto leg = [&](const FoldEvent& ev, uint64_t width_mask) {
     const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
@@ -644,8 +644,8 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
     const int64_t b = item % n_batch, sid = slice_begin + item / n_batch;
     e = cudaMemsetAsync(hdr, 0, (size_t)n * 8 + 16, st);
     if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes_backward: header");
-    int err = launch_fold(t, n, max_site, (int)p->cut_dev.size(), x1, n_batch, slice_begin, item, 1,
-                          hdr, 0, sites, 0, 0, st);
+    int err = launch_fold(t, n, max_site, (int)p->cut_dev.size(), x1, p->x1_words, n_batch, slice_begin,
+                          item, 1, hdr, 0, sites, 0, 0, st);
     if (!err) err = launch_scale(t, n, max_site, 1, hdr, 0, sites, 0, 0, st);
     if (err) return cuda_fail(err, "qfx_amplitudes_backward: fold");
     // forward sweep, keeping every step's output (full) or the boundary at the start of
@@ -720,8 +720,8 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
     }
     // back through every site's time fold
     dim3 fg((unsigned)((max_site + kT - 1) / kT), n);
-    fold_backward_kernel<<<fg, kT, 0, st>>>(t.sites, t.events, t.mats, t.cuts, (int)p->cut_dev.size(), x1, b,
-                                            sid, sgrad, (double*)(ws + Lw.bpart),
+    fold_backward_kernel<<<fg, kT, 0, st>>>(t.sites, t.events, t.mats, t.cuts, (int)p->cut_dev.size(),
+                                            x1 + b * p->x1_words, sid, sgrad, (double*)(ws + Lw.bpart),
                                             t.partoff);
     const int nev = (int)p->events.size();
     event_reduce_kernel<<<(nev * 32 + kT - 1) / kT, kT, 0, st>>>(t.sites, n, t.events,

@@ -59,7 +59,7 @@ struct PlanDev {
 struct WorkDev {
   int32_t plan, slot;
   int64_t b, sid;
-  const uint64_t* x1;
+  const uint64_t* x1;     // this work item's bitstring (x1_words words)
   double* out;            // this work item's output row
   int32_t first, pad;     // first slice of the row: assign instead of add
 };
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kT, 1) batch_kernel(const BatchArgs a) {
         float mx = 0.f;
         for (int64_t i = start + tid; i < end; i += kT) {
           const float2 v = foldk::fold_element(st, pl.t.events, pl.t.mats, pl.t.cuts, pl.n_cuts,
-                                               w.x1[w.b], w.sid, i);
+                                               w.x1, w.sid, i);
           T[i] = v;
           mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
@@ -576,7 +576,8 @@ extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_i
     for (int64_t w = 0; w < NW; ++w) {
       const qfx_plan* p = plans[work[w].plan];
       const int64_t per = int64_t(1) << p->open_sites.size();
-      wd[w] = WorkDev{work[w].plan, (int32_t)(w % G), work[w].b, work[w].sid, work[w].it->x1,
+      wd[w] = WorkDev{work[w].plan, (int32_t)(w % G), work[w].b, work[w].sid,
+                      work[w].it->x1 + work[w].b * p->x1_words,
                       work[w].it->out + 2 * work[w].b * per, work[w].first ? 1 : 0, 0};
     }
     std::memcpy(at(o_work), wd.data(), wd.size() * sizeof(WorkDev));

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <sstream>
 #include <string>
+#include <vector>
 
 #include "qfx_internal.h"
 
@@ -28,7 +29,7 @@ qfx_status build(int32_t rows, int32_t cols, const qfx_gate* gates, int64_t n_ga
   if (!out) return qfx::fail(QFX_EINVAL, "qfx_circuit_create: out is NULL");
   *out = nullptr;
   if (rows < 1 || cols < 1 || (int64_t)rows * cols > qfx::kMaxSites)
-    return qfx::fail(QFX_EINVAL, "qfx_circuit_create: need 1 <= rows*cols <= 64");
+    return qfx::fail(QFX_EINVAL, "qfx_circuit_create: need 1 <= rows*cols <= " + std::to_string(qfx::kMaxSites));
   if (n_gates < 0 || (n_gates > 0 && !gates))
     return qfx::fail(QFX_EINVAL, "qfx_circuit_create: bad gate array");
   const int n = rows * cols;
@@ -67,16 +68,16 @@ qfx_status build(int32_t rows, int32_t cols, const qfx_gate* gates, int64_t n_ga
   // disjoint qubits within each layer
   for (size_t i = 0; i < c->gates.size();) {
     size_t j = i;
-    uint64_t used = 0;
+    std::vector<char> used((size_t)n, 0);
     while (j < c->gates.size() && c->gates[j].layer == c->gates[i].layer) {
       const auto& g = c->gates[j];
-      uint64_t m = (1ull << g.q0) | (g.q1 >= 0 ? (1ull << g.q1) : 0ull);
-      if (used & m) {
+      if (used[g.q0] || (g.q1 >= 0 && used[g.q1])) {
         int layer = g.layer;
         delete c;
         return qfx::fail(QFX_EINVAL, "layer " + std::to_string(layer) + ": qubit used twice");
       }
-      used |= m;
+      used[g.q0] = 1;
+      if (g.q1 >= 0) used[g.q1] = 1;
       ++j;
     }
     i = j;

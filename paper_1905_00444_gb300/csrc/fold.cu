@@ -26,9 +26,9 @@ constexpr int kThreads = 256;
 __global__ void __launch_bounds__(kThreads) fold_kernel(
     const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events,
     const double* __restrict__ mats, const CutDev* __restrict__ cuts, int n_cuts,
-    const uint64_t* __restrict__ x1, int64_t n_batch, int64_t slice_begin, int64_t item0,
-    char* hdr, uint64_t hdr_stride, char* items, uint64_t item_bytes, uint64_t sites_off,
-    int n_sites) {
+    const uint64_t* __restrict__ x1, int x1_words, int64_t n_batch, int64_t slice_begin,
+    int64_t item0, char* hdr, uint64_t hdr_stride, char* items, uint64_t item_bytes,
+    uint64_t sites_off, int n_sites) {
   const FoldSite st = sites[blockIdx.y];
   const int g = blockIdx.z;
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) fold_kernel(
     const int64_t item = item0 + g;
     const int64_t b = item % n_batch;
     const int64_t sid = slice_begin + item / n_batch;
-    const float2 out = foldk::fold_element(st, events, mats, cuts, n_cuts, x1[b], sid, i);
+    const float2 out = foldk::fold_element(st, events, mats, cuts, n_cuts, x1 + b * x1_words, sid, i);
     float2* T = reinterpret_cast<float2*>(items + (uint64_t)g * item_bytes + sites_off) + st.offset;
     T[i] = out;
     mx = fmaxf(fabsf(out.x), fabsf(out.y));
@@ -107,12 +107,12 @@ __global__ void __launch_bounds__(kThreads) accumulate_kernel(
 }  // namespace
 
 int launch_fold(const DeviceTables& t, int n_sites, int64_t max_site_size, int n_cuts,
-                const uint64_t* x1, int64_t n_batch, int64_t slice_begin, int64_t item0,
-                int items, char* hdr, uint64_t hdr_stride, char* itemsp, uint64_t item_bytes,
-                uint64_t sites_off, void* stream) {
+                const uint64_t* x1, int x1_words, int64_t n_batch, int64_t slice_begin,
+                int64_t item0, int items, char* hdr, uint64_t hdr_stride, char* itemsp,
+                uint64_t item_bytes, uint64_t sites_off, void* stream) {
   dim3 grid((unsigned)((max_site_size + kThreads - 1) / kThreads), n_sites, items);
   fold_kernel<<<grid, kThreads, 0, (cudaStream_t)stream>>>(
-      t.sites, t.events, t.mats, t.cuts, n_cuts, x1, n_batch, slice_begin, item0, hdr,
+      t.sites, t.events, t.mats, t.cuts, n_cuts, x1, x1_words, n_batch, slice_begin, item0, hdr,
       hdr_stride, itemsp, item_bytes, sites_off, n_sites);
   count_launch();
   return (int)cudaGetLastError();

@@ -15,14 +15,16 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
   return make_double2(a.x + b.x, a.y + b.y);
 }
 
-// Element i of site `st` for slice `sid` and output bits x1v: FP64 evolution of the
+// Element i of site `st` for slice `sid` and the output bitstring x1w (its words; qubit q
+// is bit q % 64 of word q / 64): FP64 evolution of the
 // site's 2-vector through its time line, rounded once to complex64.  A diagonal two-qubit
 // gate reads one bit of the bond value (projector on q0, diagonal on q1); a general one
 // reads two, k = 2*o0 + i0 (|o0><i0| on q0, the 2x2 block B_k of the gate on q1).
 __device__ __forceinline__ float2 fold_element(const FoldSite& st, const FoldEvent* __restrict__ events,
                                                const double* __restrict__ mats,
                                                const CutDev* __restrict__ cuts, int n_cuts,
-                                               uint64_t x1v, int64_t sid, int64_t i) {
+                                               const uint64_t* __restrict__ x1w, int64_t sid,
+                                               int64_t i) {
   int64_t off[4] = {0, 0, 0, 0};
   for (int c = 0; c < n_cuts; ++c) {
     const CutDev cd = cuts[c];
@@ -39,7 +41,7 @@ __device__ __forceinline__ float2 fold_element(const FoldSite& st, const FoldEve
   const int64_t vu = r;
   const uint64_t val0 = (uint64_t)(vu + off[0]), val1 = (uint64_t)(vl + off[1]);
   const uint64_t val2 = (uint64_t)(vr + off[2]), val3 = (uint64_t)(vd + off[3]);
-  const int xv = st.x_open ? (int)vx : (int)((x1v >> st.qubit) & 1ull);
+  const int xv = st.x_open ? (int)vx : (int)((x1w[st.qubit >> 6] >> (st.qubit & 63)) & 1ull);
   double2 v0 = make_double2(1.0, 0.0), v1 = make_double2(0.0, 0.0);
   for (int e = st.ev_begin; e < st.ev_end; ++e) {
     const FoldEvent ev = events[e];

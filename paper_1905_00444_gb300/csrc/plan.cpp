@@ -145,6 +145,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     auto p = new qfx_plan;
     std::unique_ptr<qfx_plan> guard(p);
     p->rows = c->rows; p->cols = c->cols; p->n = n;
+    p->x1_words = (n + 63) / 64;
     p->n_gates = (int)c->gates.size();
     p->lines = geo.W;
     p->line_len = geo.L;
@@ -428,6 +429,7 @@ extern "C" qfx_status qfx_plan_info(const qfx_plan* p, qfx_plan_stats* s) {
   s->workspace_min = qfx_workspace_bytes(p, 1);
   s->largest_step = p->largest_step;
   s->precision = p->precision;
+  s->x1_words = p->x1_words;
   return QFX_OK;
 }
 

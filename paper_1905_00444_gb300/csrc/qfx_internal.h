@@ -12,7 +12,7 @@
 
 namespace qfx {
 
-constexpr int kMaxSites = 64;
+constexpr int kMaxSites = 144;   // 12 x 12 grids; bitstrings of more than 64 qubits span several words
 constexpr int kMaxOpen = 24;
 constexpr int kMaxCuts = 64;
 
@@ -110,6 +110,7 @@ struct DeviceTables {
 
 struct qfx_plan {
   int rows = 0, cols = 0, n = 0;
+  int x1_words = 1;               // uint64 words per bitstring, ceil(n / 64)
   int n_gates = 0;
   int lines = 0, line_len = 0;    // sweep geometry: steps [w*line_len, (w+1)*line_len) form line w
   int precision = 0;
@@ -154,9 +155,9 @@ qfx_status cuda_fail(int err, const char* what);
 
 // kernels (implemented in .cu files); all return 0 or a cudaError_t value
 int launch_fold(const DeviceTables& t, int n_sites, int64_t max_site_size, int n_cuts,
-                const uint64_t* x1, int64_t n_batch, int64_t slice_begin, int64_t item0,
-                int items, char* hdr, uint64_t hdr_stride, char* itemsp, uint64_t item_bytes,
-                uint64_t sites_off, void* stream);
+                const uint64_t* x1, int x1_words, int64_t n_batch, int64_t slice_begin,
+                int64_t item0, int items, char* hdr, uint64_t hdr_stride, char* itemsp,
+                uint64_t item_bytes, uint64_t sites_off, void* stream);
 int launch_scale(const DeviceTables& t, int n_sites, int64_t max_site_size, int items,
                  char* hdr, uint64_t hdr_stride, char* itemsp, uint64_t item_bytes,
                  uint64_t sites_off, void* stream);

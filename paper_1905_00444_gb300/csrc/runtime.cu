@@ -214,7 +214,7 @@ qfx_status exec_amplitudes(const qfx_plan* p, const DeviceTables& t, const uint6
     if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes: clearing header");
     int slot;
     profile_begin(st, &slot);
-    int err = launch_fold(t, n_sites, max_site, (int)p->cut_dev.size(), x1, n_batch,
+    int err = launch_fold(t, n_sites, max_site, (int)p->cut_dev.size(), x1, p->x1_words, n_batch,
                           slice_begin, item0, g, hdr_base, hdr, items, ib, L.sites, st);
     profile_end(st, slot, -1, 0, 1, 0.0, 0.0);
     if (err) return cuda_fail(err, "fold kernel");

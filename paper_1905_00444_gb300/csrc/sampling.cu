@@ -24,13 +24,13 @@ namespace {
 constexpr int kST = 256;
 
 struct OpenSites {
-  int8_t q[kMaxOpen];
+  int16_t q[kMaxOpen];
 };
 
 __global__ void __launch_bounds__(kST) frugal_select_kernel(
     const double* __restrict__ amps, const double* __restrict__ u, const uint64_t* __restrict__ scan_mask,
-    const uint64_t* __restrict__ x1, int n_open, OpenSites os, double scale, int64_t* __restrict__ x2_out,
-    uint64_t* __restrict__ bits_out) {
+    const uint64_t* __restrict__ x1, int x1_words, int n_open, OpenSites os, double scale,
+    int64_t* __restrict__ x2_out, uint64_t* __restrict__ bits_out) {
   __shared__ unsigned long long first;
   const int64_t b = blockIdx.x;
   const int64_t per = int64_t(1) << n_open;
@@ -56,17 +56,21 @@ __global__ void __launch_bounds__(kST) frugal_select_kernel(
   }
   if (threadIdx.x == 0) {
     const int64_t t = (int64_t)first;
-    uint64_t bits = x1[b];
-    int64_t x2 = -1;
-    if (t < per) {
-      x2 = (int64_t)((uint64_t)t ^ m);
-      for (int i = 0; i < n_open; ++i) {
-        const uint64_t bit = 1ull << os.q[i];
-        bits = ((x2 >> i) & 1) ? (bits | bit) : (bits & ~bit);
+    const int64_t x2 = t < per ? (int64_t)((uint64_t)t ^ m) : -1;
+    x2_out[b] = x2;
+    if (bits_out) {
+      // x1 with each open site's bit replaced by the sample's (x1 unchanged without one)
+      for (int wd = 0; wd < x1_words; ++wd) {
+        uint64_t bits = x1[b * x1_words + wd];
+        if (x2 >= 0)
+          for (int i = 0; i < n_open; ++i) {
+            if ((os.q[i] >> 6) != wd) continue;
+            const uint64_t bit = 1ull << (os.q[i] & 63);
+            bits = ((x2 >> i) & 1) ? (bits | bit) : (bits & ~bit);
+          }
+        bits_out[b * x1_words + wd] = bits;
       }
     }
-    x2_out[b] = x2;
-    if (bits_out) bits_out[b] = bits;
   }
 }
 
@@ -89,12 +93,12 @@ extern "C" qfx_status qfx_frugal_select(const qfx_plan* p, const uint64_t* x1, i
   const int n_open = (int)p->open_sites.size();
   if (n_open > kMaxOpen) return fail(QFX_EINVAL, "qfx_frugal_select: more than 24 open sites");
   OpenSites os{};
-  for (int i = 0; i < n_open; ++i) os.q[i] = (int8_t)p->open_sites[i];
+  for (int i = 0; i < n_open; ++i) os.q[i] = (int16_t)p->open_sites[i];
   const double scale = std::ldexp(1.0, p->rows * p->cols) / M;
   int slot;
   profile_begin(stream, &slot);
   frugal_select_kernel<<<(unsigned)n_batch, kST, 0, (cudaStream_t)stream>>>(
-      amps, u, scan_mask, x1, n_open, os, scale, x2_out, bits_out);
+      amps, u, scan_mask, x1, p->x1_words, n_open, os, scale, x2_out, bits_out);
   count_launch();
   const cudaError_t e = cudaGetLastError();
   profile_end(stream, slot, -1, 0, 5, 0.0, (double)n_batch * (24.0 * (double)(int64_t(1) << n_open) + 24.0));

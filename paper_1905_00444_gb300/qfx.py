@@ -48,7 +48,7 @@ class PlanStats(C.Structure):
                 ("n_cuts", C.c_int32), ("n_sites", C.c_int32), ("flops_per_item", C.c_double),
                 ("bytes_per_item", C.c_double), ("max_elements", C.c_int64),
                 ("item_bytes", C.c_uint64), ("workspace_min", C.c_uint64),
-                ("largest_step", C.c_int32), ("precision", C.c_int32)]
+                ("largest_step", C.c_int32), ("precision", C.c_int32), ("x1_words", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -227,6 +227,14 @@ class Plan:
         arr = (C.c_int32 * max(1, st.n_open))()
         _check(lib.qfx_plan_open_sites(h, arr))
         self.open_sites = [arr[i] for i in range(st.n_open)]
+        self.x1_words = st.x1_words
+
+    def batch_of(self, x1) -> int:
+        """Bitstrings in x1 (x1_words uint64 words each)."""
+        n = x1.numel()
+        if n % self.x1_words:
+            raise ValueError(f"x1 holds {n} words; bitstrings of this plan have {self.x1_words} each")
+        return n // self.x1_words
 
     @property
     def n_slices(self) -> int:
@@ -272,11 +280,11 @@ def amplitudes(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Optional[int]
                workspace=None, out=None, stream=None):
     """Amplitudes [n_batch, 2^n_open] (torch complex128 on x1's device).
 
-    x1: torch int64/uint64 CUDA tensor of bitstrings.  workspace: torch uint8 CUDA tensor
-    (default: room for one work item)."""
+    x1: torch int64/uint64 CUDA tensor of bitstrings, plan.x1_words words each (one word
+    up to 64 qubits).  workspace: torch uint8 CUDA tensor (default: room for one work item)."""
     import torch
     _need(x1, "x1", size=8)
-    n_batch = x1.numel()
+    n_batch = plan.batch_of(x1)
     if slice_end is None:
         slice_end = plan.n_slices
     if workspace is None:
@@ -311,10 +319,11 @@ def amplitudes_backward(plan: Plan, x1, grad_out, *, slice_begin: int = 0,
     if entries not in (4, 16):
         raise ValueError("entries must be 4 or 16")
     grad_out = grad_out.to(device=x1.device, dtype=torch.complex128).contiguous()
-    _need(grad_out, "grad_out", numel=x1.numel() << len(plan.open_sites))
+    n_batch = plan.batch_of(x1)
+    _need(grad_out, "grad_out", numel=n_batch << len(plan.open_sites))
     out = torch.empty((plan.stats_n_gates, entries), dtype=torch.complex128, device=x1.device)
     f = lib.qfx_amplitudes_backward if entries == 4 else lib.qfx_amplitudes_backward_full
-    _check(f(plan._h, x1.data_ptr(), x1.numel(), slice_begin, slice_end, grad_out.data_ptr(),
+    _check(f(plan._h, x1.data_ptr(), n_batch, slice_begin, slice_end, grad_out.data_ptr(),
              out.data_ptr(), workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)))
     return out
 
@@ -324,11 +333,11 @@ def frugal_select(plan: Plan, x1, amps, u, scan_mask, M: float = 10.0, *, stream
 
     amps: complex128 [n_batch, 2^n_open] from amplitudes(plan, x1, ...); u: float64
     [n_batch, 2^n_open] uniforms in [0, 1); scan_mask: int64/uint64 [n_batch].  Returns
-    (x2 int64 [n_batch], -1 where no candidate was accepted; bitstrings int64 [n_batch],
-    x1 with the open-site bits set from x2)."""
+    (x2 int64 [n_batch], -1 where no candidate was accepted; bitstrings int64 [n_batch]
+    (or [n_batch, x1_words] above 64 qubits), x1 with the open-site bits set from x2)."""
     import torch
     _need(x1, "x1", size=8)
-    n_batch = x1.numel()
+    n_batch = plan.batch_of(x1)
     per = 1 << len(plan.open_sites)
     _need(amps, "amps", dtype=torch.complex128, numel=n_batch * per, device=x1.device)
     _need(u, "u", dtype=torch.float64, numel=n_batch * per, device=x1.device)
@@ -336,7 +345,8 @@ def frugal_select(plan: Plan, x1, amps, u, scan_mask, M: float = 10.0, *, stream
     if tuple(amps.shape) != (n_batch, per) or tuple(u.shape) != (n_batch, per):
         raise ValueError("amps and u must be [n_batch, 2^n_open]")
     x2 = torch.empty(n_batch, dtype=torch.int64, device=x1.device)
-    bits = torch.empty(n_batch, dtype=torch.int64, device=x1.device)
+    bits = torch.empty(n_batch if plan.x1_words == 1 else (n_batch, plan.x1_words),
+                       dtype=torch.int64, device=x1.device)
     _check(lib.qfx_frugal_select(plan._h, x1.data_ptr(), n_batch, amps.data_ptr(), u.data_ptr(),
                                  scan_mask.data_ptr(), float(M), x2.data_ptr(), bits.data_ptr(),
                                  _stream_ptr(stream)))
@@ -370,11 +380,11 @@ class Batch:
         self.outs = []
         for i, (plan, x1, sb, se) in enumerate(items):
             _need(x1, f"items[{i}] x1", size=8, device=items[0][1].device)
-            out = torch.empty((x1.numel(), 1 << len(plan.open_sites)), dtype=torch.complex128,
+            out = torch.empty((plan.batch_of(x1), 1 << len(plan.open_sites)), dtype=torch.complex128,
                               device=x1.device)
             self.outs.append(out)
             self._keep += [plan, x1, out]
-            arr[i] = BatchItem(plan._h.value, x1.data_ptr(), x1.numel(), sb,
+            arr[i] = BatchItem(plan._h.value, x1.data_ptr(), plan.batch_of(x1), sb,
                                plan.n_slices if se is None else se, out.data_ptr())
         self._arr = arr
         if workspace is None:
@@ -426,7 +436,7 @@ def amplitudes_static(plan: Plan, x1, *, slice_begin: int = 0, slice_end: Option
     buffer is still the caller's).  Calls that overlap on the GPU race on that array."""
     import torch
     _need(x1, "x1", size=8)
-    n_batch = x1.numel()
+    n_batch = plan.batch_of(x1)
     if slice_end is None:
         slice_end = plan.n_slices
     if out is None:

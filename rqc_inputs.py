@@ -225,6 +225,30 @@ def random_bitstrings(n_qubits: int, count: int, seed: int) -> np.ndarray:
     return np.array([counter_draw(seed, 0xB17, i) & mask for i in range(count)], dtype=np.uint64)
 
 
+def random_bitstring_words(n_qubits: int, count: int, seed: int) -> np.ndarray:
+    """count bitstrings of n_qubits bits as uint64 words [count, ceil(n_qubits / 64)]: qubit q
+    is bit q % 64 of word q / 64.  Word w of bitstring i is counter_draw(seed, 0xB17 + w, i),
+    masked to the qubits it holds, so one-word bitstrings equal random_bitstrings'."""
+    W = (n_qubits + 63) // 64
+    out = np.zeros((count, W), dtype=np.uint64)
+    for w in range(W):
+        bits = min(64, n_qubits - 64 * w)
+        mask = (1 << bits) - 1
+        out[:, w] = [counter_draw(seed, 0xB17 + w, i) & mask for i in range(count)]
+    return out
+
+
+def words_to_int(words) -> int:
+    """The bitstring held by uint64 words (word w holds qubits 64 w .. 64 w + 63)."""
+    return sum(int(v) << (64 * w) for w, v in enumerate(np.asarray(words, dtype=np.uint64).reshape(-1)))
+
+
+def int_to_words(x: int, n_qubits: int) -> np.ndarray:
+    """Inverse of words_to_int for an n_qubits bitstring."""
+    W = (n_qubits + 63) // 64
+    return np.array([(int(x) >> (64 * w)) & _M64 for w in range(W)], dtype=np.uint64)
+
+
 def sampling_draws(n_qubits: int, n_open: int, count: int, seed: int):
     """Random inputs of `count` fast-sampling batches (one x1 each): x1 (uint64, low n_qubits
     bits uniform), a scan mask (uint64, low n_open bits uniform) and one uniform variate in

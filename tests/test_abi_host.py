@@ -396,3 +396,24 @@ def test_planner_invariants_on_random_circuits():
         assert p.n_slices == want_slices, case
         if cap:
             assert p.stats["max_elements"] * 8 <= cap, case
+
+
+def test_more_than_64_qubits_use_word_bitstrings():
+    """Grids up to 144 qubits; a bitstring spans ceil(n / 64) words (Table I's 11x11)."""
+    for rows, cols, words in ((11, 11, 2), (12, 12, 3), (8, 8, 1), (13, 5, 2)):
+        p = qfx.Plan(qfx.Circuit(ri.rqc(rows, cols, 8, seed=0)), n_open=4)
+        assert p.x1_words == words == p.stats["x1_words"]
+    with pytest.raises(qfx.QfxError) as e:
+        qfx.Circuit(ri.rqc(13, 12, 2, seed=0))
+    assert e.value.status == q.QFX_EINVAL and "144" in str(e.value)
+
+
+def test_word_bitstring_helpers():
+    a = ri.random_bitstrings(49, 4, seed=3)
+    w = ri.random_bitstring_words(49, 4, seed=3)
+    assert w.shape == (4, 1) and np.array_equal(a, w[:, 0])
+    w = ri.random_bitstring_words(121, 5, seed=1)
+    assert w.shape == (5, 2) and np.all(w[:, 1] < (1 << 57))
+    for row in w:
+        x = ri.words_to_int(row)
+        assert x < 2 ** 121 and np.array_equal(ri.int_to_words(x, 121), row)
