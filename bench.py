@@ -512,7 +512,7 @@ def measure_adjoint(qfx, torch, steps, warmup):
     clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     f_ms, b_ms = [], []
-    for _ in range(max(steps, 3)):
+    for _ in range(max(steps, 60)):      # ~0.3 s, so the clock record has samples
         ev[0].record()
         amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
         ev[1].record()
@@ -551,12 +551,13 @@ def measure_permute(qfx, torch, steps, warmup):
             qfx.permute(x, shape, perm, out=y)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(steps, 100)           # ~0.1 s per case, so the clock record has samples
         e0.record()
-        for _ in range(steps):
+        for _ in range(reps):
             qfx.permute(x, shape, perm, out=y)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
+        ms = e0.elapsed_time(e1) / reps
         gbs = 16.0 * n / (ms / 1e3) / 1e9
         out.append({"shape": list(shape), "perm": list(perm), "ms": ms, "GB/s": gbs,
                     "frac": gbs / peaks["hbm_gbs"]})
