@@ -672,8 +672,11 @@ def measure_batch(qfx, torch, mix, n_open, steps, warmup, tc, autotune):
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
     res = {"n_items": len(items), "flops_per_batch": flops,
            "fp32_persistent": {"value": flops / t_graph / 1e12, "ms_per_batch": 1e3 * t_graph,
-                               "items_per_s": len(items) / t_graph, "kernel_launches": 1,
-                               "tasks": n_tasks_fp32, "slots": slots_fp32},
+                               "items_per_s": len(items) / t_graph, "tasks_or_graph_nodes": n_tasks_fp32,
+                               "slots": slots_fp32,
+                               "what": "one batch replayed from a CUDA graph: items with steps of "
+                                       ">= 512 tiles as their own launches, the others in one "
+                                       "persistent launch"},
            "fp32_per_item": {"value": flops / t_items / 1e12, "ms_per_batch": 1e3 * t_items,
                              "items_per_s": len(items) / t_items, "kernel_launches": per_item_launches},
            "fp32_identical": bool(same), "autotuned": bool(autotune)}

@@ -313,7 +313,9 @@ struct qfx_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t graph_kernels = 0;
+  qfx_batch* sub = nullptr;        // persistent sub-batch of the small items, run inside the graph
   ~qfx_batch() {
+    delete sub;
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
   }
@@ -321,19 +323,50 @@ struct qfx_batch {
 
 using namespace qfx;
 
-// Graph executor for batches with split-precision plans.  Every item's ordinary launch
-// sequence (qfx_amplitudes' fold, scale, steps, accumulation; one work item in flight) is
-// recorded on one of `lanes` streams forked from a capture stream, each lane with its own
-// workspace slot, and the lanes join again: one CUDA graph, replayed by qfx_batch_run.
-// Items on different lanes overlap; an item's own launches keep their order.
+// Whether an FP32 work item runs as its own launch sequence in a batch's graph: its
+// largest step has at least kBigTiles output tiles, so the step kernels fill the GPU many
+// times over and launch overhead is negligible, while the same tiles run slower inside the
+// persistent kernel (measured: 48.2 against 41.6 TFLOP/s on the mixed-grid batch).
+constexpr int64_t kBigTiles = 512;
+bool item_is_big(const qfx_plan* p) {
+  int64_t most = 0;
+  for (size_t i = 1; i < p->steps.size(); ++i) {
+    const Step& sp = p->steps[i];
+    const int v = sp.variant >= kVariantTcBf16 ? pick_variant(sp.N, sp.Sd) : sp.variant;
+    most = std::max(most, step_tiles(v, sp.N, sp.P * sp.Sd));
+  }
+  return most >= kBigTiles;
+}
+
+static qfx_status prepare_persistent(const qfx_batch_item* items, int32_t n_items,
+                                     const std::map<const qfx_plan*, const DeviceTables*>& tabmap,
+                                     void* workspace, size_t ws_bytes, qfx_batch** out, void* stream);
+
+static uint64_t qfx_batch_workspace_bytes_nt(const qfx_batch_item* items, int32_t n_items, int64_t slots);
+
+// Workspace of the persistent sub-batch of a graph batch (its small items, 16 slots).
+constexpr int64_t kSubSlots = 16;
+static uint64_t sub_bytes(const std::vector<qfx_batch_item>& small) {
+  return small.empty() ? 0 : a256(qfx_batch_workspace_bytes_nt(small.data(), (int32_t)small.size(), kSubSlots));
+}
+
+// Graph executor.  Every item's ordinary launch sequence (qfx_amplitudes' fold, scale,
+// steps, accumulation; one work item in flight) is recorded on one of `lanes` streams
+// forked from a capture stream, each lane with its own workspace slot, and the lanes join
+// again: one CUDA graph, replayed by qfx_batch_run.  Items on different lanes overlap; an
+// item's own launches keep their order.  Batches with split-precision plans run all
+// their items this way; FP32 batches run their large items this way and their small items
+// (`small`) in one persistent launch recorded on a lane of its own.
 static qfx_status prepare_graph(const qfx_batch_item* items, int32_t n_items,
-                                const std::vector<const DeviceTables*>& tabs,
-                                const std::map<const qfx_plan*, int>& plan_ix, void* workspace,
-                                size_t ws_bytes, qfx_batch** out) {
+                                const std::vector<qfx_batch_item>& small,
+                                const std::map<const qfx_plan*, const DeviceTables*>& tabmap,
+                                void* workspace, size_t ws_bytes, qfx_batch** out, void* stream) {
   const uint64_t lane = graph_lane_bytes(items, n_items);
+  const uint64_t sub_ws = sub_bytes(small);
+  if (ws_bytes < sub_ws) return fail(QFX_ENOMEM, "qfx_batch_prepare: workspace smaller than the small items' share");
   int64_t n_work = 0;
   for (int i = 0; i < n_items; ++i) n_work += (items[i].slice_end - items[i].slice_begin) * items[i].n_batch;
-  const int64_t lanes = std::min<int64_t>({kGraphLanes, (int64_t)(ws_bytes / lane), (int64_t)n_items});
+  const int64_t lanes = std::min<int64_t>({kGraphLanes, (int64_t)((ws_bytes - sub_ws) / lane), (int64_t)n_items});
   if (lanes < 1) return fail(QFX_ENOMEM, "qfx_batch_prepare: workspace smaller than one work item");
   // kernel attributes are set before the capture (a captured launch must not be the first)
   int err = tc_prepare_attributes();
@@ -341,31 +374,39 @@ static qfx_status prepare_graph(const qfx_batch_item* items, int32_t n_items,
   if (err) return cuda_fail(err, "qfx_batch_prepare: kernel attributes");
   auto* B = new qfx_batch;
   std::unique_ptr<qfx_batch> guard(B);
+  if (!small.empty()) {   // uploads its schedule now, before the capture
+    qfx_status s = prepare_persistent(small.data(), (int32_t)small.size(), tabmap, workspace, sub_ws,
+                                      &B->sub, stream);
+    if (s != QFX_OK) return s;
+  }
+  char* lanes_base = (char*)workspace + sub_ws;
+  const int64_t n_streams = lanes + (small.empty() ? 0 : 1);
   cudaStream_t cap = nullptr;
-  std::vector<cudaStream_t> ls((size_t)lanes, nullptr);
-  std::vector<cudaEvent_t> ev((size_t)lanes + 1, nullptr);
+  std::vector<cudaStream_t> ls((size_t)n_streams, nullptr);
+  std::vector<cudaEvent_t> ev((size_t)n_streams + 1, nullptr);
   auto release = [&]() {
     for (auto& x : ls) if (x) cudaStreamDestroy(x);
     for (auto& x : ev) if (x) cudaEventDestroy(x);
     if (cap) cudaStreamDestroy(cap);
   };
   cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-  for (int64_t l = 0; l < lanes && e == cudaSuccess; ++l) e = cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking);
+  for (int64_t l = 0; l < n_streams && e == cudaSuccess; ++l) e = cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking);
   for (size_t l = 0; l < ev.size() && e == cudaSuccess; ++l) e = cudaEventCreateWithFlags(&ev[l], cudaEventDisableTiming);
   if (e != cudaSuccess) { release(); return cuda_fail(e, "qfx_batch_prepare: streams"); }
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { release(); return cuda_fail(e, "qfx_batch_prepare: begin capture"); }
   qfx_status st = QFX_OK;
-  e = cudaEventRecord(ev[lanes], cap);
-  for (int64_t l = 0; l < lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(ls[l], ev[lanes], 0);
+  e = cudaEventRecord(ev[n_streams], cap);
+  for (int64_t l = 0; l < n_streams && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(ls[l], ev[n_streams], 0);
   if (e != cudaSuccess) st = cuda_fail(e, "qfx_batch_prepare: fork");
+  if (st == QFX_OK && B->sub) st = qfx_batch_run(B->sub, ls[lanes]);
   for (int i = 0; i < n_items && st == QFX_OK; ++i) {
     const qfx_batch_item& it = items[i];
     const int64_t l = i % lanes;
-    st = exec_amplitudes(it.plan, *tabs[plan_ix.at(it.plan)], it.x1, it.n_batch, it.slice_begin,
-                         it.slice_end, (char*)workspace + l * lane, 1, it.out, ls[l]);
+    st = exec_amplitudes(it.plan, *tabmap.at(it.plan), it.x1, it.n_batch, it.slice_begin,
+                         it.slice_end, lanes_base + l * lane, 1, it.out, ls[l]);
   }
-  for (int64_t l = 0; l < lanes && st == QFX_OK; ++l) {
+  for (int64_t l = 0; l < n_streams && st == QFX_OK; ++l) {
     e = cudaEventRecord(ev[l], ls[l]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev[l], 0);
     if (e != cudaSuccess) st = cuda_fail(e, "qfx_batch_prepare: join");
@@ -389,77 +430,27 @@ static qfx_status prepare_graph(const qfx_batch_item* items, int32_t n_items,
     if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
   }
   B->graph_kernels = kernels;
-  B->n_work = n_work;
+  B->n_work = n_work + (B->sub ? B->sub->n_work : 0);
   B->slots = lanes;
   B->args.n_tasks = (int64_t)nn;
   *out = guard.release();
   return QFX_OK;
 }
 
-extern "C" uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32_t n_items,
-                                              int64_t slots) {
-  if (!items || n_items < 1 || slots < 1) return 0;
-  std::set<const qfx_plan*> distinct;
-  uint64_t tab = 0;   // one copy of each distinct plan's tables
-  for (int i = 0; i < n_items; ++i) {
-    if (!items[i].plan) return 0;
-    if (distinct.insert(items[i].plan).second) tab += qfx::table_bytes(items[i].plan);
-  }
-  if (qfx::batch_has_tc(items, n_items)) return tab + (uint64_t)slots * qfx::graph_lane_bytes(items, n_items);
-  uint64_t block = 0;
-  int64_t segs_est = 0, work = 0;
-  for (int i = 0; i < n_items; ++i) {
-    const qfx_plan* p = items[i].plan;
-    if (!p) return 0;
-    block = std::max<uint64_t>(block, p->layout.item_bytes);
-    const int64_t w = (items[i].slice_end - items[i].slice_begin) * items[i].n_batch;
-    work += w;
-    segs_est += w * ((int64_t)p->steps.size() + 3);
-  }
-  const uint64_t tables = a256((uint64_t)segs_est * sizeof(SegDev)) + a256((uint64_t)work * sizeof(WorkDev)) +
-                          (uint64_t)n_items * (64 * 1024) + (1u << 20);
-  const uint64_t control = a256(64 + (uint64_t)segs_est * 4);
-  return tab + control + tables + (uint64_t)slots * (a256(kMaxSites * 8) + a256(block));
-}
-
-extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_items, void* workspace,
-                                        size_t ws_bytes, qfx_batch** out, void* stream) {
-  if (!items || n_items < 1 || !workspace || !out) return fail(QFX_EINVAL, "qfx_batch_prepare: bad arguments");
-  *out = nullptr;
-  if ((uintptr_t)workspace & 255) return fail(QFX_EINVAL, "qfx_batch_prepare: workspace not 256-byte aligned");
+// The persistent scheduler: one launch runs every work item of `items` (FP32 plans).
+static qfx_status prepare_persistent(const qfx_batch_item* items, int32_t n_items,
+                                     const std::map<const qfx_plan*, const DeviceTables*>& tabmap,
+                                     void* workspace, size_t ws_bytes, qfx_batch** out, void* stream) {
   try {
     std::map<const qfx_plan*, int> plan_ix;
     std::vector<const qfx_plan*> plans;
-    for (int i = 0; i < n_items; ++i) {
-      const qfx_batch_item& it = items[i];
-      qfx_status s = check_amplitudes_args(it.plan, it.x1, it.n_batch, it.slice_begin, it.slice_end, it.out);
-      if (s != QFX_OK) return s;
-      if (!plan_ix.count(it.plan)) {
-        plan_ix[it.plan] = (int)plans.size();
-        plans.push_back(it.plan);
-      }
-    }
-    // plan tables: one copy per distinct plan at the start of the workspace, uploaded
-    // here (synchronously, before any capture); the schedule lives after them
-    std::vector<DeviceTables> tab_store(plans.size());
     std::vector<const DeviceTables*> tabs;
-    {
-      uint64_t o = 0;
-      cudaStream_t st = (cudaStream_t)stream;
-      for (size_t k = 0; k < plans.size(); ++k) {
-        if (o + table_bytes(plans[k]) > ws_bytes) return fail(QFX_ENOMEM, "qfx_batch_prepare: workspace smaller than the plans' tables");
-        qfx_status s = stage_tables(plans[k], (char*)workspace + o, stream, &tab_store[k]);
-        if (s != QFX_OK) return s;
-        tabs.push_back(&tab_store[k]);
-        o += table_bytes(plans[k]);
+    for (int i = 0; i < n_items; ++i)
+      if (!plan_ix.count(items[i].plan)) {
+        plan_ix[items[i].plan] = (int)plans.size();
+        plans.push_back(items[i].plan);
+        tabs.push_back(tabmap.at(items[i].plan));
       }
-      cudaError_t e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_prepare: plan tables");
-      workspace = (char*)workspace + o;
-      ws_bytes -= o;
-    }
-    if (batch_has_tc(items, n_items))
-      return prepare_graph(items, n_items, tabs, plan_ix, workspace, ws_bytes, out);
     // work items, slice-major within each batch item
     struct W { int plan; int64_t b, sid; const qfx_batch_item* it; bool first; };
     std::vector<W> work;
@@ -642,6 +633,94 @@ extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_i
     B->grid = (int)std::min<int64_t>((int64_t)sms * occ, std::max<int64_t>(1, task));
     *out = guard.release();
     return QFX_OK;
+  } catch (const std::exception& ex) {
+    return fail(QFX_EINVAL, std::string("qfx_batch_prepare: ") + ex.what());
+  }
+}
+
+// Workspace of a persistent batch of `items` with `slots` items in flight (no plan tables).
+static uint64_t qfx_batch_workspace_bytes_nt(const qfx_batch_item* items, int32_t n_items, int64_t slots) {
+  uint64_t block = 0;
+  int64_t segs_est = 0, work = 0;
+  for (int i = 0; i < n_items; ++i) {
+    const qfx_plan* p = items[i].plan;
+    block = std::max<uint64_t>(block, p->layout.item_bytes);
+    const int64_t w = (items[i].slice_end - items[i].slice_begin) * items[i].n_batch;
+    work += w;
+    segs_est += w * ((int64_t)p->steps.size() + 3);
+  }
+  const uint64_t tables = a256((uint64_t)segs_est * sizeof(SegDev)) + a256((uint64_t)work * sizeof(WorkDev)) +
+                          (uint64_t)n_items * (64 * 1024) + (1u << 20);
+  const uint64_t control = a256(64 + (uint64_t)segs_est * 4);
+  return control + tables + (uint64_t)slots * (a256(kMaxSites * 8) + a256(block));
+}
+
+extern "C" uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32_t n_items,
+                                              int64_t slots) {
+  if (!items || n_items < 1 || slots < 1) return 0;
+  std::set<const qfx_plan*> distinct;
+  uint64_t tab = 0;   // one copy of each distinct plan's tables
+  for (int i = 0; i < n_items; ++i) {
+    if (!items[i].plan) return 0;
+    if (distinct.insert(items[i].plan).second) tab += qfx::table_bytes(items[i].plan);
+  }
+  if (qfx::batch_has_tc(items, n_items)) return tab + (uint64_t)slots * qfx::graph_lane_bytes(items, n_items);
+  std::vector<qfx_batch_item> big, small;
+  for (int i = 0; i < n_items; ++i) (item_is_big(items[i].plan) ? big : small).push_back(items[i]);
+  if (!big.empty())
+    return tab + sub_bytes(small) + (uint64_t)slots * qfx::graph_lane_bytes(big.data(), (int32_t)big.size());
+  return tab + qfx_batch_workspace_bytes_nt(items, n_items, slots);
+}
+
+extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_items, void* workspace,
+                                        size_t ws_bytes, qfx_batch** out, void* stream) {
+  if (!items || n_items < 1 || !workspace || !out) return fail(QFX_EINVAL, "qfx_batch_prepare: bad arguments");
+  *out = nullptr;
+  if ((uintptr_t)workspace & 255) return fail(QFX_EINVAL, "qfx_batch_prepare: workspace not 256-byte aligned");
+  try {
+    std::map<const qfx_plan*, int> plan_ix;
+    std::vector<const qfx_plan*> plans;
+    for (int i = 0; i < n_items; ++i) {
+      const qfx_batch_item& it = items[i];
+      qfx_status s = check_amplitudes_args(it.plan, it.x1, it.n_batch, it.slice_begin, it.slice_end, it.out);
+      if (s != QFX_OK) return s;
+      if (!plan_ix.count(it.plan)) {
+        plan_ix[it.plan] = (int)plans.size();
+        plans.push_back(it.plan);
+      }
+    }
+    // plan tables: one copy per distinct plan at the start of the workspace, uploaded
+    // here (synchronously, before any capture); the schedule lives after them
+    std::vector<DeviceTables> tab_store(plans.size());
+    std::vector<const DeviceTables*> tabs;
+    {
+      uint64_t o = 0;
+      cudaStream_t st = (cudaStream_t)stream;
+      for (size_t k = 0; k < plans.size(); ++k) {
+        if (o + table_bytes(plans[k]) > ws_bytes) return fail(QFX_ENOMEM, "qfx_batch_prepare: workspace smaller than the plans' tables");
+        qfx_status s = stage_tables(plans[k], (char*)workspace + o, stream, &tab_store[k]);
+        if (s != QFX_OK) return s;
+        tabs.push_back(&tab_store[k]);
+        o += table_bytes(plans[k]);
+      }
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "qfx_batch_prepare: plan tables");
+      workspace = (char*)workspace + o;
+      ws_bytes -= o;
+    }
+    std::map<const qfx_plan*, const DeviceTables*> tabmap;
+    for (size_t k = 0; k < plans.size(); ++k) tabmap[plans[k]] = tabs[k];
+    if (batch_has_tc(items, n_items))
+      return prepare_graph(items, n_items, {}, tabmap, workspace, ws_bytes, out, stream);
+    // FP32 plans: items whose steps fill the GPU many times over run as their own launch
+    // sequences inside one graph (their tiles run faster in the standalone kernels than
+    // inside the persistent one, and launch overhead is negligible at their size); the
+    // others run in one persistent launch, itself a node of that graph
+    std::vector<qfx_batch_item> big, small;
+    for (int i = 0; i < n_items; ++i) (item_is_big(items[i].plan) ? big : small).push_back(items[i]);
+    if (!big.empty())
+      return prepare_graph(big.data(), (int32_t)big.size(), small, tabmap, workspace, ws_bytes, out, stream);
+    return prepare_persistent(items, n_items, tabmap, workspace, ws_bytes, out, stream);
   } catch (const std::exception& ex) {
     return fail(QFX_EINVAL, std::string("qfx_batch_prepare: ") + ex.what());
   }

@@ -173,3 +173,33 @@ def test_fp32_items_in_a_split_precision_batch(qfx):
     qfx.sync()
     for o, w in zip(outs, want):
         np.testing.assert_array_equal(o.cpu().numpy(), w)
+
+
+def test_large_fp32_items_run_as_launches_beside_the_persistent_kernel(qfx):
+    """FP32 items whose steps have at least 512 output tiles (7x7x(1+24+1): 1024) run as
+    their own launch sequences in the batch's graph; the small items run in one persistent
+    launch recorded in the same graph.  Outputs equal per-item qfx_amplitudes bit for bit,
+    also when the batch is replayed from a caller's CUDA graph."""
+    items, _ = mixed_items(qfx)
+    c = ri.rqc(7, 7, 24, seed=7)
+    big = qfx.Plan(qfx.Circuit(c), n_open=5)
+    x1 = torch.tensor(ri.random_bitstrings(49, 2, seed=4).view(np.int64), device="cuda")
+    items = [items[0], (big, x1, 0, None)] + items[1:] + [(big, x1[1:], 0, None)]
+    want = per_item(qfx, items)
+    b = qfx.Batch(items, slots=3)
+    assert b.n_work == sum(x.numel() * p.n_slices for p, x, _, _ in items)
+    outs = b.run()
+    qfx.sync()
+    for o, w in zip(outs, want):
+        np.testing.assert_array_equal(o.cpu().numpy(), w)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(stream=s)
+    for o in b.outs:
+        o.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    qfx.sync()
+    for o, w in zip(b.outs, want):
+        np.testing.assert_array_equal(o.cpu().numpy(), w)
