@@ -132,7 +132,7 @@ typedef struct {
   const qfx_cut* forced_cuts;      /* cuts always applied (before any the cap needs) */
   int32_t n_forced_cuts;
   int32_t precision;               /* qfx_precision */
-  int32_t plan_family;             /* 0 = line sweep (the only family of this build) */
+  int32_t plan_family;             /* 0 = line sweep, 1 = contraction tree (FP32; see below) */
   int32_t tc_flags;                /* tensor-core options, QFX_TC_* bits; 0 = default */
   const char* autotune_cache;      /* JSON file written by qfx_autotune, or NULL */
   uint64_t adjoint_store_bytes;    /* qfx_amplitudes_backward keeps the output of every step
@@ -152,7 +152,15 @@ typedef struct {
 #define QFX_TC_REGISTER_ROWS 4
 
 /* Sec. III.D (contraction order and cuts), Sec. III.A (slices), Sec. III.B (x2), Eq. 1.
- * Host only: the plan sweeps the grid line by line (along the shorter grid dimension),
+ * Host only.  Plan family 1 (the region plans of Sec. III, Fig. 3): a contraction tree
+ * built greedily -- contract the connected pair whose result grows least over its larger
+ * operand -- with cuts chosen by halving, one at a time, the bond of the largest
+ * intermediate that lowers the largest intermediate most, until it fits the cap.  Each
+ * node is a TTGT step (permutes where the operands' shared legs are not in place, then the
+ * step GEMM below with P, Sd the larger operand's legs before and after the shared ones).
+ * It needs QFX_PREC_FP32_SIMT; qfx_amplitudes, qfx_amplitudes_static and batches run it
+ * (the adjoint and the autotune cache do not: QFX_EUNSUPPORTED, ignored).
+ * Plan family 0: the plan sweeps the grid line by line (along the shorter grid dimension),
  * absorbing one site per step so that every step is a strided batched complex GEMM
  * C[nh][p][nl][s] = sum_k S[k][nh*NL+nl] * B[p][k][s] with no tensor transpose; then it
  * adds cuts (greedily halving the bond that keeps the total work lowest) until the

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqfx.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["circuit.cpp", "plan.cpp", "runtime.cu", "fold.cu", "cgemm_simt.cu", "permute.cu",
+SOURCES = ["circuit.cpp", "plan.cpp", "plan_tree.cpp", "runtime.cu", "fold.cu", "cgemm_simt.cu", "permute.cu",
            "static_scratch.cu", "cgemm_tc.cu",
            "adjoint.cu", "batch.cu", "autotune.cu", "sampling.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -598,6 +598,8 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
                                       "(qfx_amplitudes_backward_full writes 16)");
   qfx_status s = check_amplitudes_args(p, x1, n_batch, slice_begin, slice_end, grad_out);
   if (s != QFX_OK) return s;
+  if (p->family != 0)
+    return fail(QFX_EUNSUPPORTED, "qfx_amplitudes_backward: line-sweep plans only (plan_family 0)");
   if (!grad_gates || !workspace) return fail(QFX_EINVAL, "qfx_amplitudes_backward: NULL argument");
   if (((uintptr_t)workspace & 255) || ((uintptr_t)grad_gates & 15))
     return fail(QFX_EINVAL, "qfx_amplitudes_backward: misaligned workspace or grad_gates");

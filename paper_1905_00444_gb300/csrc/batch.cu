@@ -329,6 +329,7 @@ using namespace qfx;
 // persistent kernel (measured: 48.2 against 41.6 TFLOP/s on the mixed-grid batch).
 constexpr int64_t kBigTiles = 512;
 bool item_is_big(const qfx_plan* p) {
+  if (p->family == 1) return true;   // contraction trees run through the launch path only
   int64_t most = 0;
   for (size_t i = 1; i < p->steps.size(); ++i) {
     const Step& sp = p->steps[i];

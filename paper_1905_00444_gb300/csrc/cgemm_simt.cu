@@ -66,10 +66,10 @@ int pick_variant(int64_t N, int64_t Sd) {
 
 int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
                 int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
-                int batch, int variant, int precision, void* stream) {
+                int batch, int variant, int precision, void* stream, int beta) {
   (void)precision;
   StepArgs a{(const float2*)S, s_stride, (const float2*)B, b_stride, (float2*)C, c_stride,
-             P, K, N, NL, Sd, P * Sd};
+             P, K, N, NL, Sd, P * Sd, beta};
   if (variant < 0) variant = pick_variant(N, Sd);
   if (variant < 5 && (Sd % 2)) return (int)cudaErrorInvalidValue;  // JMODE needs even Sd
   cudaStream_t st = (cudaStream_t)stream;

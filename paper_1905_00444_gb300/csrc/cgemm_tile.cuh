@@ -28,6 +28,7 @@ struct StepArgs {
   const float2* B; int64_t b_stride;
   float2* C; int64_t c_stride;
   int64_t P, K, N, NL, Sd, J;
+  int32_t beta;   // 1: add the product into C (a chunk of a long contraction), 0: write it
 };
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
@@ -186,10 +187,22 @@ __device__ __forceinline__ void cgemm_tile(const StepArgs& a, int64_t tile, int6
       const float2 v1 = make_float2(accr[i][2 * c + 1], acci[i][2 * c + 1]);
       float2* dst0 = C + nh * strideNH + p * (NL * Sd) + nl * Sd + s;
       if (!KMODE) {
-        *reinterpret_cast<float4*>(dst0) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        float4 w = make_float4(v0.x, v0.y, v1.x, v1.y);
+        if (a.beta) {
+          const float4 o = *reinterpret_cast<const float4*>(dst0);
+          w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
+        }
+        *reinterpret_cast<float4*>(dst0) = w;
       } else {
-        *dst0 = v0;
-        if (j + 1 < J) C[nh * strideNH + p1 * (NL * Sd) + nl * Sd + s1] = v1;
+        float2 w0 = v0;
+        if (a.beta) { w0.x += dst0->x; w0.y += dst0->y; }
+        *dst0 = w0;
+        if (j + 1 < J) {
+          float2* dst1 = C + nh * strideNH + p1 * (NL * Sd) + nl * Sd + s1;
+          float2 w1 = v1;
+          if (a.beta) { w1.x += dst1->x; w1.y += dst1->y; }
+          *dst1 = w1;
+        }
       }
     }
   }

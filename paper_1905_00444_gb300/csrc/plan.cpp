@@ -134,7 +134,10 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
   if (!c || !o || !out) return qfx::fail(QFX_EINVAL, "qfx_plan_create: NULL argument");
   *out = nullptr;
   try {
-    if (o->plan_family != 0) return qfx::fail(QFX_EUNSUPPORTED, "plan_family: only 0 (line sweep)");
+    if (o->plan_family != 0 && o->plan_family != 1)
+      return qfx::fail(QFX_EINVAL, "plan_family: 0 (line sweep) or 1 (contraction tree)");
+    if (o->plan_family == 1 && o->precision != QFX_PREC_FP32_SIMT)
+      return qfx::fail(QFX_EUNSUPPORTED, "contraction-tree plans run FP32 SIMT steps only");
     if (o->precision < QFX_PREC_FP32_SIMT || o->precision > QFX_PREC_C3M_BF16X2)
       return qfx::fail(QFX_EINVAL, "unknown precision");
     const int n = c->rows * c->cols;
@@ -235,15 +238,34 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       edim[e] = k.size;
     }
 
+    const bool tree = o->plan_family == 1;
+    p->family = tree ? 1 : 0;
+    // the tree family's site legs, in the fold's layout [up][left][x][right][down]
+    std::vector<std::vector<int>> site_legs(n);
+    for (int q = 0; q < n; ++q) {
+      auto add_edge = [&](int e) { if (e >= 0 && full[e] > 1) site_legs[q].push_back(e); };
+      add_edge(slots[q][0]);
+      add_edge(slots[q][1]);
+      if (is_open[q]) site_legs[q].push_back(-(1 + q));
+      add_edge(slots[q][2]);
+      add_edge(slots[q][3]);
+    }
     SimResult sim = simulate(geo, p->order, slots, edim, is_open);
     if (!sim.ok) return qfx::fail(QFX_EPLAN, "planner: " + sim.err);
     const uint64_t cap = o->max_intermediate_bytes;
+    if (tree) {
+      std::string terr;
+      if (!qfx::tree_cut_search(site_legs, E, edim, cut_edges, cap / 8, full, &terr))
+        return qfx::fail(QFX_EPLAN, terr);
+      sim = simulate(geo, p->order, slots, edim, is_open);   // intro order of the open sites
+      if (!sim.ok) return qfx::fail(QFX_EPLAN, "planner: " + sim.err);
+    }
     auto slices_of = [&](const std::vector<int64_t>& dims) {
       double s = 1;
       for (int e : cut_edges) s *= (double)full[e] / (double)dims[e];
       return s;
     };
-    while (cap > 0 && (uint64_t)sim.peak > cap / 8) {
+    while (!tree && cap > 0 && (uint64_t)sim.peak > cap / 8) {
       int best = -1;
       SimResult best_sim;
       double best_work = 0;
@@ -269,7 +291,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       if (std::find(cut_edges.begin(), cut_edges.end(), best) == cut_edges.end()) cut_edges.push_back(best);
       sim = best_sim;
     }
-    if (sim.peak > kMaxPlanElements)
+    if (!tree && sim.peak > kMaxPlanElements)
       return qfx::fail(QFX_EPLAN, "largest intermediate above 2^50 elements: cut bonds or set "
                                   "max_intermediate_bytes");
     for (int e = 0; e < E; ++e)
@@ -401,11 +423,61 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     // workspace layout
     qfx::Layout& L = p->layout;
     L.header_per_item = align256((uint64_t)n * 8);
-    L.buf0 = 0;
-    L.buf1 = align256((uint64_t)p->max_elements * 8);
-    L.sites = L.buf1 + align256((uint64_t)p->max_elements * 8);
-    L.simage = L.sites + align256((uint64_t)p->site_total * 8);
-    L.item_bytes = L.simage + align256(simage);
+    if (tree) {
+      // item block: the site tensors, then an arena for the tree's intermediates and the
+      // permuted copies of its operands
+      L.buf0 = L.buf1 = 0;
+      L.sites = 0;
+      const uint64_t arena = align256((uint64_t)p->site_total * 8);
+      std::vector<uint64_t> site_off(n);
+      for (int q = 0; q < n; ++q) site_off[q] = L.sites + (uint64_t)p->sites[q].offset * 8;
+      std::vector<int> root;
+      uint64_t arena_bytes = 0;
+      int64_t max_el = 1;
+      std::string terr;
+      if (!qfx::build_tree_nodes(site_legs, edim, site_off, arena, p->tree, &arena_bytes, &root,
+                                 &max_el, &terr))
+        return qfx::fail(QFX_EPLAN, terr);
+      if (max_el > kMaxPlanElements)
+        return qfx::fail(QFX_EPLAN, "largest intermediate above 2^50 elements: cut bonds or set "
+                                    "max_intermediate_bytes");
+      p->tree_final_off = p->tree.empty() ? site_off[0] : p->tree.back().offC;
+      // one reported step per tree node
+      p->steps.clear();
+      p->flops_per_item = 0;
+      p->bytes_per_item = 0;
+      p->largest_step = 0;
+      for (auto& nd : p->tree) {
+        nd.variant = qfx::pick_variant(nd.N, nd.Sd);
+        qfx::Step st{};
+        st.site = nd.out;
+        st.variant = nd.variant;
+        st.P = nd.P; st.K = nd.K; st.N = nd.N; st.NL = nd.NL; st.Sd = nd.Sd;
+        st.flops = nd.flops;
+        st.bytes = nd.bytes;
+        p->flops_per_item += nd.flops;
+        p->bytes_per_item += nd.bytes;
+        p->steps.push_back(st);
+        if (st.flops > p->steps[p->largest_step].flops) p->largest_step = (int)p->steps.size() - 1;
+      }
+      p->max_elements = max_el;
+      // output bit i -> bit of the root tensor's index (its last leg is the lowest bit)
+      p->open_perm.clear();
+      for (int q : p->open_sites) {
+        const auto it = std::find(root.begin(), root.end(), -(1 + q));
+        if (it == root.end()) return qfx::fail(QFX_EPLAN, "tree planner: open site missing from the result");
+        p->open_perm.push_back((int32_t)(root.size() - 1 - (it - root.begin())));
+      }
+      if (root.size() != p->open_sites.size()) return qfx::fail(QFX_EPLAN, "tree planner: bond left open");
+      L.simage = arena + arena_bytes;
+      L.item_bytes = L.simage;
+    } else {
+      L.buf0 = 0;
+      L.buf1 = align256((uint64_t)p->max_elements * 8);
+      L.sites = L.buf1 + align256((uint64_t)p->max_elements * 8);
+      L.simage = L.sites + align256((uint64_t)p->site_total * 8);
+      L.item_bytes = L.simage + align256(simage);
+    }
     qfx::build_table_image(p);
     *out = guard.release();
     return QFX_OK;

@@ -1,0 +1,374 @@
+// Contraction-tree plans ("region" plans, plan family 1).
+//
+// The line sweep absorbs one site per step, so every column's boundary is a separator of
+// the grid and a memory cap needs cut bits in every one of them (2^59 slices for
+// 7x7x(1+40+1) at 8 GiB).  Sec. III (Fig. 3) instead contracts regions into tensors of
+// bounded rank, combines the region tensors with few high-arithmetic-intensity
+// contractions and absorbs the rest site by site; the cuts (Sec. III.A) are chosen so that
+// every intermediate fits.  This planner builds such a tree greedily:
+//   - order: repeatedly contract the connected pair whose result grows least over its
+//     larger operand (log2 sizes; ties: the smaller result, then the lower tensor ids);
+//     when no pair shares a bond (everything cut apart) the two smallest tensors are
+//     multiplied;
+//   - cuts: while the largest intermediate exceeds the cap, halve the bond of the largest
+//     intermediates whose halving gives the lowest largest intermediate, then the least
+//     total work (slices x flops per slice), rebuilding the order for each trial.
+// Each tree node is one TTGT contraction (Sec. III.E) run by the same GEMM kernel as the
+// line sweep, C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] B[p][k][s] with NL = N: the larger
+// operand is B; when its shared legs are adjacent it is used in place (P = legs before,
+// Sd = legs after, the result keeps its leg order with the shared legs replaced by the
+// other operand's free legs); otherwise it is permuted to [shared][free] first.  The
+// smaller operand is permuted to [shared, in B's order][free] unless it already is.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <string>
+
+#include "qfx_internal.h"
+
+namespace qfx {
+namespace {
+
+constexpr int64_t kSatT = int64_t(1) << 62;
+int64_t tmul(int64_t a, int64_t b) { return a > kSatT / b ? kSatT : std::min(a * b, kSatT); }
+uint64_t a256t(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+struct Pair { int a, b; };
+
+}  // namespace
+
+// Greedy contraction order of the network given each site's legs and the leg dims.
+// Fills `pairs` (tensor ids; intermediates numbered from n in creation order) and returns
+// the largest tensor (elements, saturating) and the Eq. 1 flops of the tree.
+static void greedy_tree(const std::vector<std::vector<int>>& site_legs,
+                        const std::function<int64_t(int)>& dim, std::vector<Pair>& pairs,
+                        int64_t* peak, double* flops) {
+  const int n = (int)site_legs.size();
+  std::vector<std::vector<int>> legs(site_legs);
+  std::vector<double> lsz;   // log2 size per tensor
+  auto lsize = [&](const std::vector<int>& l) {
+    double s = 0;
+    for (int x : l) s += std::log2((double)dim(x));
+    return s;
+  };
+  for (auto& l : legs) lsz.push_back(lsize(l));
+  std::vector<int> alive(n);
+  for (int i = 0; i < n; ++i) alive[i] = i;
+  *peak = 1;
+  for (auto& l : legs) {
+    int64_t e = 1;
+    for (int x : l) e = tmul(e, dim(x));
+    *peak = std::max(*peak, e);
+  }
+  *flops = 0;
+  pairs.clear();
+  while (alive.size() > 1) {
+    int bi = -1, bj = -1;
+    double best = 0, best_out = 0;
+    for (size_t i = 0; i < alive.size(); ++i)
+      for (size_t j = i + 1; j < alive.size(); ++j) {
+        const auto& la = legs[alive[i]];
+        const auto& lb = legs[alive[j]];
+        double shared = 0;
+        bool conn = false;
+        for (int x : la)
+          if (std::find(lb.begin(), lb.end(), x) != lb.end()) {
+            conn = true;
+            shared += std::log2((double)dim(x));
+          }
+        if (!conn) continue;
+        const double out = lsz[alive[i]] + lsz[alive[j]] - 2 * shared;
+        const double score = out - std::max(lsz[alive[i]], lsz[alive[j]]);
+        if (bi < 0 || score < best - 1e-9 || (std::fabs(score - best) <= 1e-9 && out < best_out - 1e-9)) {
+          bi = (int)i; bj = (int)j; best = score; best_out = out;
+        }
+      }
+    if (bi < 0) {   // nothing shares a bond: multiply the two smallest
+      std::vector<int> idx(alive.size());
+      for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return lsz[alive[x]] < lsz[alive[y]]; });
+      bi = std::min(idx[0], idx[1]);
+      bj = std::max(idx[0], idx[1]);
+    }
+    const int ta = alive[bi], tb = alive[bj];
+    std::vector<int> out;
+    int64_t k = 1, ea = 1, eb = 1;
+    for (int x : legs[ta]) {
+      ea = tmul(ea, dim(x));
+      if (std::find(legs[tb].begin(), legs[tb].end(), x) != legs[tb].end()) k = tmul(k, dim(x));
+      else out.push_back(x);
+    }
+    for (int x : legs[tb]) {
+      eb = tmul(eb, dim(x));
+      if (std::find(legs[ta].begin(), legs[ta].end(), x) == legs[ta].end()) out.push_back(x);
+    }
+    int64_t eo = 1;
+    for (int x : out) eo = tmul(eo, dim(x));
+    *peak = std::max(*peak, eo);
+    *flops += 8.0 * (double)eo * (double)k;
+    pairs.push_back({ta, tb});
+    legs.push_back(out);
+    lsz.push_back(lsize(out));
+    alive.erase(alive.begin() + bj);
+    alive.erase(alive.begin() + bi);
+    alive.push_back((int)legs.size() - 1);
+  }
+}
+
+bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges,
+                     std::vector<int64_t>& edim, std::vector<int>& cut_edges, uint64_t cap_elems,
+                     const std::vector<int64_t>& full, std::string* err) {
+  auto dimf = [&](int x) -> int64_t { return x < 0 ? 2 : edim[x]; };
+  std::vector<Pair> pairs;
+  int64_t peak;
+  double flops;
+  greedy_tree(site_legs, dimf, pairs, &peak, &flops);
+  int guard = 0;
+  while (cap_elems > 0 && (uint64_t)peak > cap_elems) {
+    if (++guard > 400) { *err = "tree planner: no cut set found"; return false; }
+    // candidate bonds: those of the largest intermediates
+    std::vector<std::vector<int>> legs(site_legs);
+    std::vector<int> cand;
+    for (const auto& pr : pairs) {
+      std::vector<int> out;
+      for (int x : legs[pr.a])
+        if (std::find(legs[pr.b].begin(), legs[pr.b].end(), x) == legs[pr.b].end()) out.push_back(x);
+      for (int x : legs[pr.b])
+        if (std::find(legs[pr.a].begin(), legs[pr.a].end(), x) == legs[pr.a].end()) out.push_back(x);
+      int64_t e = 1;
+      for (int x : out) e = tmul(e, dimf(x));
+      if (e == peak)
+        for (int x : out)
+          if (x >= 0 && edim[x] >= 2 && std::find(cand.begin(), cand.end(), x) == cand.end()) cand.push_back(x);
+      legs.push_back(out);
+    }
+    for (const auto& l : site_legs) {   // a site tensor itself can be the largest
+      int64_t e = 1;
+      for (int x : l) e = tmul(e, dimf(x));
+      if (e == peak)
+        for (int x : l)
+          if (x >= 0 && edim[x] >= 2 && std::find(cand.begin(), cand.end(), x) == cand.end()) cand.push_back(x);
+    }
+    if (cand.empty()) { *err = "tree planner: the largest tensor has no bond left to cut"; return false; }
+    int best = -1;
+    int64_t best_peak = 0;
+    double best_work = 0;
+    for (int x : cand) {
+      edim[x] /= 2;
+      std::vector<Pair> pp;
+      int64_t pk;
+      double fl;
+      greedy_tree(site_legs, dimf, pp, &pk, &fl);
+      double slices = 1;
+      for (int e = 0; e < n_edges; ++e) slices *= (double)full[e] / (double)edim[e];
+      const double work = fl * slices;
+      if (best < 0 || pk < best_peak || (pk == best_peak && work < best_work)) {
+        best = x; best_peak = pk; best_work = work;
+      }
+      edim[x] *= 2;
+    }
+    edim[best] /= 2;
+    if (std::find(cut_edges.begin(), cut_edges.end(), best) == cut_edges.end()) cut_edges.push_back(best);
+    greedy_tree(site_legs, dimf, pairs, &peak, &flops);
+  }
+  return true;
+}
+
+// Leg orders, kernel shapes, permutes and the arena layout of the tree for the final dims.
+// Fuses a permute (input shape, out axis a = input axis ord[a]): axes of extent 1 are
+// dropped and output axes that are consecutive input axes in order are merged.  Returns
+// false when more than kTreeMaxRank axes remain.
+static bool fuse_perm(const std::vector<int64_t>& shape, const std::vector<int>& ord, int* rank,
+                      int64_t* fshape, int32_t* ford) {
+  std::vector<int> keep;                       // input axes of extent > 1, kept in output order
+  for (int a : ord)
+    if (shape[a] > 1) keep.push_back(a);
+  // runs of consecutive input axes in the output order
+  std::vector<std::pair<int, int>> runs;       // [first input axis, last input axis]
+  for (int a : keep) {
+    if (!runs.empty() && runs.back().second + 1 == a) {
+      // the next kept input axis after runs.back().second must be `a` (skip extent-1 axes)
+      runs.back().second = a;
+    } else {
+      runs.push_back({a, a});
+    }
+  }
+  // extent-1 input axes between fused ones do not matter; re-index the runs by input order
+  std::vector<int> firsts;
+  for (auto& r : runs) firsts.push_back(r.first);
+  std::vector<int> sorted = firsts;
+  std::sort(sorted.begin(), sorted.end());
+  const int R = (int)runs.size();
+  if (R > kTreeMaxRank) return false;
+  if (R == 0) { *rank = 1; fshape[0] = 1; ford[0] = 0; return true; }
+  for (int j = 0; j < R; ++j) {      // input shape of the fused tensor, in input order
+    const int i = (int)(std::find(firsts.begin(), firsts.end(), sorted[j]) - firsts.begin());
+    int64_t e = 1;
+    for (int a = runs[i].first; a <= runs[i].second; ++a) e *= shape[a];
+    fshape[j] = e;
+  }
+  for (int i = 0; i < R; ++i)        // output axis i is fused input axis rank-of(runs[i])
+    ford[i] = (int32_t)(std::find(sorted.begin(), sorted.end(), runs[i].first) - sorted.begin());
+  *rank = R;
+  return true;
+}
+
+bool build_tree_nodes(const std::vector<std::vector<int>>& site_legs, const std::vector<int64_t>& edim,
+                      const std::vector<uint64_t>& site_off, uint64_t arena_base,
+                      std::vector<TreeNode>& nodes, uint64_t* arena_bytes,
+                      std::vector<int>* root_legs, int64_t* max_el, std::string* err) {
+  auto dimf = [&](int x) -> int64_t { return x < 0 ? 2 : edim[x]; };
+  const int n = (int)site_legs.size();
+  std::vector<Pair> pairs;
+  int64_t peak;
+  double flops;
+  greedy_tree(site_legs, dimf, pairs, &peak, &flops);
+  *max_el = peak;
+  std::vector<std::vector<int>> legs(site_legs);
+  auto elems = [&](const std::vector<int>& l) {
+    int64_t e = 1;
+    for (int x : l) e = tmul(e, dimf(x));
+    return e;
+  };
+  // arena: first-fit over [offset, size) blocks
+  struct Blk { uint64_t off, size; };
+  std::vector<Blk> used;
+  uint64_t top = 0;
+  auto alloc = [&](uint64_t size) -> uint64_t {
+    size = a256t(std::max<uint64_t>(size, 256));
+    std::sort(used.begin(), used.end(), [](const Blk& x, const Blk& y) { return x.off < y.off; });
+    uint64_t cur = 0;
+    for (const auto& b : used) {
+      if (b.off >= cur + size) break;
+      cur = std::max(cur, b.off + b.size);
+    }
+    used.push_back({cur, size});
+    top = std::max(top, cur + size);
+    return cur;
+  };
+  auto release = [&](uint64_t off) {
+    for (size_t i = 0; i < used.size(); ++i)
+      if (used[i].off == off) { used.erase(used.begin() + i); return; }
+  };
+  std::vector<uint64_t> where(site_off);   // byte offset per tensor; sites: in the site region
+  std::vector<char> in_arena(n, 0);
+  nodes.clear();
+  for (const auto& pr : pairs) {
+    int ta = pr.a, tb = pr.b;
+    if (elems(legs[ta]) > elems(legs[tb])) std::swap(ta, tb);   // B is the larger operand
+    const auto& la = legs[ta];
+    const auto& lb = legs[tb];
+    std::vector<int> shared, afree, bpos;
+    for (size_t i = 0; i < lb.size(); ++i)
+      if (std::find(la.begin(), la.end(), lb[i]) != la.end()) { shared.push_back(lb[i]); bpos.push_back((int)i); }
+    for (int x : la)
+      if (std::find(lb.begin(), lb.end(), x) == lb.end()) afree.push_back(x);
+    TreeNode nd{};
+    nd.a = ta;
+    nd.b = tb;
+    // a chunked contraction needs B as [shared][free] (P = 1): its chunks are row ranges
+    const bool chunked = [&] {
+      int64_t k = 1;
+      for (int x : shared) k = tmul(k, dimf(x));
+      return k > kTreeChunk;
+    }();
+    const bool adjacent = shared.empty() ||
+                          (bpos.back() - bpos.front() + 1 == (int)bpos.size() && (!chunked || bpos.front() == 0));
+    std::vector<int> outl;
+    int64_t P = 1, Sd = 1;
+    if (adjacent) {
+      const int lo = shared.empty() ? 0 : bpos.front(), hi = shared.empty() ? 0 : bpos.back() + 1;
+      for (int i = 0; i < lo; ++i) { P = tmul(P, dimf(lb[i])); outl.push_back(lb[i]); }
+      for (int x : afree) outl.push_back(x);
+      for (int i = hi; i < (int)lb.size(); ++i) { Sd = tmul(Sd, dimf(lb[i])); outl.push_back(lb[i]); }
+      nd.permB = 0;
+    } else {
+      // B -> [shared][free]
+      std::vector<int> bord;   // new order as indices into lb
+      for (int p : bpos) bord.push_back(p);
+      for (int i = 0; i < (int)lb.size(); ++i)
+        if (std::find(bpos.begin(), bpos.end(), i) == bpos.end()) { bord.push_back(i); Sd = tmul(Sd, dimf(lb[i])); }
+      nd.permB = 1;
+      std::vector<int64_t> shp;
+      for (int x : lb) shp.push_back(dimf(x));
+      if (!fuse_perm(shp, bord, &nd.rankB, nd.shapeB, nd.ordB)) {
+        *err = "tree planner: a permute needs more than 10 fused axes";
+        return false;
+      }
+      for (int x : afree) outl.push_back(x);
+      for (int i = (int)shared.size(); i < (int)bord.size(); ++i) outl.push_back(lb[bord[i]]);
+    }
+    // A -> [shared in B's order][free in A's order]
+    std::vector<int> aord;
+    for (int x : shared) aord.push_back((int)(std::find(la.begin(), la.end(), x) - la.begin()));
+    for (int i = 0; i < (int)la.size(); ++i)
+      if (std::find(shared.begin(), shared.end(), la[i]) == shared.end()) aord.push_back(i);
+    bool ident = true;
+    for (int i = 0; i < (int)aord.size(); ++i) ident = ident && aord[i] == i;
+    nd.permA = 0;
+    if (!ident) {
+      std::vector<int64_t> shp;
+      for (int x : la) shp.push_back(dimf(x));
+      if (!fuse_perm(shp, aord, &nd.rankA, nd.shapeA, nd.ordA)) {
+        *err = "tree planner: a permute needs more than 10 fused axes";
+        return false;
+      }
+      bool fid = true;   // fused to the identity (only extent-1 axes moved)
+      for (int i = 0; i < nd.rankA; ++i) fid = fid && nd.ordA[i] == i;
+      nd.permA = fid ? 0 : 1;
+    }
+    int64_t K = 1, N = 1;
+    for (int x : shared) K = tmul(K, dimf(x));
+    for (int x : afree) N = tmul(N, dimf(x));
+    nd.P = P; nd.K = K; nd.N = N; nd.NL = N; nd.Sd = Sd;
+    nd.chunk = K;
+    if (K > kTreeChunk) {
+      if (P != 1 || K % kTreeChunk) { *err = "tree planner: a chunked contraction is not in [shared][free] form"; return false; }
+      nd.chunk = kTreeChunk;
+    }
+    nd.flops = 8.0 * (double)P * (double)K * (double)N * (double)Sd;
+    nd.bytes = 8.0 * ((double)P * K * Sd + (double)K * N + (double)P * N * Sd);
+    // memory: scratch copies, then the result; operands released afterwards
+    nd.offA = where[ta];
+    nd.offB = where[tb];
+    const uint64_t sa = nd.permA ? alloc((uint64_t)elems(la) * 8) : 0;
+    const uint64_t sb = nd.permB ? alloc((uint64_t)elems(lb) * 8) : 0;
+    const uint64_t oc = alloc((uint64_t)elems(outl) * 8);
+    nd.offA2 = nd.permA ? arena_base + sa : nd.offA;
+    nd.offB2 = nd.permB ? arena_base + sb : nd.offB;
+    nd.offC = arena_base + oc;
+    if (nd.permA) release(sa);
+    if (nd.permB) release(sb);
+    if (ta >= n && in_arena[ta]) release(where[ta] - arena_base);
+    if (tb >= n && in_arena[tb]) release(where[tb] - arena_base);
+    // every access of the node stays inside its tensors (checked here, before any launch)
+    const int64_t ea = elems(la), eb = elems(lb), ec = elems(outl);
+    if (tmul(K, N) != ea || tmul(tmul(P, K), Sd) != eb || tmul(tmul(P, N), Sd) != ec) {
+      *err = "tree planner: inconsistent step shape";
+      return false;
+    }
+    legs.push_back(outl);
+    where.push_back(arena_base + oc);
+    in_arena.push_back(1);
+    nd.out = (int)legs.size() - 1;
+    nodes.push_back(nd);
+  }
+  *arena_bytes = a256t(top);
+  // operand, scratch and result regions inside the site region or the arena
+  for (const auto& nd : nodes) {
+    const uint64_t end = arena_base + *arena_bytes;
+    const uint64_t ra = (uint64_t)tmul(nd.K, nd.N) * 8, rb = (uint64_t)tmul(tmul(nd.P, nd.K), nd.Sd) * 8;
+    const uint64_t rc = (uint64_t)tmul(tmul(nd.P, nd.N), nd.Sd) * 8;
+    if (nd.offA + ra > end || nd.offA2 + ra > end || nd.offB + rb > end || nd.offB2 + rb > end ||
+        nd.offC < arena_base || nd.offC + rc > end) {
+      *err = "tree planner: a tensor leaves the work item's block";
+      return false;
+    }
+  }
+  *root_legs = legs.back();
+  if (pairs.empty()) *root_legs = site_legs[0];
+  return true;
+}
+
+}  // namespace qfx

@@ -83,6 +83,28 @@ struct Step {
   double flops, bytes;
 };
 
+// One node of a contraction-tree plan (plan family 1): C = A * B over their shared legs as
+// the step kernel's C[nh][p][nl][s] = sum_k S[k][nh*NL+nl] B[p][k][s] (NL = N), with
+// optional permutes of A (to [shared][free]) and of B (to [shared][free]) first.  Offsets
+// are bytes within one work item's block; a permute's fused form has at most 10 axes.
+constexpr int kTreeMaxRank = 10;
+struct TreeNode {
+  int32_t a, b, out;                 // tensor ids (sites 0..n-1, then results in node order)
+  int32_t permA, permB;              // 1: permute the operand first
+  int32_t rankA, rankB;              // fused permute ranks
+  int64_t shapeA[kTreeMaxRank], shapeB[kTreeMaxRank];   // fused input shapes
+  int32_t ordA[kTreeMaxRank], ordB[kTreeMaxRank];       // out axis a = input axis ord[a]
+  int64_t P, K, N, NL, Sd;
+  double flops, bytes;
+  uint64_t offA, offB, offA2, offB2, offC;
+  int32_t variant;
+  int64_t chunk;                     // K > kTreeChunk: K is summed in chunks of this many
+};
+// Contractions longer than this run as chunks of this length, each added into the result:
+// an FP32 sum's rounding error grows with the square root of its length, and the tree's
+// pairwise contractions of large tensors reach K = 2^20.
+constexpr int64_t kTreeChunk = 1024;
+
 // Workspace layout:
 //   header: per concurrent item: maxabs[n_sites] (u32) + exps[n_sites] (i32), padded
 //   items : per concurrent item: buf0 (max_elements) | buf1 (max_elements) | sites
@@ -135,6 +157,9 @@ struct qfx_plan {
   double flops_per_item = 0, bytes_per_item = 0;
   int largest_step = 0;
   qfx::Layout layout{};
+  int family = 0;                 // 0 = line sweep, 1 = contraction tree (nodes below)
+  std::vector<qfx::TreeNode> tree;
+  uint64_t tree_final_off = 0;    // byte offset of the tree's result in an item block
   // host image of the tables (page-aligned, built once at creation), copied into the
   // caller's workspace by every compute call; page-locked on first use so that the copy
   // is asynchronous and can be recorded into a CUDA graph
@@ -167,7 +192,7 @@ int launch_accumulate(const DeviceTables& t, int n_sites, int n_open, int64_t n_
                       void* stream);
 int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
                 int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
-                int batch, int variant, int precision, void* stream);
+                int batch, int variant, int precision, void* stream, int beta = 0);
 int pick_variant(int64_t N, int64_t Sd);
 // tensor-core steps (variants 10 = BF16x3, 11 = TF32x3)
 constexpr int kVariantTcBf16 = 10, kVariantTcTf32 = 11, kVariantTcBf16x2 = 14;
@@ -208,6 +233,15 @@ qfx_status stage_tables(const qfx_plan* p, void* dst, void* stream, DeviceTables
 DeviceTables tables_at(void* base, const size_t offs[kTableRegions]);
 // fold-adjoint partial entries of one site (the adjoint's per-site partial offsets)
 int64_t adjoint_site_partials(const qfx_plan* p, const FoldSite& fs);
+
+// contraction-tree planning (plan_tree.cpp)
+bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges,
+                     std::vector<int64_t>& edim, std::vector<int>& cut_edges, uint64_t cap_elems,
+                     const std::vector<int64_t>& full, std::string* err);
+bool build_tree_nodes(const std::vector<std::vector<int>>& site_legs, const std::vector<int64_t>& edim,
+                      const std::vector<uint64_t>& site_off, uint64_t arena_base,
+                      std::vector<TreeNode>& nodes, uint64_t* arena_bytes,
+                      std::vector<int>* root_legs, int64_t* max_el, std::string* err);
 
 // the executor behind qfx_amplitudes (argument checks, items in flight, run)
 qfx_status check_amplitudes_args(const qfx_plan* p, const uint64_t* x1, int64_t n_batch,

@@ -188,9 +188,79 @@ int64_t items_in_flight(const qfx_plan* p, size_t ws_bytes) {
   return G;
 }
 
+// Contraction-tree plans: per group of items in flight, fold and scale their site
+// tensors, then run the tree's nodes in order -- each operand's permute (one launch per
+// item) and one batched GEMM launch over the items -- and add the root into `out`.
+static qfx_status exec_tree(const qfx_plan* p, const DeviceTables& t, const uint64_t* x1,
+                            int64_t n_batch, int64_t slice_begin, int64_t slice_end,
+                            void* workspace, int64_t G, double* out, void* stream) {
+  const Layout& L = p->layout;
+  const uint64_t hdr = L.header_per_item, ib = L.item_bytes;
+  const int64_t n_items = (slice_end - slice_begin) * n_batch;
+  G = std::min<int64_t>({G, n_items, 65535});
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n_open = (int)p->open_sites.size();
+  int64_t max_site = 1;
+  for (const auto& fs : p->sites) max_site = std::max(max_site, fs.size);
+  char* hdr_base = (char*)workspace;
+  char* items = hdr_base + align256((uint64_t)G * hdr);
+  cudaError_t e = cudaMemsetAsync(out, 0, (size_t)(n_batch << n_open) * 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes: clearing out");
+  for (int64_t item0 = 0; item0 < n_items; item0 += G) {
+    const int g = (int)std::min<int64_t>(G, n_items - item0);
+    e = cudaMemsetAsync(hdr_base, 0, (size_t)g * hdr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qfx_amplitudes: clearing header");
+    int slot;
+    profile_begin(st, &slot);
+    int err = launch_fold(t, p->n, max_site, (int)p->cut_dev.size(), x1, p->x1_words, n_batch,
+                          slice_begin, item0, g, hdr_base, hdr, items, ib, L.sites, st);
+    profile_end(st, slot, -1, 0, 1, 0.0, 0.0);
+    if (err) return cuda_fail(err, "fold kernel");
+    err = launch_scale(t, p->n, max_site, g, hdr_base, hdr, items, ib, L.sites, st);
+    if (err) return cuda_fail(err, "scale kernel");
+    for (size_t i = 0; i < p->tree.size(); ++i) {
+      const TreeNode& nd = p->tree[i];
+      for (int gi = 0; gi < g && (nd.permA || nd.permB); ++gi) {
+        char* blk = items + (uint64_t)gi * ib;
+        if (nd.permA) {
+          profile_begin(st, &slot);
+          err = launch_permute(blk + nd.offA, blk + nd.offA2, nd.rankA, nd.shapeA, nd.ordA, st);
+          double el = 1;
+          for (int a = 0; a < nd.rankA; ++a) el *= (double)nd.shapeA[a];
+          profile_end(st, slot, (int)i, 0, 4, 0.0, 16.0 * el);
+          if (err) return cuda_fail(err, "tree permute");
+        }
+        if (nd.permB) {
+          profile_begin(st, &slot);
+          err = launch_permute(blk + nd.offB, blk + nd.offB2, nd.rankB, nd.shapeB, nd.ordB, st);
+          double el = 1;
+          for (int a = 0; a < nd.rankB; ++a) el *= (double)nd.shapeB[a];
+          profile_end(st, slot, (int)i, 0, 4, 0.0, 16.0 * el);
+          if (err) return cuda_fail(err, "tree permute");
+        }
+      }
+      profile_begin(st, &slot);
+      // a long contraction in chunks of nd.chunk rows of S and B (P = 1), each added into C
+      for (int64_t k0 = 0; k0 < nd.K && !err; k0 += nd.chunk)
+        err = launch_step(items + nd.offA2 + (uint64_t)(k0 * nd.N) * 8, (int64_t)(ib / 8),
+                          items + nd.offB2 + (uint64_t)(k0 * nd.Sd) * 8, (int64_t)(ib / 8),
+                          items + nd.offC, (int64_t)(ib / 8), nd.P, nd.chunk, nd.N, nd.NL, nd.Sd, g,
+                          nd.variant, QFX_PREC_FP32_SIMT, st, k0 > 0 ? 1 : 0);
+      profile_end(st, slot, (int)i, nd.variant, 0, nd.flops * g, nd.bytes * g);
+      if (err) return cuda_fail(err, "contraction step kernel");
+    }
+    err = launch_accumulate(t, p->n, n_open, n_batch, item0, g, hdr_base, hdr, items, ib,
+                            p->tree_final_off, out, st);
+    if (err) return cuda_fail(err, "accumulate kernel");
+  }
+  return QFX_OK;
+}
+
 qfx_status exec_amplitudes(const qfx_plan* p, const DeviceTables& t, const uint64_t* x1,
                            int64_t n_batch, int64_t slice_begin, int64_t slice_end,
                            void* workspace, int64_t G, double* out, void* stream) {
+  if (p->family == 1)
+    return exec_tree(p, t, x1, n_batch, slice_begin, slice_end, workspace, G, out, stream);
   const Layout& L = p->layout;
   const uint64_t hdr = L.header_per_item, ib = L.item_bytes;
   const int64_t n_items = (slice_end - slice_begin) * n_batch;

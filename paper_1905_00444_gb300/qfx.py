@@ -188,7 +188,7 @@ class Plan:
                  n_open: int = 0, max_intermediate_bytes: int = 0,
                  cuts: Iterable = (), precision: str = "fp32", fast_accumulation: bool = False,
                  autotune_cache: Optional[str] = None, tensor_maps: bool = True,
-                 adjoint_store_bytes: int = 0):
+                 adjoint_store_bytes: int = 0, family: str = "line"):
         opts = PlanOpts()
         opts.max_intermediate_bytes = int(max_intermediate_bytes)
         self._open_arr = None
@@ -206,6 +206,7 @@ class Plan:
         opts.tc_flags = (1 if fast_accumulation else 0) | (0 if tensor_maps else 4)
         opts.autotune_cache = autotune_cache.encode() if autotune_cache else None
         opts.adjoint_store_bytes = int(adjoint_store_bytes)
+        opts.plan_family = {"line": 0, "tree": 1}[family]
         h = C.c_void_p()
         _check(lib.qfx_plan_create(circuit._h, C.byref(opts), C.byref(h)))
         self._h = h

@@ -417,3 +417,32 @@ def test_word_bitstring_helpers():
     for row in w:
         x = ri.words_to_int(row)
         assert x < 2 ** 121 and np.array_equal(ri.int_to_words(x, 121), row)
+
+
+def test_tree_plans_steps_cap_and_slices():
+    """Plan family 1: Eq. 1 per step, the cap met, an output order over the open sites, and
+    far fewer slices than the line sweep for the paper's 7x7x(1+40+1) at 8 GiB."""
+    c = qfx.Circuit(ri.rqc(7, 7, 40, seed=0))
+    tree = qfx.Plan(c, n_open=6, max_intermediate_bytes=8 << 30, family="tree")
+    line = qfx.Plan(c, n_open=6, max_intermediate_bytes=8 << 30)
+    assert tree.stats["max_elements"] * 8 <= 8 << 30
+    assert tree.n_slices <= 1 << 24 < (1 << 50) <= line.n_slices
+    total = 0.0
+    for s in tree.steps:
+        assert s["flops"] == 8.0 * s["P"] * s["K"] * s["N"] * s["Sd"]
+        total += s["flops"]
+    assert total == tree.stats["flops_per_item"]
+    assert tree.stats["n_steps"] == 48                # n - 1 pairwise contractions
+    assert tree.open_sites == line.open_sites
+    with pytest.raises(qfx.QfxError) as e:
+        qfx.Plan(c, n_open=6, max_intermediate_bytes=8 << 30, family="tree", precision="bf16x3")
+    assert e.value.status == q.QFX_EUNSUPPORTED
+
+
+def test_tree_plan_forced_cuts_keep_the_slice_numbering():
+    g = ri.rqc(7, 7, 32, seed=0)
+    cuts = [(r * 7 + c, (r + 1) * 7 + c, 1) for c in (0, 6) for r in range(6)]
+    tree = qfx.Plan(qfx.Circuit(g), n_open=6, cuts=cuts, family="tree")
+    line = qfx.Plan(qfx.Circuit(g), n_open=6, cuts=cuts)
+    assert tree.cuts == line.cuts == cuts and tree.n_slices == line.n_slices == 16 ** 12
+    assert tree.stats["flops_per_item"] < line.stats["flops_per_item"] / 10
