@@ -8,7 +8,7 @@ one x1 batch through the whole path: fold, scale, 48 contraction steps, FP64 sum
 Counted work is Eq. 1 (F = 8 sqrt(v0 v1 v2) per contraction), 2.256e14 flop per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qfx|reference]
-                  [--workload full|small|kstep|batch|batch_small|permute|adjoint|sample|wide]
+                  [--workload full|small|kstep|batch|batch_small|permute|adjoint|sample|wide|region]
 
 The default line also carries, each with its own clock record and roofline: every
 split-precision mode on the same workload (precision_modes), the adjoint at 6x6x(1+24+1)
@@ -18,7 +18,8 @@ BF16x3), the FP64 oracle on the host cores (cpu_baseline) and, last, a compact s
 all of them.  Workloads other than full/small print their own JSON line: kstep (the
 dominant step's kernel in one precision), batch / batch_small (the full 512-item mix or
 4096 small items), permute, adjoint, sample (fast sampling with frugal rejection, ideal
-and at a quarter of the paths), wide (slices of the 121-qubit 11x11x(1+24+1) shape).
+and at a quarter of the paths), wide (slices of the 121-qubit 11x11x(1+24+1) shape),
+region (slices of contraction-tree plans for 7x7x(1+40+1) and 8x8x(1+32+1)).
 
 Multi-GPU (torchrun): replicas -- each rank contracts its own x1 batches (no exchange on
 the data path); value is the sum over ranks, time the max over ranks ("weak" scaling).
@@ -953,6 +954,72 @@ def run_wide(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- region plans
+def run_region(args):
+    """Region (contraction-tree) plans for the paper's 7x7x(1+40+1) shape and for
+    8x8x(1+32+1), both at an 8 GiB cap on the largest intermediate, |x2| = 6: each timed
+    step contracts one seeded slice of one x1 batch (FP32), against the line sweep's slice
+    count and work at the same cap (planned only)."""
+    import torch
+    import paper_1905_00444_gb300 as qfx
+    dev = torch.device("cuda", 0)
+    res = {}
+    for rows, cols, depth in ((7, 7, 40), (8, 8, 32)):
+        circ = qfx.Circuit(ri.rqc(rows, cols, depth, seed=0))
+        t0 = time.perf_counter()
+        plan = qfx.Plan(circ, n_open=6, max_intermediate_bytes=8 << 30, family="tree")
+        plan_s = time.perf_counter() - t0
+        line = qfx.Plan(circ, n_open=6, max_intermediate_bytes=8 << 30)
+        x1 = torch.tensor(ri.random_bitstrings(rows * cols, 1, seed=2).view(np.int64), device=dev)
+        sids = [int(v) for v in np.random.default_rng(1).integers(0, plan.n_slices, args.warmup + args.steps)]
+        ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
+        out = torch.empty((1, 64), dtype=torch.complex128, device=dev)
+        for s in sids[:args.warmup]:
+            qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(0)
+        clocks.start()
+        qfx.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in sids[args.warmup:]:
+            qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        qfx.profile_enable(False)
+        recs = qfx.profile_collect()
+        clk = clocks.stop()
+        qfx.sync()
+        el = e0.elapsed_time(e1) / 1e3
+        flops = plan.stats["flops_per_item"]
+        kt = {}
+        for r in recs:
+            k = {0: "contraction_step", 1: "fold", 4: "permute"}.get(r["kind"], str(r["kind"]))
+            kt[k] = kt.get(k, 0.0) + r["ms"]
+        tot = sum(kt.values()) or 1.0
+        peak, _ = fp32_peak(torch, dev, clk.get("sm_max_mhz") or 2070.0)
+        big = plan.steps[plan.stats["largest_step"]]
+        dom = [r["ms"] for r in recs if r["kind"] == 0 and r["step"] == plan.stats["largest_step"]]
+        dom_tf = big["flops"] / (float(np.mean(dom)) / 1e3) / 1e12 if dom else float("nan")
+        res[f"{rows}x{cols}x(1+{depth}+1)"] = {
+            "value": flops * args.steps / el / 1e12, "unit": "TFLOP/s", "ms_per_slice": 1e3 * el / args.steps,
+            "slices": plan.n_slices, "flops_per_slice": flops, "flops_per_x1_batch": flops * plan.n_slices,
+            "max_intermediate_bytes": plan.stats["max_elements"] * 8, "workspace_bytes": plan.workspace_bytes(1),
+            "plan_s": plan_s, "cuts": len(plan.cuts),
+            "line_sweep_at_same_cap": {"slices": line.n_slices, "flops_per_slice": line.stats["flops_per_item"],
+                                       "flops_per_x1_batch": line.stats["flops_per_item"] * line.n_slices},
+            "kernel_share": {k: v / tot for k, v in kt.items()},
+            "roofline": {"bound": "alu", "kernel": f"largest step (P,K,N,Sd)=({big['P']},{big['K']},{big['N']},{big['Sd']})",
+                         "achieved": dom_tf, "peak": peak, "unit": "TFLOP/s", "frac": dom_tf / peak},
+            "clocks": clk}
+        del ws
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "region (contraction-tree) plans at an 8 GiB cap, |x2| = 6, FP32 SIMT, "
+                                  "one seeded slice per step", "metric": "contraction TFLOP/s", **res}),
+          flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- kernel case
 def run_kstep(args):
     """The dominant contraction step alone (K = N = 256 as in the 7x7x32 interior steps)
@@ -1010,7 +1077,7 @@ def main():
     ap.add_argument("--impl", default="qfx", choices=["qfx", "reference"])
     ap.add_argument("--workload", default="full",
                     choices=sorted(WORKLOADS) + ["kstep", "batch", "batch_small", "permute", "adjoint",
-                                                 "sample", "wide"])
+                                                 "sample", "wide", "region"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "bf16x2", "bf16x3_fast"],
@@ -1034,6 +1101,8 @@ def main():
         return run_sample(args)
     if args.workload == "wide":
         return run_wide(args)
+    if args.workload == "region":
+        return run_region(args)
     return run_qfx(args)
 
 

@@ -41,9 +41,9 @@ struct Pair { int a, b; };
 // Greedy contraction order of the network given each site's legs and the leg dims.
 // Fills `pairs` (tensor ids; intermediates numbered from n in creation order) and returns
 // the largest tensor (elements, saturating) and the Eq. 1 flops of the tree.
-static void greedy_tree(const std::vector<std::vector<int>>& site_legs,
-                        const std::function<int64_t(int)>& dim, std::vector<Pair>& pairs,
-                        int64_t* peak, double* flops) {
+static void greedy_tree_seed(const std::vector<std::vector<int>>& site_legs,
+                             const std::function<int64_t(int)>& dim, uint64_t seed,
+                             std::vector<Pair>& pairs, int64_t* peak, double* flops) {
   const int n = (int)site_legs.size();
   std::vector<std::vector<int>> legs(site_legs);
   std::vector<double> lsz;   // log2 size per tensor
@@ -79,7 +79,12 @@ static void greedy_tree(const std::vector<std::vector<int>>& site_legs,
           }
         if (!conn) continue;
         const double out = lsz[alive[i]] + lsz[alive[j]] - 2 * shared;
-        const double score = out - std::max(lsz[alive[i]], lsz[alive[j]]);
+        double score = out - std::max(lsz[alive[i]], lsz[alive[j]]);
+        if (seed) {   // a small deterministic perturbation: another tie-break per seed
+          uint64_t h = seed * 0x9E3779B97F4A7C15ull ^ ((uint64_t)alive[i] << 32 ^ (uint64_t)alive[j]);
+          h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 29;
+          score += 0.02 * (double)(h >> 11) / 9007199254740992.0;
+        }
         if (bi < 0 || score < best - 1e-9 || (std::fabs(score - best) <= 1e-9 && out < best_out - 1e-9)) {
           bi = (int)i; bj = (int)j; best = score; best_out = out;
         }
@@ -113,6 +118,22 @@ static void greedy_tree(const std::vector<std::vector<int>>& site_legs,
     alive.erase(alive.begin() + bj);
     alive.erase(alive.begin() + bi);
     alive.push_back((int)legs.size() - 1);
+  }
+}
+
+// The order used: the best, by largest tensor then flops, of the plain greedy order and
+// kTreeSeeds perturbed ones (deterministic).
+constexpr int kTreeSeeds = 8;
+static void greedy_tree(const std::vector<std::vector<int>>& site_legs,
+                        const std::function<int64_t(int)>& dim, std::vector<Pair>& pairs,
+                        int64_t* peak, double* flops) {
+  greedy_tree_seed(site_legs, dim, 0, pairs, peak, flops);
+  for (int sd = 1; sd <= kTreeSeeds; ++sd) {
+    std::vector<Pair> pp;
+    int64_t pk;
+    double fl;
+    greedy_tree_seed(site_legs, dim, (uint64_t)sd, pp, &pk, &fl);
+    if (pk < *peak || (pk == *peak && fl < *flops)) { pairs.swap(pp); *peak = pk; *flops = fl; }
   }
 }
 
