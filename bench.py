@@ -958,63 +958,71 @@ def run_wide(args):
 def run_region(args):
     """Region (contraction-tree) plans for the paper's 7x7x(1+40+1) shape and for
     8x8x(1+32+1), both at an 8 GiB cap on the largest intermediate, |x2| = 6: each timed
-    step contracts one seeded slice of one x1 batch (FP32), against the line sweep's slice
-    count and work at the same cap (planned only)."""
+    step contracts one seeded slice of one x1 batch, in FP32 and in BF16x3, against the line
+    sweep's slice count and work at the same cap (planned only)."""
     import torch
     import paper_1905_00444_gb300 as qfx
     dev = torch.device("cuda", 0)
     res = {}
     for rows, cols, depth in ((7, 7, 40), (8, 8, 32)):
         circ = qfx.Circuit(ri.rqc(rows, cols, depth, seed=0))
-        t0 = time.perf_counter()
-        plan = qfx.Plan(circ, n_open=6, max_intermediate_bytes=8 << 30, family="tree")
-        plan_s = time.perf_counter() - t0
         line = qfx.Plan(circ, n_open=6, max_intermediate_bytes=8 << 30)
         x1 = torch.tensor(ri.random_bitstrings(rows * cols, 1, seed=2).view(np.int64), device=dev)
-        sids = [int(v) for v in np.random.default_rng(1).integers(0, plan.n_slices, args.warmup + args.steps)]
-        ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
-        out = torch.empty((1, 64), dtype=torch.complex128, device=dev)
-        for s in sids[:args.warmup]:
-            qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
-        torch.cuda.synchronize(dev)
-        clocks = ClockSampler(0)
-        clocks.start()
-        qfx.profile_enable(True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for s in sids[args.warmup:]:
-            qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        qfx.profile_enable(False)
-        recs = qfx.profile_collect()
-        clk = clocks.stop()
-        qfx.sync()
-        el = e0.elapsed_time(e1) / 1e3
-        flops = plan.stats["flops_per_item"]
-        kt = {}
-        for r in recs:
-            k = {0: "contraction_step", 1: "fold", 4: "permute"}.get(r["kind"], str(r["kind"]))
-            kt[k] = kt.get(k, 0.0) + r["ms"]
-        tot = sum(kt.values()) or 1.0
-        peak, _ = fp32_peak(torch, dev, clk.get("sm_max_mhz") or 2070.0)
-        big = plan.steps[plan.stats["largest_step"]]
-        dom = [r["ms"] for r in recs if r["kind"] == 0 and r["step"] == plan.stats["largest_step"]]
-        dom_tf = big["flops"] / (float(np.mean(dom)) / 1e3) / 1e12 if dom else float("nan")
-        res[f"{rows}x{cols}x(1+{depth}+1)"] = {
-            "value": flops * args.steps / el / 1e12, "unit": "TFLOP/s", "ms_per_slice": 1e3 * el / args.steps,
-            "slices": plan.n_slices, "flops_per_slice": flops, "flops_per_x1_batch": flops * plan.n_slices,
-            "max_intermediate_bytes": plan.stats["max_elements"] * 8, "workspace_bytes": plan.workspace_bytes(1),
-            "plan_s": plan_s, "cuts": len(plan.cuts),
-            "line_sweep_at_same_cap": {"slices": line.n_slices, "flops_per_slice": line.stats["flops_per_item"],
-                                       "flops_per_x1_batch": line.stats["flops_per_item"] * line.n_slices},
-            "kernel_share": {k: v / tot for k, v in kt.items()},
-            "roofline": {"bound": "alu", "kernel": f"largest step (P,K,N,Sd)=({big['P']},{big['K']},{big['N']},{big['Sd']})",
-                         "achieved": dom_tf, "peak": peak, "unit": "TFLOP/s", "frac": dom_tf / peak},
-            "clocks": clk}
-        del ws
-        torch.cuda.empty_cache()
-    print(json.dumps({"workload": "region (contraction-tree) plans at an 8 GiB cap, |x2| = 6, FP32 SIMT, "
+        entry = {}
+        for prec in ("fp32", "bf16x3"):
+            t0 = time.perf_counter()
+            plan = qfx.Plan(circ, n_open=6, max_intermediate_bytes=8 << 30, family="tree", precision=prec)
+            plan_s = time.perf_counter() - t0
+            sids = [int(v) for v in np.random.default_rng(1).integers(0, plan.n_slices, args.warmup + args.steps)]
+            ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
+            out = torch.empty((1, 64), dtype=torch.complex128, device=dev)
+            for s in sids[:args.warmup]:
+                qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
+            torch.cuda.synchronize(dev)
+            clocks = ClockSampler(0)
+            clocks.start()
+            qfx.profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for s in sids[args.warmup:]:
+                qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            qfx.profile_enable(False)
+            recs = qfx.profile_collect()
+            clk = clocks.stop()
+            qfx.sync()
+            el = e0.elapsed_time(e1) / 1e3
+            flops = plan.stats["flops_per_item"]
+            kt = {}
+            for r in recs:
+                k = {0: "contraction_step", 1: "fold", 4: "permute"}.get(r["kind"], str(r["kind"]))
+                kt[k] = kt.get(k, 0.0) + r["ms"]
+            tot = sum(kt.values()) or 1.0
+            big = plan.steps[plan.stats["largest_step"]]
+            dom = [r["ms"] for r in recs if r["kind"] == 0 and r["step"] == plan.stats["largest_step"]]
+            dom_tf = big["flops"] / (float(np.mean(dom)) / 1e3) / 1e12 if dom else float("nan")
+            if prec == "fp32":
+                peak, _ = fp32_peak(torch, dev, clk.get("sm_max_mhz") or 2070.0)
+                roof = {"bound": "alu", "achieved": dom_tf, "peak": peak, "unit": "TFLOP/s", "frac": dom_tf / peak}
+            else:
+                probe = qfx.tensor_peak("bf16x3", 1 << 16)
+                ach = dom_tf * TENSOR_FACTOR["bf16x3"]
+                roof = {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                        "tensor_probe": {"tflops": probe, "frac": ach / probe}}
+            roof["kernel"] = f"largest node (P,K,N,Sd)=({big['P']},{big['K']},{big['N']},{big['Sd']})"
+            entry[prec] = {
+                "value": flops * args.steps / el / 1e12, "unit": "TFLOP/s", "ms_per_slice": 1e3 * el / args.steps,
+                "slices": plan.n_slices, "flops_per_slice": flops, "flops_per_x1_batch": flops * plan.n_slices,
+                "max_intermediate_bytes": plan.stats["max_elements"] * 8, "workspace_bytes": plan.workspace_bytes(1),
+                "plan_s": plan_s, "cuts": len(plan.cuts), "kernel_share": {k: v / tot for k, v in kt.items()},
+                "roofline": roof, "clocks": clk}
+            del ws
+            torch.cuda.empty_cache()
+        entry["line_sweep_at_same_cap"] = {"slices": line.n_slices, "flops_per_slice": line.stats["flops_per_item"],
+                                           "flops_per_x1_batch": line.stats["flops_per_item"] * line.n_slices}
+        res[f"{rows}x{cols}x(1+{depth}+1)"] = entry
+    print(json.dumps({"workload": "region (contraction-tree) plans at an 8 GiB cap, |x2| = 6, "
                                   "one seeded slice per step", "metric": "contraction TFLOP/s", **res}),
           flush=True)
     return 0

@@ -158,8 +158,10 @@ typedef struct {
  * intermediate that lowers the largest intermediate most, until it fits the cap.  Each
  * node is a TTGT step (permutes where the operands' shared legs are not in place, then the
  * step GEMM below with P, Sd the larger operand's legs before and after the shared ones).
- * It needs QFX_PREC_FP32_SIMT; qfx_amplitudes, qfx_amplitudes_static and batches run it
- * (the adjoint and the autotune cache do not: QFX_EUNSUPPORTED, ignored).
+ * Contractions longer than 1024 are summed in chunks of 1024, each added into the result.
+ * Split precisions run every node the tensor-core tiles take on them (as for the line
+ * sweep).  qfx_amplitudes, qfx_amplitudes_static and batches run tree plans (the adjoint
+ * and the autotune cache do not: QFX_EUNSUPPORTED, ignored).
  * Plan family 0: the plan sweeps the grid line by line (along the shorter grid dimension),
  * absorbing one site per step so that every step is a strided batched complex GEMM
  * C[nh][p][nl][s] = sum_k S[k][nh*NL+nl] * B[p][k][s] with no tensor transpose; then it

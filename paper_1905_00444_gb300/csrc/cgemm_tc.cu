@@ -218,6 +218,7 @@ struct TcArgs {
   int withhold_s;    // test hook: never stream S, so the bounded waits expire
   int use_tma;       // producers read FP32 rows staged by tensor-map copies (default tiles)
   int box_s, box_p;  // tensor-map box: box_s consecutive s (columns), box_p values of p
+  int beta;          // 1: add the product into C (a chunk of a long contraction)
 };
 
 // Persistent CTA, one per SM.  TMEM columns: with SPLITACC the hh-term products go to
@@ -536,7 +537,9 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
           float2* dst = Cg + (int64_t)(n0 / NL) * strideNH + (int64_t)nl * a.Sd + jofs;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            *dst = make_float2(vr[i], vi[i]);
+            float2 w = make_float2(vr[i], vi[i]);
+            if (a.beta) { const float2 o = *dst; w.x += o.x; w.y += o.y; }
+            *dst = w;
             dst += a.Sd;
             if (++nl == NL) { nl = 0; dst += strideNH - (int64_t)NL * a.Sd; }
           }
@@ -648,7 +651,7 @@ int ensure_tc_attr() {
 template <int MODE, bool SPLITACC>
 int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
                    int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
-                   int batch, char* scratch, int64_t scratch_stride, int withhold, bool no_tma,
+                   int batch, char* scratch, int64_t scratch_stride, int withhold, bool no_tma, int beta,
                    cudaStream_t st) {
   using M_ = Mode<MODE>;
   using CF = TcCfg<MODE, SPLITACC>;
@@ -670,6 +673,7 @@ int launch_tc_mode(const void* S, int64_t s_stride, const void* B, int64_t b_str
   a.JT = (a.J + kRows - 1) / kRows;
   a.tiles = (int64_t)batch * a.JT * a.NHt;
   a.withhold_s = withhold;
+  a.beta = beta;
   alignas(64) CUtensorMap tmA;
   std::memset(&tmA, 0, sizeof(tmA));
   a.use_tma = 0;
@@ -816,24 +820,25 @@ int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_str
                    int batch, int precision, char* scratch, int64_t scratch_stride, void* stream,
                    int flags) {
   cudaStream_t st = (cudaStream_t)stream;
+  const int beta = (flags & kTcBeta) ? 1 : 0;
   const bool fast = (flags & kTcFast) != 0;
   const int withhold = (flags & kTcWithhold) ? 1 : 0;
   const bool no_tma = (flags & kTcNoTma) != 0;
   if (precision == QFX_PREC_C3M_BF16X3)
     return fast ? launch_tc_mode<QFX_PREC_C3M_BF16X3, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, st)
+                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, beta, st)
                 : launch_tc_mode<QFX_PREC_C3M_BF16X3, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, st);
+                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, beta, st);
   if (precision == QFX_PREC_C3M_BF16X2)
     return fast ? launch_tc_mode<QFX_PREC_C3M_BF16X2, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, st)
+                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, beta, st)
                 : launch_tc_mode<QFX_PREC_C3M_BF16X2, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, st);
+                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, beta, st);
   if (precision == QFX_PREC_C3M_TF32X3)
     return fast ? launch_tc_mode<QFX_PREC_C3M_TF32X3, false>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, st)
+                                                             Sd, batch, scratch, scratch_stride, withhold, no_tma, beta, st)
                 : launch_tc_mode<QFX_PREC_C3M_TF32X3, true>(S, s_stride, B, b_stride, C, c_stride, P, K, N, NL,
-                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, st);
+                                                            Sd, batch, scratch, scratch_stride, withhold, no_tma, beta, st);
   return (int)cudaErrorInvalidValue;
 }
 

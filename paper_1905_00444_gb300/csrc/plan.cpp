@@ -136,8 +136,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
   try {
     if (o->plan_family != 0 && o->plan_family != 1)
       return qfx::fail(QFX_EINVAL, "plan_family: 0 (line sweep) or 1 (contraction tree)");
-    if (o->plan_family == 1 && o->precision != QFX_PREC_FP32_SIMT)
-      return qfx::fail(QFX_EUNSUPPORTED, "contraction-tree plans run FP32 SIMT steps only");
+
     if (o->precision < QFX_PREC_FP32_SIMT || o->precision > QFX_PREC_C3M_BF16X2)
       return qfx::fail(QFX_EINVAL, "unknown precision");
     const int n = c->rows * c->cols;
@@ -447,8 +446,15 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       p->flops_per_item = 0;
       p->bytes_per_item = 0;
       p->largest_step = 0;
+      uint64_t tc_scratch = 0;
       for (auto& nd : p->tree) {
         nd.variant = qfx::pick_variant(nd.N, nd.Sd);
+        // split-precision plans run every node the tensor-core tiles take (N >= 32, as for
+        // the line sweep) on them, chunk by chunk
+        if (nd.N >= 32 && qfx::tc_eligible(p->precision, nd.chunk, nd.N, nd.P * nd.Sd, p->tc_flags)) {
+          nd.variant = qfx::tc_variant_of(p->precision);
+          tc_scratch = std::max(tc_scratch, qfx::tc_scratch_bytes(p->precision, nd.chunk, nd.N));
+        }
         qfx::Step st{};
         st.site = nd.out;
         st.variant = nd.variant;
@@ -470,7 +476,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       }
       if (root.size() != p->open_sites.size()) return qfx::fail(QFX_EPLAN, "tree planner: bond left open");
       L.simage = arena + arena_bytes;
-      L.item_bytes = L.simage;
+      L.item_bytes = L.simage + align256(tc_scratch);
     } else {
       L.buf0 = 0;
       L.buf1 = align256((uint64_t)p->max_elements * 8);

@@ -199,6 +199,7 @@ constexpr int kVariantTcBf16 = 10, kVariantTcTf32 = 11, kVariantTcBf16x2 = 14;
 constexpr int kTcFast = 1;       // QFX_TC_FAST_ACCUMULATION
 constexpr int kTcWithhold = 2;   // test hook: S stream withheld
 constexpr int kTcNoTma = 4;      // QFX_TC_REGISTER_ROWS
+constexpr int kTcBeta = 8;       // add the product into C instead of writing it
 bool tc_eligible(int precision, int64_t K, int64_t N, int64_t J, int flags);
 uint64_t tc_scratch_bytes(int precision, int64_t K, int64_t N);
 int launch_step_tc(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,

@@ -241,11 +241,18 @@ static qfx_status exec_tree(const qfx_plan* p, const DeviceTables& t, const uint
       }
       profile_begin(st, &slot);
       // a long contraction in chunks of nd.chunk rows of S and B (P = 1), each added into C
-      for (int64_t k0 = 0; k0 < nd.K && !err; k0 += nd.chunk)
-        err = launch_step(items + nd.offA2 + (uint64_t)(k0 * nd.N) * 8, (int64_t)(ib / 8),
-                          items + nd.offB2 + (uint64_t)(k0 * nd.Sd) * 8, (int64_t)(ib / 8),
-                          items + nd.offC, (int64_t)(ib / 8), nd.P, nd.chunk, nd.N, nd.NL, nd.Sd, g,
-                          nd.variant, QFX_PREC_FP32_SIMT, st, k0 > 0 ? 1 : 0);
+      for (int64_t k0 = 0; k0 < nd.K && !err; k0 += nd.chunk) {
+        const char* Sk = items + nd.offA2 + (uint64_t)(k0 * nd.N) * 8;
+        const char* Bk = items + nd.offB2 + (uint64_t)(k0 * nd.Sd) * 8;
+        if (nd.variant >= kVariantTcBf16)
+          err = launch_step_tc(Sk, (int64_t)(ib / 8), Bk, (int64_t)(ib / 8), items + nd.offC,
+                               (int64_t)(ib / 8), nd.P, nd.chunk, nd.N, nd.NL, nd.Sd, g, p->precision,
+                               items + L.simage, (int64_t)ib, st, p->tc_flags | (k0 > 0 ? kTcBeta : 0));
+        else
+          err = launch_step(Sk, (int64_t)(ib / 8), Bk, (int64_t)(ib / 8), items + nd.offC,
+                            (int64_t)(ib / 8), nd.P, nd.chunk, nd.N, nd.NL, nd.Sd, g, nd.variant,
+                            QFX_PREC_FP32_SIMT, st, k0 > 0 ? 1 : 0);
+      }
       profile_end(st, slot, (int)i, nd.variant, 0, nd.flops * g, nd.bytes * g);
       if (err) return cuda_fail(err, "contraction step kernel");
     }

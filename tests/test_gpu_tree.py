@@ -10,6 +10,8 @@ tree of TTGT steps with greedy cuts, run by the permute and step kernels.
 * 7x7x(1+40+1), the paper's own shape, at an 8 GiB cap (2^20 slices instead of the line
   sweep's 2^59): a slice against its refinement (two finer slices sum to it).
 * The tree plan inside a batch and through the allocation-free entry point.
+* Split precisions: tensor-core nodes (chunked contractions added into the result) against
+  the oracle on small grids and against the stored 7x7x32 slices, within the modes' bounds.
 """
 import json
 import os
@@ -197,3 +199,36 @@ def test_tree_plan_in_a_batch_and_the_static_entry(qfx):
     st = qfx.amplitudes_static(t2, x3).cpu().numpy()
     qfx.sync()
     np.testing.assert_array_equal(st, qfx.amplitudes(t2, x3).cpu().numpy())
+
+
+BOUND = {"bf16x3": 1e-5, "tf32x3": 3e-5}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_split_precision_tree_plans_vs_oracle(qfx, prec):
+    c = ri.rqc(6, 6, 24, seed=4)
+    plan = qfx.Plan(qfx.Circuit(c), n_open=6, family="tree", precision=prec)
+    assert any(s["variant"] >= 10 for s in plan.steps)
+    x1s = ri.random_bitstrings(36, 2, seed=7)
+    out = run(qfx, plan, x1s, items=2)
+    want = np.array([network.amplitudes_open(c, int(x), plan.open_sites) for x in x1s])
+    check(out, want, 36, rel=BOUND[prec])
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_split_precision_tree_plan_on_the_stored_7x7x32_slices(qfx, prec):
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    c = ri.rqc(7, 7, 32, seed=0)
+    plan = qfx.Plan(qfx.Circuit(c), n_open=6, cuts=[tuple(x) for x in g["cuts"]], family="tree",
+                    precision=prec)
+    assert any(s["variant"] >= 10 and s["K"] > 1024 for s in plan.steps)   # chunked tensor-core nodes
+    top = max(s["norm"] for s in g["slices"])
+    for s in g["slices"]:
+        if s["norm"] < 1e-9 * top:
+            continue
+        sid = int(s["slice"])
+        want = np.array(s["re"]) + 1j * np.array(s["im"])
+        got = run(qfx, plan, [int(g["x1"])], slices=(sid, sid + 1))[0]
+        rms = np.linalg.norm(want) / np.sqrt(want.size)
+        assert np.all(np.abs(got - want) <= BOUND[prec] * np.maximum(np.abs(want), rms)), sid
