@@ -905,8 +905,9 @@ def run_wide(args):
     x1 = torch.tensor(words.view(np.int64), device=dev)
     peaks, src = measured_peaks()
     res = {}
-    for prec in ("fp32", "bf16x3"):
-        plan = qfx.Plan(circ, n_open=6, max_intermediate_bytes=64 << 30, precision=prec)
+    for fam, cap, prec in (("line", 64 << 30, "fp32"), ("line", 64 << 30, "bf16x3"),
+                           ("tree", 32 << 30, "fp32"), ("tree", 32 << 30, "bf16x3")):
+        plan = qfx.Plan(circ, n_open=6, max_intermediate_bytes=cap, precision=prec, family=fam)
         plan.upload()
         sids = [int(v) for v in np.random.default_rng(3).integers(0, plan.n_slices, args.warmup + args.steps)]
         ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
@@ -941,16 +942,17 @@ def run_wide(args):
             roof = {"bound": "tensor", "achieved": counted * TENSOR_FACTOR["bf16x3"], "unit": "TFLOP/s",
                     "peak": peaks["bf16_tflops"], "frac_of_burst": counted * TENSOR_FACTOR["bf16x3"] / peaks["bf16_tflops"],
                     "tensor_probe": {"tflops": probe, "frac": counted * TENSOR_FACTOR["bf16x3"] / probe}}
-        res[prec] = {"value": flops * args.steps / el / 1e12, "unit": "TFLOP/s",
-                     "ms_per_slice": 1e3 * el / args.steps, "slices": args.steps,
+        res[f"{fam}_{prec}"] = {"value": flops * args.steps / el / 1e12, "unit": "TFLOP/s",
+                     "ms_per_slice": 1e3 * el / args.steps, "timed_slices": args.steps,
+                     "slices": plan.n_slices, "flops_per_slice": flops, "cap_bytes": cap,
+                     "seconds_per_x1_batch": plan.n_slices * el / args.steps,
                      "dominant_step": f"(P,K,N,Sd)=({big['P']},{big['K']},{big['N']},{big['Sd']})",
                      "roofline": roof, "clocks": clk}
         del ws
         torch.cuda.empty_cache()
-    print(json.dumps({"workload": "11x11x(1+24+1) RQC seed 0 (121 qubits), |x2| = 6, 64 GiB cap: "
-                                  f"{plan.n_slices} slices of {plan.stats['flops_per_item']:.3g} flop; "
-                                  "one seeded slice per step", "metric": "contraction TFLOP/s",
-                      **res}), flush=True)
+    print(json.dumps({"workload": "11x11x(1+24+1) RQC seed 0 (121 qubits), |x2| = 6: line sweep at a "
+                                  "64 GiB cap and tree plan at a 32 GiB cap; one seeded slice per step",
+                      "metric": "contraction TFLOP/s", **res}), flush=True)
     return 0
 
 
@@ -1011,8 +1013,12 @@ def run_region(args):
                 roof = {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
                         "tensor_probe": {"tflops": probe, "frac": ach / probe}}
             roof["kernel"] = f"largest node (P,K,N,Sd)=({big['P']},{big['K']},{big['N']},{big['Sd']})"
+            spl = el / args.steps
+            f_paper = 0.006          # the paper's fidelity for this shape (Sec. V, Table I)
             entry[prec] = {
-                "value": flops * args.steps / el / 1e12, "unit": "TFLOP/s", "ms_per_slice": 1e3 * el / args.steps,
+                "value": flops * args.steps / el / 1e12, "unit": "TFLOP/s", "ms_per_slice": 1e3 * spl,
+                "amplitudes_per_s_at_fidelity_0.006": 64.0 / (max(1, round(f_paper * plan.n_slices)) * spl),
+                "amplitudes_per_s_full": 64.0 / (plan.n_slices * spl),
                 "slices": plan.n_slices, "flops_per_slice": flops, "flops_per_x1_batch": flops * plan.n_slices,
                 "max_intermediate_bytes": plan.stats["max_elements"] * 8, "workspace_bytes": plan.workspace_bytes(1),
                 "plan_s": plan_s, "cuts": len(plan.cuts), "kernel_share": {k: v / tot for k, v in kt.items()},

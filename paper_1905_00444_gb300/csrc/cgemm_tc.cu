@@ -535,13 +535,21 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
           const int n0 = (int)nh * a.Nt + c0, NL = (int)a.NL;
           int nl = n0 % NL;
           float2* dst = Cg + (int64_t)(n0 / NL) * strideNH + (int64_t)nl * a.Sd + jofs;
+          if (!a.beta) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            float2 w = make_float2(vr[i], vi[i]);
-            if (a.beta) { const float2 o = *dst; w.x += o.x; w.y += o.y; }
-            *dst = w;
-            dst += a.Sd;
-            if (++nl == NL) { nl = 0; dst += strideNH - (int64_t)NL * a.Sd; }
+            for (int i = 0; i < 16; ++i) {
+              *dst = make_float2(vr[i], vi[i]);
+              dst += a.Sd;
+              if (++nl == NL) { nl = 0; dst += strideNH - (int64_t)NL * a.Sd; }
+            }
+          } else {   // a chunk of a long contraction: add into C
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float2 o = *dst;
+              *dst = make_float2(vr[i] + o.x, vi[i] + o.y);
+              dst += a.Sd;
+              if (++nl == NL) { nl = 0; dst += strideNH - (int64_t)NL * a.Sd; }
+            }
           }
         }
       }
