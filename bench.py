@@ -408,7 +408,7 @@ def summarize(line):
     if "adjoint" in line:
         a = line["adjoint"]
         s["adjoint"] = {"fwd_ms": _r(a["forward_ms"]), "bwd_ms": _r(a["backward_ms"]),
-                        "bwd_frac": _r(a["roofline"]["frac"])}
+                        "bwd_frac": _r(a["roofline"]["frac"]), "graph_ms": _r(a["graph_forward_backward_ms"])}
     if "permute" in line:
         s["permute_frac"] = [_r(c["frac"], 2) for c in line["permute"]["cases"]]
     if "batch" in line:
@@ -524,6 +524,27 @@ def measure_adjoint(qfx, torch, steps, warmup):
         b_ms.append(ev[1].elapsed_time(ev[2]))
     clk = clocks.stop()
     qfx.sync()
+    # the same forward + backward replayed from one CUDA graph (no launch gaps)
+    gs = torch.cuda.Stream()
+    with torch.cuda.stream(gs):
+        amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
+        qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        amp = qfx.amplitudes(plan, x1, workspace=ws, out=out)
+        qfx.amplitudes_backward(plan, x1, 2 * amp, workspace=bws)
+    with torch.cuda.stream(gs):
+        graph.replay()
+        torch.cuda.synchronize()
+        ev[0].record(gs)
+        for _ in range(50):
+            graph.replay()
+        ev[1].record(gs)
+    torch.cuda.synchronize()
+    qfx.sync()
+    graph_ms = ev[0].elapsed_time(ev[1]) / 50
+    del graph
     flops = plan.stats["flops_per_item"]
     fwd, bwd = float(np.median(f_ms)), float(np.median(b_ms))
     peak, _ = fp32_peak(torch, torch.device("cuda", 0), clk.get("sm_max_mhz") or 2070.0)
@@ -531,7 +552,8 @@ def measure_adjoint(qfx, torch, steps, warmup):
     return {"workload": f"6x6x(1+24+1) parametrised RQC, 128 bitstrings, {len(circ.gates)} gate "
                         f"tensors, every step output stored",
             "forward_ms": fwd, "backward_ms": bwd, "forward_tflops": flops / (fwd / 1e3) / 1e12,
-            "backward_tflops": bt,
+            "backward_tflops": bt, "graph_forward_backward_ms": graph_ms,
+            "graph_tflops": 4 * flops / (graph_ms / 1e3) / 1e12,
             "roofline": {"bound": "alu", "achieved": bt, "peak": peak, "unit": "TFLOP/s",
                          "frac": bt / peak, "what": "backward, 3 x forward flops / time, FP32 FMA peak"},
             "clocks": clk}

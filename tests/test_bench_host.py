@@ -47,7 +47,8 @@ def test_summary_holds_every_part():
             "clocks": clk}
     line = {"value": 55.2, "roofline": {"frac": 0.70}, "e2e": {"value": 55.1}, "clocks": clk,
             "precision_modes": {"bf16x3": mode},
-            "adjoint": {"forward_ms": 1.0, "backward_ms": 3.9, "roofline": {"frac": 0.18}},
+            "adjoint": {"forward_ms": 1.0, "backward_ms": 3.9, "roofline": {"frac": 0.18},
+                        "graph_forward_backward_ms": 4.5},
             "permute": {"cases": [{"frac": 0.75}, {"frac": 0.9}]},
             "batch": {"fp32_persistent": {"value": 41.6}, "fp32_per_item": {"value": 48.2},
                       "bf16x3_graph": {"value": 157.7}, "bf16x3_per_item": {"value": 153.6}},

@@ -237,6 +237,10 @@ def test_contract_step_variants(qfx, variant, shape):
     out = qfx.contract_step(dS, dB, P, K, N, NL, Sd, variant=variant)
     qfx.sync()
     got = out.cpu().numpy().reshape(NH, P, NL, Sd)
+    # element by element against each output's own scale sum_k |S||B|, and normwise
+    scale = primitives.contract_step(np.abs(S), np.abs(B), P, K, N, Sd).real
+    scale = scale.reshape(P, NH, NL, Sd).transpose(1, 0, 2, 3)
+    assert np.all(np.abs(got - want) <= 1e-6 * scale)
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err < 1e-6, err
 
