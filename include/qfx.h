@@ -199,6 +199,9 @@ typedef struct {
   int64_t P, K, N, NL, Sd;  /* shapes as in qfx_plan_create's formula; NH = N / NL */
   double flops;       /* 8*P*K*N*Sd = 8 sqrt(v0 v1 v2), Eq. 1 */
   double bytes;       /* 8*(P*K*Sd + K*N + P*N*Sd) */
+  int32_t parts;      /* contraction-tree nodes: > 0 when K runs as this many 1024-long chunks
+                         side by side (partial products summed in FP64), else 0 */
+  int32_t reserved;
 } qfx_step_info;
 
 qfx_status qfx_plan_step(const qfx_plan* p, int32_t i, qfx_step_info* out);

@@ -48,7 +48,51 @@ int launch_cfg(const StepArgs& a, int batch, cudaStream_t stream) {
   return (int)cudaGetLastError();
 }
 
+// Split-K sum of a chunked contraction.  A block covers kRedE consecutive outputs with
+// kRedL lanes each: lane l of an output adds chunks l, l + kRedL, ... in FP64 (a warp reads
+// kRedE-long runs of each chunk's row), then lane 0 adds the lanes' sums in lane order and
+// rounds once to FP32.
+constexpr int kRedE = 32, kRedL = 8;
+__global__ void __launch_bounds__(kRedE * kRedL) reduce_parts_kernel(const float2* __restrict__ part,
+                                                                     int64_t part_stride, int64_t parts,
+                                                                     int64_t out, float2* __restrict__ C,
+                                                                     int64_t c_stride) {
+  __shared__ double2 lanes[kRedL][kRedE];
+  const int el = threadIdx.x % kRedE, lane = threadIdx.x / kRedE;
+  const int64_t e = (int64_t)blockIdx.x * kRedE + el;
+  const float2* pp = part + (int64_t)blockIdx.y * part_stride;
+  double re = 0.0, im = 0.0;
+  if (e < out) {
+#pragma unroll 4
+    for (int64_t c = lane; c < parts; c += kRedL) {
+      const float2 v = pp[c * out + e];
+      re += (double)v.x;
+      im += (double)v.y;
+    }
+  }
+  lanes[lane][el] = make_double2(re, im);
+  __syncthreads();
+  if (lane == 0 && e < out) {
+    for (int l = 1; l < kRedL; ++l) {
+      re += lanes[l][el].x;
+      im += lanes[l][el].y;
+    }
+    C[(int64_t)blockIdx.y * c_stride + e] = make_float2((float)re, (float)im);
+  }
+}
+
 }  // namespace
+
+int launch_reduce_parts(const void* part, int64_t part_stride, int64_t parts, int64_t out, void* C,
+                        int64_t c_stride, int batch, void* stream) {
+  if (parts < 1 || out < 1 || batch < 1 || batch > 65535) return (int)cudaErrorInvalidValue;
+  const int64_t blocks = (out + kRedE - 1) / kRedE;
+  if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
+  reduce_parts_kernel<<<dim3((unsigned)blocks, (unsigned)batch), kRedE * kRedL, 0, (cudaStream_t)stream>>>(
+      (const float2*)part, part_stride, parts, out, (float2*)C, c_stride);
+  count_launch();
+  return (int)cudaGetLastError();
+}
 
 int simt_prepare_attributes() {
 #define QFX_ATTR(V, BM, BJ, TM, TJ, KM, ST) \

@@ -455,12 +455,23 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
           nd.variant = qfx::tc_variant_of(p->precision);
           tc_scratch = std::max(tc_scratch, qfx::tc_scratch_bytes(p->precision, nd.chunk, nd.N));
         }
+        // a chunked contraction with a small result: its chunks side by side in one FP32
+        // launch, partial products in the item's scratch, then their sum
+        nd.parts = 0;
+        const int64_t out_el = nd.P * nd.N * nd.Sd, parts = nd.K / nd.chunk;
+        if (nd.chunk < nd.K && nd.K % nd.chunk == 0 && nd.P == 1 && out_el <= qfx::kTreeSplitOut &&
+            parts <= 65535 && (uint64_t)parts * (uint64_t)out_el * 8 <= qfx::kTreeSplitBytes) {
+          nd.variant = qfx::pick_variant(nd.N, nd.Sd);
+          nd.parts = (int32_t)parts;
+          tc_scratch = std::max(tc_scratch, (uint64_t)parts * (uint64_t)out_el * 8);
+        }
         qfx::Step st{};
         st.site = nd.out;
         st.variant = nd.variant;
         st.P = nd.P; st.K = nd.K; st.N = nd.N; st.NL = nd.NL; st.Sd = nd.Sd;
         st.flops = nd.flops;
         st.bytes = nd.bytes;
+        st.parts = nd.parts;
         p->flops_per_item += nd.flops;
         p->bytes_per_item += nd.bytes;
         p->steps.push_back(st);
@@ -526,6 +537,8 @@ extern "C" qfx_status qfx_plan_step(const qfx_plan* p, int32_t i, qfx_step_info*
   out->P = s.P; out->K = s.K; out->N = s.N; out->NL = s.NL; out->Sd = s.Sd;
   out->flops = s.flops;
   out->bytes = s.bytes;
+  out->parts = s.parts;
+  out->reserved = 0;
   return QFX_OK;
 }
 

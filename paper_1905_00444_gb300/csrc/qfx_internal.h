@@ -81,6 +81,7 @@ struct Step {
   int32_t variant;
   int64_t P, K, N, NL, Sd;
   double flops, bytes;
+  int32_t parts;   // tree nodes: split-K partial products (TreeNode::parts)
 };
 
 // One node of a contraction-tree plan (plan family 1): C = A * B over their shared legs as
@@ -99,11 +100,17 @@ struct TreeNode {
   uint64_t offA, offB, offA2, offB2, offC;
   int32_t variant;
   int64_t chunk;                     // K > kTreeChunk: K is summed in chunks of this many
+  int32_t parts;                     // > 0: the chunks' products side by side, then summed
 };
 // Contractions longer than this run as chunks of this length, each added into the result:
 // an FP32 sum's rounding error grows with the square root of its length, and the tree's
 // pairwise contractions of large tensors reach K = 2^20.
 constexpr int64_t kTreeChunk = 1024;
+// A chunked contraction whose result has at most kTreeSplitOut elements fills too few CTAs
+// per chunk: its chunks instead run as one launch (one CTA row per chunk) into partial
+// products of at most kTreeSplitBytes per item, summed by launch_reduce_parts.
+constexpr int64_t kTreeSplitOut = int64_t(1) << 18;
+constexpr uint64_t kTreeSplitBytes = uint64_t(64) << 20;
 
 // Workspace layout:
 //   header: per concurrent item: maxabs[n_sites] (u32) + exps[n_sites] (i32), padded
@@ -194,6 +201,10 @@ int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride
                 int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
                 int batch, int variant, int precision, void* stream, int beta = 0);
 int pick_variant(int64_t N, int64_t Sd);
+// C[b][e] = sum over c < parts of part[b][c][e] (e < out; complex FP32 in and out), per batch
+// entry b < batch, in FP64 and a fixed order; strides in float2 units.
+int launch_reduce_parts(const void* part, int64_t part_stride, int64_t parts, int64_t out, void* C,
+                        int64_t c_stride, int batch, void* stream);
 // tensor-core steps (variants 10 = BF16x3, 11 = TF32x3)
 constexpr int kVariantTcBf16 = 10, kVariantTcTf32 = 11, kVariantTcBf16x2 = 14;
 constexpr int kTcFast = 1;       // QFX_TC_FAST_ACCUMULATION

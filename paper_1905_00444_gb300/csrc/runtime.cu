@@ -240,8 +240,20 @@ static qfx_status exec_tree(const qfx_plan* p, const DeviceTables& t, const uint
         }
       }
       profile_begin(st, &slot);
+      if (nd.parts > 0) {
+        // split K: chunk c's product into part[c] (the item's scratch), then the sum into C
+        for (int gi = 0; gi < g && !err; ++gi) {
+          char* blk = items + (uint64_t)gi * ib;
+          err = launch_step(blk + nd.offA2, nd.chunk * nd.N, blk + nd.offB2, nd.chunk * nd.Sd,
+                            blk + L.simage, nd.N * nd.Sd, 1, nd.chunk, nd.N, nd.NL, nd.Sd, nd.parts,
+                            nd.variant, QFX_PREC_FP32_SIMT, st, 0);
+        }
+        if (!err)
+          err = launch_reduce_parts(items + L.simage, (int64_t)(ib / 8), nd.parts, nd.N * nd.Sd,
+                                    items + nd.offC, (int64_t)(ib / 8), g, st);
+      }
       // a long contraction in chunks of nd.chunk rows of S and B (P = 1), each added into C
-      for (int64_t k0 = 0; k0 < nd.K && !err; k0 += nd.chunk) {
+      for (int64_t k0 = 0; k0 < nd.K && !err && nd.parts == 0; k0 += nd.chunk) {
         const char* Sk = items + nd.offA2 + (uint64_t)(k0 * nd.N) * 8;
         const char* Bk = items + nd.offB2 + (uint64_t)(k0 * nd.Sd) * 8;
         if (nd.variant >= kVariantTcBf16)

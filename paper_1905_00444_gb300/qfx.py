@@ -54,7 +54,7 @@ class PlanStats(C.Structure):
 class StepInfo(C.Structure):
     _fields_ = [("site", C.c_int32), ("variant", C.c_int32), ("P", C.c_int64), ("K", C.c_int64),
                 ("N", C.c_int64), ("NL", C.c_int64), ("Sd", C.c_int64), ("flops", C.c_double),
-                ("bytes", C.c_double)]
+                ("bytes", C.c_double), ("parts", C.c_int32), ("reserved", C.c_int32)]
 
 
 class BatchItem(C.Structure):

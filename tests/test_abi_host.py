@@ -435,7 +435,24 @@ def test_tree_plans_steps_cap_and_slices():
     assert tree.stats["n_steps"] == 48                # n - 1 pairwise contractions
     assert tree.open_sites == line.open_sites
     tc = qfx.Plan(c, n_open=6, max_intermediate_bytes=8 << 30, family="tree", precision="bf16x3")
-    assert tc.cuts == tree.cuts and all(s["variant"] >= 10 for s in tc.steps if s["N"] >= 128)
+    assert tc.cuts == tree.cuts and all(s["variant"] >= 10 for s in tc.steps if s["N"] >= 128 and not s["parts"])
+    assert all(s["parts"] == 0 for s in line.steps)
+
+
+def test_tree_plan_split_k_root():
+    """8x8x(1+32+1) at 8 GiB: the root contracts K = 2^21 into 8x8 outputs; it runs as 2048
+    side-by-side chunks (FP32, whatever the plan's precision) whose partial products fit the
+    item's scratch."""
+    c = qfx.Circuit(ri.rqc(8, 8, 32, seed=0))
+    for prec in ("fp32", "bf16x3"):
+        tree = qfx.Plan(c, n_open=6, max_intermediate_bytes=8 << 30, family="tree", precision=prec)
+        root = tree.steps[-1]
+        assert (root["K"], root["N"] * root["Sd"], root["parts"]) == (1 << 21, 64, 2048)
+        assert root["variant"] < 10
+        for s in tree.steps:
+            if s["parts"]:
+                assert s["K"] == 1024 * s["parts"] and s["P"] * s["N"] * s["Sd"] <= 1 << 18
+        assert tree.workspace_bytes(1) >= 2048 * 64 * 8 + tree.stats["max_elements"] * 8
 
 
 def test_tree_plan_forced_cuts_keep_the_slice_numbering():

@@ -3,7 +3,8 @@ tree of TTGT steps with greedy cuts, run by the permute and step kernels.
 
 * Small grids against the FP64 oracle, element by element (1e-5, floor 2^(-n/2)): the
   state vector (every output open), the network route with open sites, capped plans whose
-  slices sum to the amplitude, general two-qubit gates.
+  slices sum to the amplitude, general two-qubit gates, split-K nodes (a long contraction
+  into a small result as side-by-side chunks and an FP64 sum).
 * The benchmarked 7x7x(1+32+1) workload under the 12 stored vertical cuts: the tree plan
   contracts each slice with a different order and different kernels shapes than the line
   sweep (9.7e12 instead of 2.3e14 flop), and must match the stored FP64 slices.
@@ -87,6 +88,25 @@ def test_capped_tree_plan_slices_sum_to_the_amplitude(qfx):
     got = run(qfx, plan, [x1], slices=(s, s + 1))[0]
     ref = network.amplitudes_sliced(c, x1, plan.open_sites, plan.cuts, [s])
     np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("shape", [(5, 5, 24, 0), (4, 4, 32, 4), (6, 6, 24, 6)])
+def test_split_k_nodes_vs_oracle(qfx, shape):
+    # a long contraction into a small result (the root, typically) runs its 1024-long
+    # chunks side by side and sums the partial products in FP64
+    rows, cols, d, n_open = shape
+    c = ri.rqc(rows, cols, d, seed=0)
+    plan = qfx.Plan(qfx.Circuit(c), n_open=n_open, family="tree")
+    split = [s for s in plan.steps if s["parts"] > 0]
+    assert split and all(s["K"] == 1024 * s["parts"] for s in split)
+    x1s = ri.random_bitstrings(rows * cols, 2, seed=8)
+    out = run(qfx, plan, x1s, items=2)
+    if rows * cols <= 16:
+        psi = statevector.amplitudes(c)
+        want = np.array([[psi[expand(x, plan.open_sites, j)] for j in range(1 << n_open)] for x in x1s])
+    else:
+        want = np.array([network.amplitudes_open(c, int(x), plan.open_sites) for x in x1s])
+    check(out, want, rows * cols)
 
 
 def test_general_two_qubit_gates(qfx):
