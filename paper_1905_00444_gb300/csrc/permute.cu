@@ -36,15 +36,18 @@ struct PermArgs {
   int64_t ostr[kMaxRank];   // output stride of each output axis
   int la, lb;               // tiled: la = innermost output axis, lb = axis with input stride 1
   int64_t tiles_a, tiles_b;
+  int na;                   // tiled: the tile's a side spans the last na output axes (not lb)
+  int64_t da;               // their extent (contiguous in the output)
 };
 
 // ---- case 1: innermost axis shared -> contiguous rows ------------------------
 // Each block copies 4096 consecutive output elements (any number of rows): thread pairs
 // of elements stay in one row when D is even, so they move as 16-byte vectors.  The
-// input offset of every row the block touches is computed once into shared memory
-// (the mixed-radix divisions per row, not per element).
+// input offset of every row the block touches is computed once into shared memory: each
+// thread takes a run of consecutive rows, decomposes the first one (mixed-radix
+// divisions) and steps an odometer through the rest.
 constexpr int kRowChunk = 4096;
-constexpr int kMaxChunkRows = kRowChunk / 8 + 2;   // D >= 8 for this kernel
+constexpr int kMaxChunkRows = kRowChunk / 2 + 2;   // D >= 2 for this kernel
 __global__ void __launch_bounds__(256) permute_rows_kernel(const float2* __restrict__ in,
                                                            float2* __restrict__ out,
                                                            const PermArgs a, int64_t total) {
@@ -54,14 +57,25 @@ __global__ void __launch_bounds__(256) permute_rows_kernel(const float2* __restr
   const int64_t r0 = base / D;
   const int64_t end = min(total, base + kRowChunk);
   const int nrows = (int)((end - 1) / D - r0 + 1);
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-    int64_t row = r0 + i, ib = 0;
+  const int per = (nrows + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int i0 = (int)threadIdx.x * per, i1 = min(nrows, i0 + per);
+  if (i0 < i1) {
+    int64_t coord[kMaxRank];
+    int64_t row = r0 + i0, ib = 0;
     for (int ax = a.rank - 2; ax >= 0; --ax) {
-      const int64_t c = row % a.dim[ax];
+      coord[ax] = row % a.dim[ax];
       row /= a.dim[ax];
-      ib += c * a.istr[ax];
+      ib += coord[ax] * a.istr[ax];
     }
-    rowoff[i] = ib;
+    for (int i = i0; i < i1; ++i) {
+      rowoff[i] = ib;
+      for (int ax = a.rank - 2; ax >= 0; --ax) {   // the next row
+        ib += a.istr[ax];
+        if (++coord[ax] < a.dim[ax]) break;
+        ib -= coord[ax] * a.istr[ax];
+        coord[ax] = 0;
+      }
+    }
   }
   __syncthreads();
   const int Di = (int)D, first = (int)(base - r0 * D);   // column of the block's first element
@@ -82,8 +96,7 @@ __global__ void __launch_bounds__(256) permute_rows_kernel(const float2* __restr
   }
 }
 
-// Rows shorter than 8 elements (or longer than 2^30): the mixed-radix divisions stay per
-// element.
+// Rows of one element (or longer than 2^30): the mixed-radix divisions stay per element.
 __global__ void __launch_bounds__(256) permute_short_rows_kernel(const float2* __restrict__ in,
                                                                  float2* __restrict__ out,
                                                                  const PermArgs a, int64_t total) {
@@ -108,6 +121,7 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const float2* __restr
                                                            float2* __restrict__ out,
                                                            const PermArgs a, int64_t batch) {
   __shared__ float2 tile[32][33];
+  __shared__ int64_t offa[32];
   const int64_t per = a.tiles_a * a.tiles_b;
   const int64_t t = blockIdx.x % per;
   const int64_t b0 = (int64_t)(blockIdx.x / per) * kTileBatch;
@@ -115,21 +129,32 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const float2* __restr
   // batch coordinates of b0
   int64_t coord[kMaxRank];
   int64_t r = b0, ib = 0, ob = 0;
+  const int afirst = a.rank - a.na;   // the a side: output axes afirst .. rank-1
   for (int ax = a.rank - 1; ax >= 0; --ax) {
     coord[ax] = 0;
-    if (ax == a.la || ax == a.lb) continue;
+    if (ax >= afirst || ax == a.lb) continue;
     coord[ax] = r % a.dim[ax];
     r /= a.dim[ax];
     ib += coord[ax] * a.istr[ax];
     ob += coord[ax] * a.ostr[ax];
   }
   const int64_t A0 = ta * 32, B0 = tb * 32;
-  const int64_t Da = a.dim[a.la], Db = a.dim[a.lb];
+  const int64_t Da = a.da, Db = a.dim[a.lb];
   const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+  if (threadIdx.x < 32) {   // input offsets of the tile's 32 positions along a
+    int64_t ia = A0 + threadIdx.x, off = 0;
+    if (ia < Da)
+      for (int ax = a.rank - 1; ax >= afirst; --ax) {
+        off += (ia % a.dim[ax]) * a.istr[ax];
+        ia /= a.dim[ax];
+      }
+    offa[threadIdx.x] = off;
+  }
+  __syncthreads();
   for (int64_t bi = b0; bi < b0 + kTileBatch && bi < batch; ++bi) {
     for (int yy = y; yy < 32; yy += 8) {
       const int64_t ia = A0 + yy, jb = B0 + x;
-      if (ia < Da && jb < Db) tile[yy][x] = in[ib + ia * a.istr[a.la] + jb];
+      if (ia < Da && jb < Db) tile[yy][x] = in[ib + offa[yy] + jb];
     }
     __syncthreads();
     for (int yy = y; yy < 32; yy += 8) {
@@ -139,7 +164,7 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const float2* __restr
     __syncthreads();
     // odometer: next batch coordinate (innermost batch axis first)
     for (int ax = a.rank - 1; ax >= 0; --ax) {
-      if (ax == a.la || ax == a.lb) continue;
+      if (ax >= afirst || ax == a.lb) continue;
       ib += a.istr[ax];
       ob += a.ostr[ax];
       if (++coord[ax] < a.dim[ax]) break;
@@ -426,7 +451,7 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
   const float2* src = (const float2*)in;
   float2* dst = (float2*)out;
   if (a.istr[fr - 1] == 1) {
-    if (a.dim[fr - 1] >= 8 && a.dim[fr - 1] < (int64_t(1) << 30)) {
+    if (a.dim[fr - 1] >= 2 && a.dim[fr - 1] < (int64_t(1) << 30)) {
       const int64_t blocks = (total + kRowChunk - 1) / kRowChunk;
       if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
       permute_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, a, total);
@@ -457,9 +482,17 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
       count_launch();
       return err;
     }
-    a.tiles_a = (a.dim[a.la] + 31) / 32;
+    // the tile's a side: the innermost output axis, widened by the next ones outwards
+    // (stopping at lb) until it spans 32 elements; they are contiguous in the output
+    a.na = 1;
+    a.da = a.dim[fr - 1];
+    while (a.da < 32 && fr - 1 - a.na >= 0 && fr - 1 - a.na != a.lb) {
+      a.da *= a.dim[fr - 1 - a.na];
+      ++a.na;
+    }
+    a.tiles_a = (a.da + 31) / 32;
     a.tiles_b = (a.dim[a.lb] + 31) / 32;
-    const int64_t batch = total / (a.dim[a.la] * a.dim[a.lb]);
+    const int64_t batch = total / (a.da * a.dim[a.lb]);
     const int64_t blocks = ((batch + kTileBatch - 1) / kTileBatch) * a.tiles_a * a.tiles_b;
     if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
     permute_tile_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, a, batch);

@@ -256,7 +256,14 @@ def test_contract_step_variants(qfx, variant, shape):
                                   # tensor-map path: two input runs, edge tiles, no batch
                                   # axis, a batch axis of 2
                                   ((6, 16, 5, 18, 32), (3, 0, 4, 2, 1)), ((48, 20, 100), (2, 1, 0)),
-                                  ((130, 72), (1, 0)), ((16, 2, 16), (2, 1, 0))])
+                                  ((130, 72), (1, 0)), ((16, 2, 16), (2, 1, 0)),
+                                  # rows of 2, 3 and 4 elements (row offsets per thread run)
+                                  ((7, 3, 2), (1, 0, 2)), ((5, 6, 3), (1, 0, 2)),
+                                  ((9, 5, 4), (1, 0, 2)), ((33, 129, 2), (1, 0, 2)),
+                                  # tiled transpose whose a side spans several output axes
+                                  ((3, 40, 16, 2, 16), (0, 2, 4, 1, 3)),
+                                  ((5, 2, 2, 2, 16), (4, 0, 3, 2, 1)),
+                                  ((2, 24, 2, 2), (1, 3, 0, 2))])
 def test_permute_vs_numpy(qfx, case):
     shape, perm = case
     x = ri.random_complex(int(np.prod(shape)), seed=3)
