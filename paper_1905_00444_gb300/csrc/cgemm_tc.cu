@@ -229,6 +229,25 @@ struct TcArgs {
 // 12 TMEM owner + MMA issuer, 13 S stream and tensor-map copies.
 constexpr uint32_t kAlignPad = 128;
 
+// Tile t -> (item g, 128-row tile jt, column tile nh).  Within an item the column tiles
+// come in bands of kBand; inside a band the column tile runs fastest, so the tiles in
+// flight at once (one per CTA) share a few column slices of the S image and a few row
+// tiles of B in L2 (with N = 8192 one k-chunk of the S image alone is 151 MB).  With
+// NHt <= kBand this is the plain order, column tile fastest.
+constexpr int64_t kBand = 8;
+__device__ __forceinline__ void tile_coords(const TcArgs& a, int64_t t, int64_t& g, int64_t& jt,
+                                            int64_t& nh) {
+  const int64_t per_item = a.JT * a.NHt;
+  g = t / per_item;
+  int64_t r = t - g * per_item;
+  const int64_t band = r / (kBand * a.JT);
+  const int64_t n0 = band * kBand;
+  const int64_t w = a.NHt - n0 < kBand ? a.NHt - n0 : kBand;
+  r -= band * kBand * a.JT;
+  jt = r / w;
+  nh = n0 + (r - jt * w);
+}
+
 template <int MODE, bool SPLITACC>
 struct TcCfg {
   using M_ = Mode<MODE>;
@@ -307,7 +326,6 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_slot;
   volatile int* abort = &abort_flag;
-  const int64_t per_item = a.JT * a.NHt;
 
   if (warp < 4) {
     // ---- producers: split 128 rows of B per k-stage into term planes -------------------
@@ -345,7 +363,8 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
       }
     } else {
     auto row_ptr = [&](int64_t tt, int64_t& pofs) -> const float2* {
-      const int64_t g = tt / per_item, jt = (tt % per_item) / a.NHt;
+      int64_t g, jt, nh;
+      tile_coords(a, tt, g, jt, nh);
       const int64_t jg = jt * kRows + tid;
       pofs = jg < a.J ? (jg / a.Sd) * a.K * a.Sd + (jg % a.Sd) : -1;
       return a.B + g * a.b_stride;
@@ -384,7 +403,8 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
       int64_t q = 0, issued = 0;
       bool ok = !a.withhold_s;
       for (int64_t t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
-        const int64_t g = t / per_item, nh = t % a.NHt;
+        int64_t g, jt, nh;
+        tile_coords(a, t, g, jt, nh);
         const char* img = a.simage + g * a.img_stride;
         for (int64_t it = 0; it < KT; ++it, ++q) {
           const int s = (int)(q % STAGES);
@@ -407,7 +427,8 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
       int64_t q = 0, issued = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
-        const int64_t g = t / per_item, jt = (t % per_item) / a.NHt;
+        int64_t g, jt, nh;
+        tile_coords(a, t, g, jt, nh);
         const int64_t j0 = jt * kRows;
         const int c0 = (int)(j0 % a.Sd), c2 = (int)(j0 / a.Sd);
         for (int64_t it = 0; it < KT; ++it, ++q) {
@@ -493,7 +514,8 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
       const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)(tc & 1), abort, 256) && !*abort);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t g = t / per_item, jt = (t % per_item) / a.NHt, nh = t % a.NHt;
+      int64_t g, jt, nh;
+      tile_coords(a, t, g, jt, nh);
       const int64_t jg = jt * kRows + row;
       const bool valid = jg < a.J;
       float2* Cg = a.C + g * a.c_stride;
@@ -543,10 +565,20 @@ __global__ void __launch_bounds__(TcCfg<MODE, SPLITACC>::THREADS, 1)
               if (++nl == NL) { nl = 0; dst += strideNH - (int64_t)NL * a.Sd; }
             }
           } else {   // a chunk of a long contraction: add into C
+            // all 16 reads first (C is written only by this tile in this launch, so the
+            // read-only path applies): one memory latency per chunk, not one per element
+            float2 o[16];
+            float2* d = dst;
+            int l = nl;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const float2 o = *dst;
-              *dst = make_float2(vr[i] + o.x, vi[i] + o.y);
+              o[i] = __ldg(d);
+              d += a.Sd;
+              if (++l == NL) { l = 0; d += strideNH - (int64_t)NL * a.Sd; }
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              *dst = make_float2(vr[i] + o[i].x, vi[i] + o[i].y);
               dst += a.Sd;
               if (++nl == NL) { nl = 0; dst += strideNH - (int64_t)NL * a.Sd; }
             }
