@@ -348,7 +348,10 @@ qfx_status qfx_tensor_peak(int32_t precision, int64_t mmas_per_sm, double* tflop
 
 /* One contraction step of the TTGT form (Sec. III.E), for tests and microbenchmarks:
  * C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] * B[p][k][s], complex64, all device pointers,
- * 16-byte aligned, no aliasing.  `variant` < 0 lets the library choose (FP32 only).
+ * 16-byte aligned, no aliasing.  `variant` < 0 lets the library choose (FP32 only);
+ * FP32 tile variants are 0-9 (0-4 need an even Sd) and their fill variants 20-23 (even
+ * Sd) and 25-28, which compute 4096 or 2048 outputs per CTA for grids that would leave SMs
+ * idle; every variant gives bit-identical results.
  * Tensor-core precisions run on tcgen05 when N % 16 == 0 and N <= 128 or a multiple of 128
  * (fast accumulation: N <= 256 or a multiple of 256), K a multiple of the term's k step
  * (16 for BF16x3 and BF16x2, 8 for TF32x3) and P*Sd >= 128, otherwise on the FP32

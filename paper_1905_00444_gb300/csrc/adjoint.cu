@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kMaxEvents = 64;     // events per site the fold adjoint supports
-constexpr int64_t kGradsBlocks = 608;   // site-gradient grid target: 4 blocks per SM of 152
+constexpr int64_t kGradsBlocks = 304;   // site-gradient grid target: 2 blocks per SM of 152
 
 uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
@@ -140,6 +140,42 @@ __global__ void __launch_bounds__(kT) rstep_kernel(const float2* __restrict__ S,
   }
 }
 
+// ---- conjugate transposes of the site matrices for the reverse steps with NL = N -------
+// Such a reverse step is a forward step of the step tile: Rout[p][k][s] =
+// sum_n S'[n][k] Rin[p][n][s] with S'[n][k] = conj(S[k][n]) (K and N swapped, NL = K).
+// One launch for all of them: entry y of the table below transposes its K x N matrix in
+// 32 x 32 tiles through shared memory (tile x of ceil(K/32) * ceil(N/32); extra blocks exit).
+constexpr int kConjMax = 144;
+struct ConjTable {
+  int64_t off[kConjMax];   // element offset of the site matrix (and of its transpose)
+  int32_t K[kConjMax], N[kConjMax];
+  int32_t count;
+};
+__global__ void __launch_bounds__(kT) conj_transpose_kernel(const float2* __restrict__ sites,
+                                                            float2* __restrict__ sconj, const ConjTable tab) {
+  __shared__ float2 tile[32][33];
+  const int y = blockIdx.y;
+  const int64_t K = tab.K[y], N = tab.N[y];
+  const int64_t tk = (K + 31) / 32, tn = (N + 31) / 32;
+  if ((int64_t)blockIdx.x >= tk * tn) return;   // block-uniform
+  const int64_t k0 = (blockIdx.x % tk) * 32, n0 = (blockIdx.x / tk) * 32;
+  const float2* S = sites + tab.off[y];
+  float2* St = sconj + tab.off[y];
+  const int x = threadIdx.x & 31, r = threadIdx.x >> 5;
+  for (int rr = r; rr < 32; rr += kT / 32) {   // read rows k, columns n (coalesced along n)
+    const int64_t k = k0 + rr, n = n0 + x;
+    if (k < K && n < N) tile[rr][x] = S[k * N + n];
+  }
+  __syncthreads();
+  for (int rr = r; rr < 32; rr += kT / 32) {   // write rows n, columns k (coalesced along k)
+    const int64_t n = n0 + rr, k = k0 + x;
+    if (k < K && n < N) {
+      const float2 v = tile[x][rr];
+      St[n * K + k] = make_float2(v.x, -v.y);
+    }
+  }
+}
+
 int launch_rstep(const float2* S, const float2* Rin, float2* Rout, int64_t P, int64_t K, int64_t N, int64_t NL,
                  int64_t Sd, cudaStream_t st) {
   const int64_t J = P * Sd;
@@ -156,28 +192,30 @@ int launch_rstep(const float2* S, const float2* Rin, float2* Rout, int64_t P, in
 // ---- site gradient, split over columns: part[c][k][n] = sum_{j in c} conj(L(k,j)) R(n,j) ----
 // BM x BN output tiles (16 or 64 each, so that K or N of 8 or 16 does not fill 64-wide
 // tiles with zeros); thread (ty, tx) owns BM/16 x BN/16 outputs.  The columns j are cut
-// into chunks so that the grid has about kGradsBlocks blocks whatever K and N are.
+// into chunks so that the grid has about kGradsBlocks blocks whatever K and N are.  Slabs
+// of 16 columns of L and R move through two shared-memory buffers by cp.async (the next
+// slab's copies overlap this one's FMAs); a thread's column j steps through (p, s) without
+// divisions.
+__device__ __forceinline__ void g_cp_async8(void* smem, const void* gmem, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(pred ? 8 : 0));
+}
 template <int BM, int BN>
 __global__ void __launch_bounds__(kT) grads_kernel(const float2* __restrict__ Lin, const float2* __restrict__ Rin,
                                                    float2* __restrict__ part, int64_t P, int64_t K,
                                                    int64_t N, int64_t NL, int64_t Sd, int64_t chunk) {
   constexpr int BJ = 16, TMK = BM / 16, TNN = BN / 16;
+  constexpr int LA = BM + 2, LB = BN + 2;   // rows of 16-byte multiples, 2-way store conflicts
   static_assert(kT == 256 && BM % 16 == 0 && BN % 16 == 0, "thread layout");
-  __shared__ float2 As[BJ][BM + 1];
-  __shared__ float2 Bs[BJ][BN + 1];
+  __shared__ __align__(16) float2 As[2][BJ][LA];
+  __shared__ __align__(16) float2 Bs[2][BJ][LB];
   const int64_t J = P * Sd;
   const int64_t k0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   const int64_t jb = (int64_t)blockIdx.z * chunk, je = min(J, jb + chunk);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int64_t strideNH = P * NL * Sd;
-  float2 acc[TMK][TNN];
-#pragma unroll
-  for (int i = 0; i < TMK; ++i)
-#pragma unroll
-    for (int j = 0; j < TNN; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  // every element this thread loads has column jj = threadIdx.x % BJ and rows
-  // c = threadIdx.x / BJ + 16 i: the k and n parts of the addresses are fixed, the j part
-  // takes one division per step
+  // every element this thread copies has column jj = threadIdx.x % BJ of the slab and rows
+  // c0 + 16 i: the k and n parts of the addresses are fixed
   const int jj = threadIdx.x % BJ, c0 = threadIdx.x / BJ;
   int64_t koff[TMK], noff[TNN];
 #pragma unroll
@@ -190,47 +228,80 @@ __global__ void __launch_bounds__(kT) grads_kernel(const float2* __restrict__ Li
     const int64_t n = n0 + c0 + 16 * i;
     noff[i] = n < N ? (n / NL) * strideNH + (n % NL) * Sd : -1;
   }
-  for (int64_t j0 = jb; j0 < je; j0 += BJ) {
-    const int64_t j = j0 + jj;
+  int64_t j = jb + jj;
+  int64_t jp = j / Sd, js = j - jp * Sd;
+  auto load = [&](int buf) {
     const bool jok = j < je;
-    const int64_t jp = jok ? j / Sd : 0, js = jok ? j - jp * Sd : 0;
+    const float2* Lp = Lin + jp * K * Sd + js;
+    const float2* Rp = Rin + jp * NL * Sd + js;
 #pragma unroll
     for (int i = 0; i < TMK; ++i) {
-      float2 a = make_float2(0.f, 0.f);
-      if (jok && koff[i] >= 0) { a = Lin[jp * K * Sd + koff[i] + js]; a.y = -a.y; }
-      As[jj][c0 + 16 * i] = a;
+      const bool ok = jok && koff[i] >= 0;
+      g_cp_async8(&As[buf][jj][c0 + 16 * i], ok ? Lp + koff[i] : Lin, ok);
     }
 #pragma unroll
     for (int i = 0; i < TNN; ++i) {
-      float2 b = make_float2(0.f, 0.f);
-      if (jok && noff[i] >= 0) b = Rin[jp * NL * Sd + noff[i] + js];
-      Bs[jj][c0 + 16 * i] = b;
+      const bool ok = jok && noff[i] >= 0;
+      g_cp_async8(&Bs[buf][jj][c0 + 16 * i], ok ? Rp + noff[i] : Rin, ok);
     }
-    __syncthreads();
+    asm volatile("cp.async.commit_group;\n" ::);
+    j += BJ;   // this thread's column in the next slab
+    js += BJ;
+    while (js >= Sd) { js -= Sd; ++jp; }
+  };
+  float2 acc[TMK][TNN];
+#pragma unroll
+  for (int i = 0; i < TMK; ++i)
+#pragma unroll
+    for (int q = 0; q < TNN; ++q) acc[i][q] = make_float2(0.f, 0.f);
+  const int64_t nslab = (je - jb + BJ - 1) / BJ;
+  if (nslab > 0) load(0);
+  for (int64_t t = 0; t < nslab; ++t) {
+    const int buf = (int)(t & 1);
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncthreads();   // slab t landed for every thread; slab t-1's buffer is free
+    if (t + 1 < nslab) load(buf ^ 1);
 #pragma unroll
     for (int r = 0; r < BJ; ++r) {
       float2 a[TMK], b[TNN];
+      if constexpr (TMK % 2 == 0) {   // 16-byte pairs (ty * TMK even, rows 16-byte multiples)
 #pragma unroll
-      for (int i = 0; i < TMK; ++i) a[i] = As[r][ty * TMK + i];
+        for (int i = 0; i < TMK; i += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(&As[buf][r][ty * TMK + i]);
+          a[i] = make_float2(v.x, v.y);
+          a[i + 1] = make_float2(v.z, v.w);
+        }
+      } else {
 #pragma unroll
-      for (int j = 0; j < TNN; ++j) b[j] = Bs[r][tx * TNN + j];
+        for (int i = 0; i < TMK; ++i) a[i] = As[buf][r][ty * TMK + i];
+      }
+      if constexpr (TNN % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < TNN; q += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(&Bs[buf][r][tx * TNN + q]);
+          b[q] = make_float2(v.x, v.y);
+          b[q + 1] = make_float2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < TNN; ++q) b[q] = Bs[buf][r][tx * TNN + q];
+      }
 #pragma unroll
       for (int i = 0; i < TMK; ++i)
 #pragma unroll
-        for (int j = 0; j < TNN; ++j) {
-          acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
-          acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
+        for (int q = 0; q < TNN; ++q) {   // conj(a) * b
+          acc[i][q].x = fmaf(a[i].x, b[q].x, fmaf(a[i].y, b[q].y, acc[i][q].x));
+          acc[i][q].y = fmaf(a[i].x, b[q].y, fmaf(-a[i].y, b[q].x, acc[i][q].y));
         }
     }
-    __syncthreads();
   }
   float2* out = part + (int64_t)blockIdx.z * K * N;
 #pragma unroll
   for (int i = 0; i < TMK; ++i)
 #pragma unroll
-    for (int j = 0; j < TNN; ++j) {
-      const int64_t k = k0 + ty * TMK + i, n = n0 + tx * TNN + j;
-      if (k < K && n < N) out[k * N + n] = acc[i][j];
+    for (int q = 0; q < TNN; ++q) {
+      const int64_t k = k0 + ty * TMK + i, n = n0 + tx * TNN + q;
+      if (k < K && n < N) out[k * N + n] = acc[i][q];
     }
 }
 
@@ -523,7 +594,7 @@ __global__ void __launch_bounds__(kT) gate_accum_kernel(const int32_t* __restric
 }
 
 struct BwdLayout {
-  uint64_t tab, hdr, sites, sgrad, ckpt, lb, rr, gpart, bpart, evgrad, total;
+  uint64_t tab, hdr, sites, sconj, sgrad, ckpt, lb, rr, gpart, bpart, evgrad, total;
 };
 
 // Every step output is kept (no recomputation in the reverse sweep) when all of them fit in
@@ -545,6 +616,7 @@ BwdLayout bwd_layout(const qfx_plan* p) {
   L.tab = o; o += table_bytes(p);   // the plan's tables, copied in by every call
   L.hdr = o; o += a256((uint64_t)p->n * 8 + 16);
   L.sites = o; o += a256((uint64_t)p->site_total * 8);
+  L.sconj = o; o += a256((uint64_t)p->site_total * 8);
   L.sgrad = o; o += a256((uint64_t)p->site_total * 8);
   if (full_store(p)) {   // ckpt holds the output of every step
     L.ckpt = o; o += (uint64_t)p->n * B;
@@ -637,10 +709,28 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
   const int64_t n_items = (slice_end - slice_begin) * n_batch;
   auto step_fwd = [&](int i, const char* in, char* out) -> int {
     const Step& sp = p->steps[i];
-    const int v = pick_variant(sp.N, sp.Sd);
+    const int v = fill_variant(pick_variant(sp.N, sp.Sd), sp.N, sp.P * sp.Sd, 1);
     return launch_step(site_ptr(sp.site), 0, in, 0, out, 0, sp.P, sp.K, sp.N, sp.NL, sp.Sd, 1, v,
                        QFX_PREC_FP32_SIMT, st);
   };
+
+  // reverse steps with NL = N run on the step tile with the conjugate transpose of their
+  // site matrix (conj_transpose_kernel, once per item); the others on rstep_kernel
+  ConjTable ctab{};
+  std::vector<char> use_conj(p->steps.size(), 0);
+  int64_t conj_tiles = 0;
+  for (size_t i = 1; i < p->steps.size() && ctab.count < kConjMax; ++i) {
+    const Step& sp = p->steps[i];
+    const FoldSite& fs = p->sites[sp.site];
+    if (sp.NL != sp.N || fs.size != sp.K * sp.N || sp.K > 0x7fffffff || sp.N > 0x7fffffff) continue;
+    use_conj[i] = 1;
+    ctab.off[ctab.count] = fs.offset;
+    ctab.K[ctab.count] = (int32_t)sp.K;
+    ctab.N[ctab.count] = (int32_t)sp.N;
+    ++ctab.count;
+    conj_tiles = std::max(conj_tiles, ((sp.K + 31) / 32) * ((sp.N + 31) / 32));
+  }
+  float2* sconj = (float2*)(ws + Lw.sconj);
 
   for (int64_t item = 0; item < n_items; ++item) {
     const int64_t b = item % n_batch, sid = slice_begin + item / n_batch;
@@ -650,6 +740,11 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
                           item, 1, hdr, 0, sites, 0, 0, st);
     if (!err) err = launch_scale(t, n, max_site, 1, hdr, 0, sites, 0, 0, st);
     if (err) return cuda_fail(err, "qfx_amplitudes_backward: fold");
+    if (ctab.count > 0) {
+      conj_transpose_kernel<<<dim3((unsigned)conj_tiles, (unsigned)ctab.count), kT, 0, st>>>(
+          (const float2*)sites, sconj, ctab);
+      count_launch();
+    }
     // forward sweep, keeping every step's output (full) or the boundary at the start of
     // every line
     const char* cur = site_ptr(p->steps[0].site);
@@ -684,8 +779,16 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
       const int64_t KN = sp.K * sp.N;
       reduce_chunks_kernel<<<(unsigned)((KN * 32 + kT - 1) / kT), kT, 0, st>>>(part, gg.chunks, KN, gdst);
       float2* Rnext = (float2*)rr(rsel ^ 1);
-      launch_rstep((const float2*)site_ptr(sp.site), Rcur, Rnext, sp.P, sp.K, sp.N, sp.NL, sp.Sd, st);
-      count_launch(3);
+      if (use_conj[i]) {
+        const int v = fill_variant(pick_variant(sp.K, sp.Sd), sp.K, J, 1);
+        const int err2 = launch_step(sconj + p->sites[sp.site].offset, 0, Rcur, 0, Rnext, 0, sp.P, sp.N, sp.K,
+                                     sp.K, sp.Sd, 1, v, QFX_PREC_FP32_SIMT, st);
+        if (err2) return cuda_fail(err2, "qfx_amplitudes_backward: reverse step");
+        count_launch(2);
+      } else {
+        launch_rstep((const float2*)site_ptr(sp.site), Rcur, Rnext, sp.P, sp.K, sp.N, sp.NL, sp.Sd, st);
+        count_launch(3);
+      }
       rsel ^= 1;
       Rcur = Rnext;
       cudaError_t e2 = cudaGetLastError();

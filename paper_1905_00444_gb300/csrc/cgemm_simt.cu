@@ -98,6 +98,7 @@ int simt_prepare_attributes() {
 #define QFX_ATTR(V, BM, BJ, TM, TJ, KM, ST) \
   if (int e = ensure_attr<BM, BJ, TM, TJ, KM, ST>()) return e;
   QFX_SIMT_VARIANTS(QFX_ATTR)
+  QFX_SIMT_FILL_VARIANTS(QFX_ATTR)
 #undef QFX_ATTR
   return 0;
 }
@@ -108,6 +109,37 @@ int pick_variant(int64_t N, int64_t Sd) {
   return base + ((Sd % 2) ? 5 : 0);
 }
 
+int num_sms() {
+  static int n[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64) dev = 63;
+  if (!n[dev]) cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev);
+  return n[dev] > 0 ? n[dev] : 1;
+}
+
+// Variants 0..9 keep their tile when its grid gives at least two CTAs per SM; otherwise the
+// fill variant of the same row range (QFX_SIMT_FILL_VARIANTS) when it gives more CTAs.
+// Both sum every output's k terms in the same order, so the choice never changes a result.
+int fill_variant(int variant, int64_t N, int64_t J, int batch) {
+  static const int bm[10] = {128, 64, 32, 16, 8, 128, 64, 32, 16, 8};
+  static const int bj[10] = {128, 256, 512, 512, 512, 128, 256, 512, 512, 512};
+  static const int fill[10] = {20, 20, 21, 22, 23, 25, 25, 26, 27, 28};
+  static const int fbm[10] = {64, 64, 32, 16, 8, 64, 64, 32, 16, 8};
+  static const int fbj[10] = {64, 64, 128, 256, 256, 64, 64, 128, 256, 256};
+  if (variant < 0 || variant > 9 || batch < 1) return variant;
+  const int64_t blocks = ((N + bm[variant] - 1) / bm[variant]) * ((J + bj[variant] - 1) / bj[variant]) * batch;
+  if (blocks >= 2 * (int64_t)num_sms()) return variant;
+  const int64_t fb = ((N + fbm[variant] - 1) / fbm[variant]) * ((J + fbj[variant] - 1) / fbj[variant]) * batch;
+  return fb > blocks ? fill[variant] : variant;
+}
+
+bool simt_variant_valid(int variant, int64_t Sd) {
+  const bool jmode = (variant >= 0 && variant < 5) || (variant >= 20 && variant < 25);
+  const bool kmode = (variant >= 5 && variant < 10) || (variant >= 25 && variant < 30 && variant != 29);
+  return (jmode && Sd % 2 == 0) || kmode;
+}
+
 int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride, void* C,
                 int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
                 int batch, int variant, int precision, void* stream, int beta) {
@@ -115,12 +147,13 @@ int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride
   StepArgs a{(const float2*)S, s_stride, (const float2*)B, b_stride, (float2*)C, c_stride,
              P, K, N, NL, Sd, P * Sd, beta};
   if (variant < 0) variant = pick_variant(N, Sd);
-  if (variant < 5 && (Sd % 2)) return (int)cudaErrorInvalidValue;  // JMODE needs even Sd
+  if (!simt_variant_valid(variant, Sd)) return (int)cudaErrorInvalidValue;  // JMODE needs even Sd
   cudaStream_t st = (cudaStream_t)stream;
   switch (variant) {
 #define QFX_CASE(V, BM, BJ, TM, TJ, KM, ST) \
   case V: return launch_cfg<BM, BJ, TM, TJ, KM, ST>(a, batch, st);
     QFX_SIMT_VARIANTS(QFX_CASE)
+    QFX_SIMT_FILL_VARIANTS(QFX_CASE)
 #undef QFX_CASE
     default: return (int)cudaErrorInvalidValue;
   }

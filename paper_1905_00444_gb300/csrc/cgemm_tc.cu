@@ -638,15 +638,6 @@ __global__ void __launch_bounds__(128) split_site_kernel(const float2* __restric
   }
 }
 
-int num_sms() {
-  static int n[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 64) dev = 63;
-  if (!n[dev]) cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev);
-  return n[dev] > 0 ? n[dev] : 1;
-}
-
 // Tensor map over B viewed as (s, k, p, item) 8-byte elements, box (box_s, KS, box_p, 1)
 // = one 128-row, KS-deep k-stage of a tile.  False if the shape does not allow it (the
 // box's inner extent must be at least 16 bytes: Sd >= 2; tiles must not straddle p

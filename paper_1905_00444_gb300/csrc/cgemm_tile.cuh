@@ -222,5 +222,19 @@ __device__ __forceinline__ void cgemm_tile(const StepArgs& a, int64_t tile, int6
   X(8, 16, 512, 8, 4, true, 3)             \
   X(9, 8, 512, 8, 2, true, 3)
 
+// Fill variants: the same tiles with a quarter (or half) of the outputs per CTA, 4 x 4 (or
+// 4 x 2) per thread, for grids that the tiles above would leave with fewer CTAs than two
+// per SM (fill_variant picks them at launch time; the batch scheduler keeps 0..9).
+// Variant 20 + v serves 0..4 (21 for 1 and 2 ...), 25 + v the KMODE ones.
+#define QFX_SIMT_FILL_VARIANTS(X)          \
+  X(20, 64, 64, 4, 4, false, 3)            \
+  X(21, 32, 128, 4, 4, false, 3)           \
+  X(22, 16, 256, 4, 4, false, 3)           \
+  X(23, 8, 256, 4, 2, false, 3)            \
+  X(25, 64, 64, 4, 4, true, 3)             \
+  X(26, 32, 128, 4, 4, true, 3)            \
+  X(27, 16, 256, 4, 4, true, 3)            \
+  X(28, 8, 256, 4, 2, true, 3)
+
 }  // namespace simt
 }  // namespace qfx

@@ -201,6 +201,11 @@ int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride
                 int64_t c_stride, int64_t P, int64_t K, int64_t N, int64_t NL, int64_t Sd,
                 int batch, int variant, int precision, void* stream, int beta = 0);
 int pick_variant(int64_t N, int64_t Sd);
+// Per-step launches: variant 0..9 -> its fill variant (20..28) when the grid of `batch`
+// entries would leave SMs idle (same results); any other variant unchanged.
+int fill_variant(int variant, int64_t N, int64_t J, int batch);
+bool simt_variant_valid(int variant, int64_t Sd);
+int num_sms();
 // C[b][e] = sum over c < parts of part[b][c][e] (e < out; complex FP32 in and out), per batch
 // entry b < batch, in FP64 and a fixed order; strides in float2 units.
 int launch_reduce_parts(const void* part, int64_t part_stride, int64_t parts, int64_t out, void* C,

@@ -246,7 +246,7 @@ static qfx_status exec_tree(const qfx_plan* p, const DeviceTables& t, const uint
           char* blk = items + (uint64_t)gi * ib;
           err = launch_step(blk + nd.offA2, nd.chunk * nd.N, blk + nd.offB2, nd.chunk * nd.Sd,
                             blk + L.simage, nd.N * nd.Sd, 1, nd.chunk, nd.N, nd.NL, nd.Sd, nd.parts,
-                            nd.variant, QFX_PREC_FP32_SIMT, st, 0);
+                            fill_variant(nd.variant, nd.N, nd.Sd, nd.parts), QFX_PREC_FP32_SIMT, st, 0);
         }
         if (!err)
           err = launch_reduce_parts(items + L.simage, (int64_t)(ib / 8), nd.parts, nd.N * nd.Sd,
@@ -262,8 +262,9 @@ static qfx_status exec_tree(const qfx_plan* p, const DeviceTables& t, const uint
                                items + L.simage, (int64_t)ib, st, p->tc_flags | (k0 > 0 ? kTcBeta : 0));
         else
           err = launch_step(Sk, (int64_t)(ib / 8), Bk, (int64_t)(ib / 8), items + nd.offC,
-                            (int64_t)(ib / 8), nd.P, nd.chunk, nd.N, nd.NL, nd.Sd, g, nd.variant,
-                            QFX_PREC_FP32_SIMT, st, k0 > 0 ? 1 : 0);
+                            (int64_t)(ib / 8), nd.P, nd.chunk, nd.N, nd.NL, nd.Sd, g,
+                            fill_variant(nd.variant, nd.N, nd.P * nd.Sd, g), QFX_PREC_FP32_SIMT, st,
+                            k0 > 0 ? 1 : 0);
       }
       profile_end(st, slot, (int)i, nd.variant, 0, nd.flops * g, nd.bytes * g);
       if (err) return cuda_fail(err, "contraction step kernel");
@@ -321,7 +322,8 @@ qfx_status exec_amplitudes(const qfx_plan* p, const DeviceTables& t, const uint6
                              (int64_t)ib, st, p->tc_flags);
       else
         err = launch_step(S, (int64_t)(ib / 8), B, (int64_t)(ib / 8), C, (int64_t)(ib / 8), sp.P,
-                          sp.K, sp.N, sp.NL, sp.Sd, g, sp.variant, p->precision, st);
+                          sp.K, sp.N, sp.NL, sp.Sd, g, fill_variant(sp.variant, sp.N, sp.P * sp.Sd, g),
+                          p->precision, st);
       profile_end(st, slot, i, sp.variant, 0, sp.flops * g, sp.bytes * g);
       if (err) return cuda_fail(err, "contraction step kernel");
     }
@@ -428,12 +430,13 @@ extern "C" qfx_status qfx_contract_step(const void* S, const void* B, void* C, i
   if (variant == 99 && tc) { flags = kTcWithhold; variant = -1; }
   if (variant == 12 && tc) { flags = kTcFast; variant = -1; }
   if (variant == 13 && tc) { flags = kTcNoTma; variant = -1; }
-  if (variant >= 10) return fail(QFX_EINVAL, "qfx_contract_step: unknown variant");
-  if (variant >= 0 && variant < 5 && Sd % 2)
-    return fail(QFX_EINVAL, "qfx_contract_step: variants 0-4 need an even Sd");
+  if (variant >= 0 && !simt_variant_valid(variant, 2))
+    return fail(QFX_EINVAL, "qfx_contract_step: unknown variant");
+  if (variant >= 0 && !simt_variant_valid(variant, Sd))
+    return fail(QFX_EINVAL, "qfx_contract_step: variants 0-4 and 20-23 need an even Sd");
   int slot;
   profile_begin(stream, &slot);
-  int v = variant < 0 ? pick_variant(N, Sd) : variant;
+  int v = variant < 0 ? fill_variant(pick_variant(N, Sd), N, P * Sd, 1) : variant;
   int err;
   if (tc) {
     v = precision == QFX_PREC_C3M_BF16X3 ? kVariantTcBf16

@@ -220,12 +220,15 @@ def test_7x7x32_slicing_invariance(qfx):
 
 # --- single operations: contraction step and permute --------------------------------
 
-@pytest.mark.parametrize("variant", list(range(10)))
+FILL = {0: 20, 1: 20, 2: 21, 3: 22, 4: 23, 5: 25, 6: 25, 7: 26, 8: 27, 9: 28}
+
+
+@pytest.mark.parametrize("variant", list(range(10)) + [20, 21, 22, 23, 25, 26, 27, 28])
 @pytest.mark.parametrize("shape", [(3, 37, 130, 130, 6), (2, 9, 70, 35, 34), (5, 16, 16, 16, 1),
                                    (1, 1, 3, 3, 10), (7, 130, 8, 4, 2), (1, 300, 33, 33, 1)])
 def test_contract_step_variants(qfx, variant, shape):
     P, K, N, NL, Sd = shape
-    if variant < 5 and Sd % 2:
+    if (variant < 5 or 20 <= variant < 25) and Sd % 2:
         pytest.skip("JMODE variants need even Sd")
     S = ri.random_complex((K, N), seed=1)
     B = ri.random_complex((P, K, Sd), seed=2)
@@ -243,6 +246,25 @@ def test_contract_step_variants(qfx, variant, shape):
     assert np.all(np.abs(got - want) <= 1e-6 * scale)
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("shape", [(8, 64, 64, 64, 4096), (3, 37, 130, 130, 6), (4096, 64, 16, 8, 1),
+                                   (2, 9, 70, 35, 34)])
+def test_fill_variants_bit_identical(qfx, shape):
+    # the fill tiles (4 x 4 outputs per thread) sum every output's k terms in the order of
+    # the tiles they stand in for, so per-step launches may swap them in freely
+    P, K, N, NL, Sd = shape
+    S = torch.from_numpy(ri.random_complex(K * N, seed=4)).cuda()
+    B = torch.from_numpy(ri.random_complex(P * K * Sd, seed=5)).cuda()
+    for v, f in FILL.items():
+        if v < 5 and Sd % 2:
+            continue
+        a = qfx.contract_step(S, B, P, K, N, NL, Sd, variant=v).cpu().numpy()
+        b = qfx.contract_step(S, B, P, K, N, NL, Sd, variant=f).cpu().numpy()
+        np.testing.assert_array_equal(a, b)
+    auto = qfx.contract_step(S, B, P, K, N, NL, Sd).cpu().numpy()
+    np.testing.assert_array_equal(auto, a)
+    qfx.sync()
 
 
 @pytest.mark.parametrize("case", [((4, 5, 6), (2, 0, 1)), ((33, 65), (1, 0)),
