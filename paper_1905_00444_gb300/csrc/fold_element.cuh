@@ -8,23 +8,26 @@
 namespace qfx {
 namespace foldk {
 
+// Complex FP64 products with the rounding steps written out (one product, one fused
+// multiply-add per part), so that every caller rounds exactly alike whatever the compiler
+// would contract in its context: the group fold below relies on it to reproduce the
+// per-element fold bit for bit.
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
-  return make_double2(a.x + b.x, a.y + b.y);
+  return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
 }
 
-// Element i of site `st` for slice `sid` and the output bitstring x1w (its words; qubit q
-// is bit q % 64 of word q / 64): FP64 evolution of the
-// site's 2-vector through its time line, rounded once to complex64.  A diagonal two-qubit
-// gate reads one bit of the bond value (projector on q0, diagonal on q1); a general one
-// reads two, k = 2*o0 + i0 (|o0><i0| on q0, the 2x2 block B_k of the gate on q1).
-__device__ __forceinline__ float2 fold_element(const FoldSite& st, const FoldEvent* __restrict__ events,
-                                               const double* __restrict__ mats,
-                                               const CutDev* __restrict__ cuts, int n_cuts,
-                                               const uint64_t* __restrict__ x1w, int64_t sid,
-                                               int64_t i) {
+// Bond values (up, left, right, down, each plus its cut offset for slice `sid`) and the x
+// value of element i of site `st`; the output bitstring x1w is given as words (qubit q is
+// bit q % 64 of word q / 64).
+struct FoldCoord {
+  uint64_t val[4];
+  int xv;
+};
+__device__ __forceinline__ FoldCoord fold_coord(const FoldSite& st, const CutDev* __restrict__ cuts, int n_cuts,
+                                                const uint64_t* __restrict__ x1w, int64_t sid, int64_t i) {
   int64_t off[4] = {0, 0, 0, 0};
   for (int c = 0; c < n_cuts; ++c) {
     const CutDev cd = cuts[c];
@@ -39,48 +42,63 @@ __device__ __forceinline__ float2 fold_element(const FoldSite& st, const FoldEve
   const int64_t vx = r % st.dim[2]; r /= st.dim[2];
   const int64_t vl = r % st.dim[1]; r /= st.dim[1];
   const int64_t vu = r;
-  const uint64_t val0 = (uint64_t)(vu + off[0]), val1 = (uint64_t)(vl + off[1]);
-  const uint64_t val2 = (uint64_t)(vr + off[2]), val3 = (uint64_t)(vd + off[3]);
-  const int xv = st.x_open ? (int)vx : (int)((x1w[st.qubit >> 6] >> (st.qubit & 63)) & 1ull);
+  FoldCoord fc;
+  fc.val[0] = (uint64_t)(vu + off[0]);
+  fc.val[1] = (uint64_t)(vl + off[1]);
+  fc.val[2] = (uint64_t)(vr + off[2]);
+  fc.val[3] = (uint64_t)(vd + off[3]);
+  fc.xv = st.x_open ? (int)vx : (int)((x1w[st.qubit >> 6] >> (st.qubit & 63)) & 1ull);
+  return fc;
+}
+
+// The bond bits an event reads for an element (0 for a one-qubit gate): one bit for a
+// diagonal two-qubit gate, two (k = 2*o0 + i0) for a general one.
+__device__ __forceinline__ int event_key(const FoldEvent& ev, const FoldCoord& fc) {
+  if (ev.kind == EV_GATE) return 0;
+  const uint64_t bv = ev.slot == 0 ? fc.val[0] : ev.slot == 1 ? fc.val[1] : ev.slot == 2 ? fc.val[2] : fc.val[3];
+  const uint64_t mask = (ev.kind == EV_PROJ || ev.kind == EV_DIAG) ? 1ull : 3ull;
+  return (int)((bv >> ev.bit) & mask);
+}
+
+// One event on the site's 2-vector (v0, v1), for bond bits k: a one-qubit gate; the
+// projector on q0 or the diagonal on q1 of a diagonal two-qubit gate; |o0><i0| on q0 or
+// the 2x2 block B_k on q1 of a general one.
+__device__ __forceinline__ void apply_event(const FoldEvent& ev, const double* __restrict__ mats, int k,
+                                            double2& v0, double2& v1) {
+  const double* m = mats + 8 * (int64_t)ev.mat;
+  if (ev.kind == EV_GATE || ev.kind == EV_BLOCK) {
+    const double* b = ev.kind == EV_GATE ? m : m + 8 * k;
+    const double2 n0 = cadd(cmul(make_double2(b[0], b[1]), v0), cmul(make_double2(b[2], b[3]), v1));
+    const double2 n1 = cadd(cmul(make_double2(b[4], b[5]), v0), cmul(make_double2(b[6], b[7]), v1));
+    v0 = n0;
+    v1 = n1;
+  } else if (ev.kind == EV_PROJ) {
+    if (k) v0 = make_double2(0.0, 0.0);
+    else   v1 = make_double2(0.0, 0.0);
+  } else if (ev.kind == EV_DIAG) {
+    v0 = cmul(v0, make_double2(m[4 * k + 0], m[4 * k + 1]));
+    v1 = cmul(v1, make_double2(m[4 * k + 2], m[4 * k + 3]));
+  } else {   // EV_ELEM: |o0><i0|
+    const double2 src = (k & 1) ? v1 : v0;
+    v0 = (k >> 1) ? make_double2(0.0, 0.0) : src;
+    v1 = (k >> 1) ? src : make_double2(0.0, 0.0);
+  }
+}
+
+// Element i of site `st` for slice `sid`: FP64 evolution of the site's 2-vector through
+// its time line from |0>, rounded once to complex64.
+__device__ __forceinline__ float2 fold_element(const FoldSite& st, const FoldEvent* __restrict__ events,
+                                               const double* __restrict__ mats,
+                                               const CutDev* __restrict__ cuts, int n_cuts,
+                                               const uint64_t* __restrict__ x1w, int64_t sid,
+                                               int64_t i) {
+  const FoldCoord fc = fold_coord(st, cuts, n_cuts, x1w, sid, i);
   double2 v0 = make_double2(1.0, 0.0), v1 = make_double2(0.0, 0.0);
   for (int e = st.ev_begin; e < st.ev_end; ++e) {
     const FoldEvent ev = events[e];
-    const double* m = mats + 8 * (int64_t)ev.mat;
-    if (ev.kind == EV_GATE) {
-      const double2 g00 = make_double2(m[0], m[1]), g01 = make_double2(m[2], m[3]);
-      const double2 g10 = make_double2(m[4], m[5]), g11 = make_double2(m[6], m[7]);
-      const double2 n0 = cadd(cmul(g00, v0), cmul(g01, v1));
-      const double2 n1 = cadd(cmul(g10, v0), cmul(g11, v1));
-      v0 = n0;
-      v1 = n1;
-    } else {
-      const uint64_t bv = ev.slot == 0 ? val0 : ev.slot == 1 ? val1 : ev.slot == 2 ? val2 : val3;
-      if (ev.kind == EV_PROJ || ev.kind == EV_DIAG) {
-        const int k = (int)((bv >> ev.bit) & 1ull);
-        if (ev.kind == EV_PROJ) {
-          if (k) v0 = make_double2(0.0, 0.0);
-          else   v1 = make_double2(0.0, 0.0);
-        } else {
-          v0 = cmul(v0, make_double2(m[4 * k + 0], m[4 * k + 1]));
-          v1 = cmul(v1, make_double2(m[4 * k + 2], m[4 * k + 3]));
-        }
-      } else {
-        const int k = (int)((bv >> ev.bit) & 3ull);   // k = 2*o0 + i0
-        if (ev.kind == EV_ELEM) {                      // |o0><i0|
-          const double2 src = (k & 1) ? v1 : v0;
-          v0 = (k >> 1) ? make_double2(0.0, 0.0) : src;
-          v1 = (k >> 1) ? src : make_double2(0.0, 0.0);
-        } else {                                       // B_k
-          const double* b = m + 8 * k;
-          const double2 n0 = cadd(cmul(make_double2(b[0], b[1]), v0), cmul(make_double2(b[2], b[3]), v1));
-          const double2 n1 = cadd(cmul(make_double2(b[4], b[5]), v0), cmul(make_double2(b[6], b[7]), v1));
-          v0 = n0;
-          v1 = n1;
-        }
-      }
-    }
+    apply_event(ev, mats, event_key(ev, fc), v0, v1);
   }
-  const double2 res = xv ? v1 : v0;
+  const double2 res = fc.xv ? v1 : v0;
   return make_float2((float)res.x, (float)res.y);
 }
 
