@@ -12,7 +12,11 @@
 //     multiplied;
 //   - cuts: while the largest intermediate exceeds the cap, halve the bond of the largest
 //     intermediates whose halving gives the lowest largest intermediate, then the least
-//     total work (slices x flops per slice), rebuilding the order for each trial.
+//     total work (slices x flops per slice), rebuilding the order for each trial; then
+//     double back, one at a time, the halvings that the later ones made unnecessary, as
+//     long as the total work drops;
+//   - every order is the best of greedy runs with small and with larger random
+//     perturbations of the score (the larger ones only where they keep the largest tensor).
 // Each tree node is one TTGT contraction (Sec. III.E) run by the same GEMM kernel as the
 // line sweep, C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] B[p][k][s] with NL = N: the larger
 // operand is B; when its shared legs are adjacent it is used in place (P = legs before,
@@ -43,7 +47,8 @@ struct Pair { int a, b; };
 // the largest tensor (elements, saturating) and the Eq. 1 flops of the tree.
 static void greedy_tree_seed(const std::vector<std::vector<int>>& site_legs,
                              const std::function<int64_t(int)>& dim, uint64_t seed,
-                             std::vector<Pair>& pairs, int64_t* peak, double* flops) {
+                             std::vector<Pair>& pairs, int64_t* peak, double* flops,
+                             double noise = 0.02) {
   const int n = (int)site_legs.size();
   std::vector<std::vector<int>> legs(site_legs);
   std::vector<double> lsz;   // log2 size per tensor
@@ -83,7 +88,7 @@ static void greedy_tree_seed(const std::vector<std::vector<int>>& site_legs,
         if (seed) {   // a small deterministic perturbation: another tie-break per seed
           uint64_t h = seed * 0x9E3779B97F4A7C15ull ^ ((uint64_t)alive[i] << 32 ^ (uint64_t)alive[j]);
           h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 29;
-          score += 0.02 * (double)(h >> 11) / 9007199254740992.0;
+          score += noise * (double)(h >> 11) / 9007199254740992.0;
         }
         if (bi < 0 || score < best - 1e-9 || (std::fabs(score - best) <= 1e-9 && out < best_out - 1e-9)) {
           bi = (int)i; bj = (int)j; best = score; best_out = out;
@@ -137,10 +142,28 @@ static void greedy_tree(const std::vector<std::vector<int>>& site_legs,
   }
 }
 
+// Polish of an order: greedy orders with larger perturbations of the score (up to 0.25,
+// 0.5 or 1 in log2 units, `seeds` of them, deterministic) may find fewer flops for the
+// same cuts; one is kept when its largest tensor is no larger than the order's.
+constexpr int kPolishSeeds = 48;
+static void polish_tree(const std::vector<std::vector<int>>& site_legs, const std::function<int64_t(int)>& dim,
+                        std::vector<Pair>& pairs, int64_t* peak, double* flops, int seeds = kPolishSeeds) {
+  static const double amp[3] = {0.25, 0.5, 1.0};
+  for (int sd = 0; sd < seeds; ++sd) {
+    std::vector<Pair> pp;
+    int64_t pk;
+    double fl;
+    greedy_tree_seed(site_legs, dim, (uint64_t)(1000 + sd), pp, &pk, &fl, amp[sd % 3]);
+    if (pk <= *peak && fl < *flops) { pairs.swap(pp); *peak = pk; *flops = fl; }
+  }
+}
+
 bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges,
                      std::vector<int64_t>& edim, std::vector<int>& cut_edges, uint64_t cap_elems,
                      const std::vector<int64_t>& full, std::string* err) {
   auto dimf = [&](int x) -> int64_t { return x < 0 ? 2 : edim[x]; };
+  const std::vector<int64_t> entry = edim;          // the caller's (forced) cuts stay
+  const size_t n_entry = cut_edges.size();
   std::vector<Pair> pairs;
   int64_t peak;
   double flops;
@@ -181,6 +204,7 @@ bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges
       int64_t pk;
       double fl;
       greedy_tree(site_legs, dimf, pp, &pk, &fl);
+      polish_tree(site_legs, dimf, pp, &pk, &fl);
       double slices = 1;
       for (int e = 0; e < n_edges; ++e) slices *= (double)full[e] / (double)edim[e];
       const double work = fl * slices;
@@ -192,6 +216,39 @@ bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges
     edim[best] /= 2;
     if (std::find(cut_edges.begin(), cut_edges.end(), best) == cut_edges.end()) cut_edges.push_back(best);
     greedy_tree(site_legs, dimf, pairs, &peak, &flops);
+    polish_tree(site_legs, dimf, pairs, &peak, &flops);
+  }
+  // undo halvings that later ones made unnecessary: double a bond this search cut back
+  // while some order still fits the cap with less total work, the largest gain first
+  if (cap_elems > 0) {
+    auto total_work = [&](double fl) {
+      double slices = 1;
+      for (int e = 0; e < n_edges; ++e) slices *= (double)full[e] / (double)edim[e];
+      return fl * slices;
+    };
+    double work = total_work(flops);
+    for (int pass = 0; pass < 64; ++pass) {
+      int best = -1;
+      double best_work = work;
+      for (int x : cut_edges) {
+        if (edim[x] >= entry[x]) continue;
+        edim[x] *= 2;
+        std::vector<Pair> pp;
+        int64_t pk;
+        double fl;
+        greedy_tree(site_legs, dimf, pp, &pk, &fl);
+        polish_tree(site_legs, dimf, pp, &pk, &fl);
+        const double w = total_work(fl);
+        if ((uint64_t)pk <= cap_elems && w < best_work) { best = x; best_work = w; }
+        edim[x] /= 2;
+      }
+      if (best < 0) break;
+      edim[best] *= 2;
+      work = best_work;
+    }
+    cut_edges.erase(std::remove_if(cut_edges.begin() + (std::ptrdiff_t)n_entry, cut_edges.end(),
+                                   [&](int x) { return edim[x] >= entry[x]; }),
+                    cut_edges.end());
   }
   return true;
 }
@@ -245,6 +302,7 @@ bool build_tree_nodes(const std::vector<std::vector<int>>& site_legs, const std:
   int64_t peak;
   double flops;
   greedy_tree(site_legs, dimf, pairs, &peak, &flops);
+  polish_tree(site_legs, dimf, pairs, &peak, &flops);
   *max_el = peak;
   std::vector<std::vector<int>> legs(site_legs);
   auto elems = [&](const std::vector<int>& l) {

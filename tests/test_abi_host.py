@@ -440,19 +440,22 @@ def test_tree_plans_steps_cap_and_slices():
 
 
 def test_tree_plan_split_k_root():
-    """8x8x(1+32+1) at 8 GiB: the root contracts K = 2^21 into 8x8 outputs; it runs as 2048
-    side-by-side chunks (FP32, whatever the plan's precision) whose partial products fit the
-    item's scratch."""
-    c = qfx.Circuit(ri.rqc(8, 8, 32, seed=0))
-    for prec in ("fp32", "bf16x3"):
-        tree = qfx.Plan(c, n_open=6, max_intermediate_bytes=8 << 30, family="tree", precision=prec)
-        root = tree.steps[-1]
-        assert (root["K"], root["N"] * root["Sd"], root["parts"]) == (1 << 21, 64, 2048)
-        assert root["variant"] < 10
-        for s in tree.steps:
-            if s["parts"]:
-                assert s["K"] == 1024 * s["parts"] and s["P"] * s["N"] * s["Sd"] <= 1 << 18
-        assert tree.workspace_bytes(1) >= 2048 * 64 * 8 + tree.stats["max_elements"] * 8
+    """Region plans at 8 GiB: the roots contract long K into 64 outputs; they run as
+    side-by-side 1024-long chunks (FP32, whatever the plan's precision) whose partial
+    products fit the item's scratch."""
+    for rows, cols, depth in ((7, 7, 40), (8, 8, 32)):
+        c = qfx.Circuit(ri.rqc(rows, cols, depth, seed=0))
+        for prec in ("fp32", "bf16x3"):
+            tree = qfx.Plan(c, n_open=6, max_intermediate_bytes=8 << 30, family="tree", precision=prec)
+            root = tree.steps[-1]
+            assert root["N"] * root["Sd"] == 64 and root["K"] >= 4096 and root["parts"] == root["K"] // 1024
+            assert root["variant"] < 10
+            parts = 0
+            for s in tree.steps:
+                if s["parts"]:
+                    assert s["K"] == 1024 * s["parts"] and s["P"] * s["N"] * s["Sd"] <= 1 << 18
+                    parts = max(parts, s["parts"] * s["P"] * s["N"] * s["Sd"])
+            assert tree.workspace_bytes(1) >= parts * 8 + tree.stats["max_elements"] * 8
 
 
 def test_tree_plan_forced_cuts_keep_the_slice_numbering():
