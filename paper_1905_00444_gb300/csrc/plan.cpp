@@ -252,9 +252,10 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
     SimResult sim = simulate(geo, p->order, slots, edim, is_open);
     if (!sim.ok) return qfx::fail(QFX_EPLAN, "planner: " + sim.err);
     const uint64_t cap = o->max_intermediate_bytes;
+    int tree_base = 0;   // seed base of the tree planner's chosen order
     if (tree) {
       std::string terr;
-      if (!qfx::tree_cut_search(site_legs, E, edim, cut_edges, cap / 8, full, &terr))
+      if (!qfx::tree_cut_search(site_legs, E, edim, cut_edges, cap / 8, full, &tree_base, &terr))
         return qfx::fail(QFX_EPLAN, terr);
       sim = simulate(geo, p->order, slots, edim, is_open);   // intro order of the open sites
       if (!sim.ok) return qfx::fail(QFX_EPLAN, "planner: " + sim.err);
@@ -434,7 +435,7 @@ extern "C" qfx_status qfx_plan_create(const qfx_circuit* c, const qfx_plan_opts*
       uint64_t arena_bytes = 0;
       int64_t max_el = 1;
       std::string terr;
-      if (!qfx::build_tree_nodes(site_legs, edim, site_off, arena, p->tree, &arena_bytes, &root,
+      if (!qfx::build_tree_nodes(site_legs, edim, tree_base, site_off, arena, p->tree, &arena_bytes, &root,
                                  &max_el, &terr))
         return qfx::fail(QFX_EPLAN, terr);
       if (max_el > kMaxPlanElements)

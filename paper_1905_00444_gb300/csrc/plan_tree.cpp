@@ -16,7 +16,8 @@
 //     double back, one at a time, the halvings that the later ones made unnecessary, as
 //     long as the total work drops;
 //   - every order is the best of greedy runs with small and with larger random
-//     perturbations of the score (the larger ones only where they keep the largest tensor).
+//     perturbations of the score (the larger ones only where they keep the largest tensor);
+//   - the whole search runs from several seed bases and keeps the least total work.
 // Each tree node is one TTGT contraction (Sec. III.E) run by the same GEMM kernel as the
 // line sweep, C[nh][p][nl][s] = sum_k S[k][nh*NL + nl] B[p][k][s] with NL = N: the larger
 // operand is B; when its shared legs are adjacent it is used in place (P = legs before,
@@ -44,22 +45,35 @@ struct Pair { int a, b; };
 
 // Greedy contraction order of the network given each site's legs and the leg dims.
 // Fills `pairs` (tensor ids; intermediates numbered from n in creation order) and returns
-// the largest tensor (elements, saturating) and the Eq. 1 flops of the tree.
+// the largest tensor (elements, saturating) and the Eq. 1 flops of the tree.  Every bond
+// joins two tensors, so the candidate pairs of a step are found through the bonds of the
+// live tensors (owner[x] = its two endpoints), not among all pairs.
 static void greedy_tree_seed(const std::vector<std::vector<int>>& site_legs,
                              const std::function<int64_t(int)>& dim, uint64_t seed,
                              std::vector<Pair>& pairs, int64_t* peak, double* flops,
                              double noise = 0.02) {
   const int n = (int)site_legs.size();
   std::vector<std::vector<int>> legs(site_legs);
+  legs.reserve(2 * (size_t)n);
+  int maxleg = -1;
+  for (const auto& l : site_legs)
+    for (int x : l) maxleg = std::max(maxleg, x);
+  std::vector<double> ld(maxleg + 1);   // log2 dim per bond (open legs: 1)
+  std::vector<int> own0(maxleg + 1, -1), own1(maxleg + 1, -1);
+  for (int x = 0; x <= maxleg; ++x) ld[x] = std::log2((double)dim(x));
+  auto ldim = [&](int x) { return x < 0 ? 1.0 : ld[x]; };
+  for (int t = 0; t < n; ++t)
+    for (int x : legs[t])
+      if (x >= 0) (own0[x] < 0 ? own0[x] : own1[x]) = t;
+  auto other = [&](int x, int t) { return own0[x] == t ? own1[x] : own0[x]; };
   std::vector<double> lsz;   // log2 size per tensor
-  auto lsize = [&](const std::vector<int>& l) {
-    double s = 0;
-    for (int x : l) s += std::log2((double)dim(x));
-    return s;
-  };
-  for (auto& l : legs) lsz.push_back(lsize(l));
-  std::vector<int> alive(n);
-  for (int i = 0; i < n; ++i) alive[i] = i;
+  for (auto& l : legs) {
+    double sz = 0;
+    for (int x : l) sz += ldim(x);
+    lsz.push_back(sz);
+  }
+  std::vector<char> alive(n, 1);
+  int n_alive = n;
   *peak = 1;
   for (auto& l : legs) {
     int64_t e = 1;
@@ -68,61 +82,69 @@ static void greedy_tree_seed(const std::vector<std::vector<int>>& site_legs,
   }
   *flops = 0;
   pairs.clear();
-  while (alive.size() > 1) {
-    int bi = -1, bj = -1;
+  while (n_alive > 1) {
+    int ta = -1, tb = -1;
     double best = 0, best_out = 0;
-    for (size_t i = 0; i < alive.size(); ++i)
-      for (size_t j = i + 1; j < alive.size(); ++j) {
-        const auto& la = legs[alive[i]];
-        const auto& lb = legs[alive[j]];
+    for (int t = 0; t < (int)legs.size(); ++t) {
+      if (!alive[t]) continue;
+      for (int x : legs[t]) {
+        if (x < 0) continue;
+        const int u = other(x, t);
+        if (u < t || !alive[u]) continue;   // each pair from its lower id
         double shared = 0;
-        bool conn = false;
-        for (int x : la)
-          if (std::find(lb.begin(), lb.end(), x) != lb.end()) {
-            conn = true;
-            shared += std::log2((double)dim(x));
-          }
-        if (!conn) continue;
-        const double out = lsz[alive[i]] + lsz[alive[j]] - 2 * shared;
-        double score = out - std::max(lsz[alive[i]], lsz[alive[j]]);
-        if (seed) {   // a small deterministic perturbation: another tie-break per seed
-          uint64_t h = seed * 0x9E3779B97F4A7C15ull ^ ((uint64_t)alive[i] << 32 ^ (uint64_t)alive[j]);
+        bool seen = false, first = true;   // evaluate the pair once: at its first shared bond
+        for (int y : legs[t]) {
+          if (y < 0 || other(y, t) != u) continue;
+          if (!seen && y != x) { first = false; break; }
+          seen = true;
+          shared += ldim(y);
+        }
+        if (!first) continue;
+        const double out = lsz[t] + lsz[u] - 2 * shared;
+        double score = out - std::max(lsz[t], lsz[u]);
+        if (seed) {   // a deterministic perturbation per seed
+          uint64_t h = seed * 0x9E3779B97F4A7C15ull ^ ((uint64_t)t << 32 ^ (uint64_t)u);
           h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 29;
           score += noise * (double)(h >> 11) / 9007199254740992.0;
         }
-        if (bi < 0 || score < best - 1e-9 || (std::fabs(score - best) <= 1e-9 && out < best_out - 1e-9)) {
-          bi = (int)i; bj = (int)j; best = score; best_out = out;
+        if (ta < 0 || score < best - 1e-9 || (std::fabs(score - best) <= 1e-9 && out < best_out - 1e-9)) {
+          ta = t; tb = u; best = score; best_out = out;
         }
       }
-    if (bi < 0) {   // nothing shares a bond: multiply the two smallest
-      std::vector<int> idx(alive.size());
-      for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
-      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return lsz[alive[x]] < lsz[alive[y]]; });
-      bi = std::min(idx[0], idx[1]);
-      bj = std::max(idx[0], idx[1]);
     }
-    const int ta = alive[bi], tb = alive[bj];
+    if (ta < 0) {   // nothing shares a bond: multiply the two smallest
+      for (int t = 0; t < (int)legs.size(); ++t) {
+        if (!alive[t]) continue;
+        if (ta < 0 || lsz[t] < lsz[ta]) { tb = ta; ta = t; }
+        else if (tb < 0 || lsz[t] < lsz[tb]) tb = t;
+      }
+      if (ta > tb) std::swap(ta, tb);
+    }
     std::vector<int> out;
-    int64_t k = 1, ea = 1, eb = 1;
+    int64_t k = 1, eo = 1;
     for (int x : legs[ta]) {
-      ea = tmul(ea, dim(x));
-      if (std::find(legs[tb].begin(), legs[tb].end(), x) != legs[tb].end()) k = tmul(k, dim(x));
+      if (x >= 0 && other(x, ta) == tb) k = tmul(k, dim(x));
       else out.push_back(x);
     }
-    for (int x : legs[tb]) {
-      eb = tmul(eb, dim(x));
-      if (std::find(legs[ta].begin(), legs[ta].end(), x) == legs[ta].end()) out.push_back(x);
-    }
-    int64_t eo = 1;
+    for (int x : legs[tb])
+      if (!(x >= 0 && other(x, tb) == ta)) out.push_back(x);
     for (int x : out) eo = tmul(eo, dim(x));
     *peak = std::max(*peak, eo);
     *flops += 8.0 * (double)eo * (double)k;
     pairs.push_back({ta, tb});
-    legs.push_back(out);
-    lsz.push_back(lsize(out));
-    alive.erase(alive.begin() + bj);
-    alive.erase(alive.begin() + bi);
-    alive.push_back((int)legs.size() - 1);
+    const int c = (int)legs.size();
+    for (int x : out)
+      if (x >= 0) {
+        if (own0[x] == ta || own0[x] == tb) own0[x] = c;
+        else own1[x] = c;
+      }
+    double sz = 0;
+    for (int x : out) sz += ldim(x);
+    legs.push_back(std::move(out));
+    lsz.push_back(sz);
+    alive[ta] = alive[tb] = 0;
+    alive.push_back(1);
+    --n_alive;
   }
 }
 
@@ -131,13 +153,13 @@ static void greedy_tree_seed(const std::vector<std::vector<int>>& site_legs,
 constexpr int kTreeSeeds = 8;
 static void greedy_tree(const std::vector<std::vector<int>>& site_legs,
                         const std::function<int64_t(int)>& dim, std::vector<Pair>& pairs,
-                        int64_t* peak, double* flops) {
+                        int64_t* peak, double* flops, uint64_t base) {
   greedy_tree_seed(site_legs, dim, 0, pairs, peak, flops);
   for (int sd = 1; sd <= kTreeSeeds; ++sd) {
     std::vector<Pair> pp;
     int64_t pk;
     double fl;
-    greedy_tree_seed(site_legs, dim, (uint64_t)sd, pp, &pk, &fl);
+    greedy_tree_seed(site_legs, dim, (uint64_t)sd + 16 * base, pp, &pk, &fl);
     if (pk < *peak || (pk == *peak && fl < *flops)) { pairs.swap(pp); *peak = pk; *flops = fl; }
   }
 }
@@ -147,27 +169,30 @@ static void greedy_tree(const std::vector<std::vector<int>>& site_legs,
 // same cuts; one is kept when its largest tensor is no larger than the order's.
 constexpr int kPolishSeeds = 48;
 static void polish_tree(const std::vector<std::vector<int>>& site_legs, const std::function<int64_t(int)>& dim,
-                        std::vector<Pair>& pairs, int64_t* peak, double* flops, int seeds = kPolishSeeds) {
+                        std::vector<Pair>& pairs, int64_t* peak, double* flops, uint64_t base) {
   static const double amp[3] = {0.25, 0.5, 1.0};
-  for (int sd = 0; sd < seeds; ++sd) {
+  for (int sd = 0; sd < kPolishSeeds; ++sd) {
     std::vector<Pair> pp;
     int64_t pk;
     double fl;
-    greedy_tree_seed(site_legs, dim, (uint64_t)(1000 + sd), pp, &pk, &fl, amp[sd % 3]);
+    greedy_tree_seed(site_legs, dim, (uint64_t)(1000 + sd) + 64 * base, pp, &pk, &fl, amp[sd % 3]);
     if (pk <= *peak && fl < *flops) { pairs.swap(pp); *peak = pk; *flops = fl; }
   }
 }
 
-bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges,
-                     std::vector<int64_t>& edim, std::vector<int>& cut_edges, uint64_t cap_elems,
-                     const std::vector<int64_t>& full, std::string* err) {
+// One cut search from the caller's dims with the orders of seed base `base`; *work_out is
+// the total work (flops per slice x slices) of the final polished order.
+static bool cut_search_once(const std::vector<std::vector<int>>& site_legs, int n_edges,
+                            std::vector<int64_t>& edim, std::vector<int>& cut_edges, uint64_t cap_elems,
+                            const std::vector<int64_t>& full, uint64_t base, std::string* err,
+                            double* work_out) {
   auto dimf = [&](int x) -> int64_t { return x < 0 ? 2 : edim[x]; };
   const std::vector<int64_t> entry = edim;          // the caller's (forced) cuts stay
   const size_t n_entry = cut_edges.size();
   std::vector<Pair> pairs;
   int64_t peak;
   double flops;
-  greedy_tree(site_legs, dimf, pairs, &peak, &flops);
+  greedy_tree(site_legs, dimf, pairs, &peak, &flops, base);
   int guard = 0;
   while (cap_elems > 0 && (uint64_t)peak > cap_elems) {
     if (++guard > 400) { *err = "tree planner: no cut set found"; return false; }
@@ -203,8 +228,8 @@ bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges
       std::vector<Pair> pp;
       int64_t pk;
       double fl;
-      greedy_tree(site_legs, dimf, pp, &pk, &fl);
-      polish_tree(site_legs, dimf, pp, &pk, &fl);
+      greedy_tree(site_legs, dimf, pp, &pk, &fl, base);
+      polish_tree(site_legs, dimf, pp, &pk, &fl, base);
       double slices = 1;
       for (int e = 0; e < n_edges; ++e) slices *= (double)full[e] / (double)edim[e];
       const double work = fl * slices;
@@ -215,17 +240,17 @@ bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges
     }
     edim[best] /= 2;
     if (std::find(cut_edges.begin(), cut_edges.end(), best) == cut_edges.end()) cut_edges.push_back(best);
-    greedy_tree(site_legs, dimf, pairs, &peak, &flops);
-    polish_tree(site_legs, dimf, pairs, &peak, &flops);
+    greedy_tree(site_legs, dimf, pairs, &peak, &flops, base);
+    polish_tree(site_legs, dimf, pairs, &peak, &flops, base);
   }
   // undo halvings that later ones made unnecessary: double a bond this search cut back
   // while some order still fits the cap with less total work, the largest gain first
+  auto total_work = [&](double fl) {
+    double slices = 1;
+    for (int e = 0; e < n_edges; ++e) slices *= (double)full[e] / (double)edim[e];
+    return fl * slices;
+  };
   if (cap_elems > 0) {
-    auto total_work = [&](double fl) {
-      double slices = 1;
-      for (int e = 0; e < n_edges; ++e) slices *= (double)full[e] / (double)edim[e];
-      return fl * slices;
-    };
     double work = total_work(flops);
     for (int pass = 0; pass < 64; ++pass) {
       int best = -1;
@@ -236,8 +261,8 @@ bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges
         std::vector<Pair> pp;
         int64_t pk;
         double fl;
-        greedy_tree(site_legs, dimf, pp, &pk, &fl);
-        polish_tree(site_legs, dimf, pp, &pk, &fl);
+        greedy_tree(site_legs, dimf, pp, &pk, &fl, base);
+        polish_tree(site_legs, dimf, pp, &pk, &fl, base);
         const double w = total_work(fl);
         if ((uint64_t)pk <= cap_elems && w < best_work) { best = x; best_work = w; }
         edim[x] /= 2;
@@ -250,6 +275,47 @@ bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges
                                    [&](int x) { return edim[x] >= entry[x]; }),
                     cut_edges.end());
   }
+  greedy_tree(site_legs, dimf, pairs, &peak, &flops, base);   // the order build_tree_nodes makes
+  polish_tree(site_legs, dimf, pairs, &peak, &flops, base);
+  *work_out = total_work(flops);
+  return true;
+}
+
+// The cut search from kStarts seed bases (each a different family of perturbed orders: the
+// searches diverge after their first different choice); the one with the least total work
+// is kept, and its base, which build_tree_nodes needs to rebuild the same order.
+constexpr int kStarts = 8;
+bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges,
+                     std::vector<int64_t>& edim, std::vector<int>& cut_edges, uint64_t cap_elems,
+                     const std::vector<int64_t>& full, int* base_out, std::string* err) {
+  bool found = false;
+  double best_work = 0;
+  std::vector<int64_t> best_dim;
+  std::vector<int> best_cuts;
+  std::string last_err;
+  for (int b = 0; b < kStarts; ++b) {
+    std::vector<int64_t> d = edim;
+    std::vector<int> c = cut_edges;
+    double w = 0;
+    std::string e;
+    if (!cut_search_once(site_legs, n_edges, d, c, cap_elems, full, (uint64_t)b, &e, &w)) {
+      last_err = e;
+      continue;
+    }
+    if (!found || w < best_work) {
+      found = true;
+      best_work = w;
+      best_dim = d;
+      best_cuts = c;
+      *base_out = b;
+    }
+  }
+  if (!found) {
+    *err = last_err;
+    return false;
+  }
+  edim = best_dim;
+  cut_edges = best_cuts;
   return true;
 }
 
@@ -293,7 +359,7 @@ static bool fuse_perm(const std::vector<int64_t>& shape, const std::vector<int>&
 }
 
 bool build_tree_nodes(const std::vector<std::vector<int>>& site_legs, const std::vector<int64_t>& edim,
-                      const std::vector<uint64_t>& site_off, uint64_t arena_base,
+                      int base, const std::vector<uint64_t>& site_off, uint64_t arena_base,
                       std::vector<TreeNode>& nodes, uint64_t* arena_bytes,
                       std::vector<int>* root_legs, int64_t* max_el, std::string* err) {
   auto dimf = [&](int x) -> int64_t { return x < 0 ? 2 : edim[x]; };
@@ -301,8 +367,8 @@ bool build_tree_nodes(const std::vector<std::vector<int>>& site_legs, const std:
   std::vector<Pair> pairs;
   int64_t peak;
   double flops;
-  greedy_tree(site_legs, dimf, pairs, &peak, &flops);
-  polish_tree(site_legs, dimf, pairs, &peak, &flops);
+  greedy_tree(site_legs, dimf, pairs, &peak, &flops, (uint64_t)base);
+  polish_tree(site_legs, dimf, pairs, &peak, &flops, (uint64_t)base);
   *max_el = peak;
   std::vector<std::vector<int>> legs(site_legs);
   auto elems = [&](const std::vector<int>& l) {

@@ -254,9 +254,9 @@ int64_t adjoint_site_partials(const qfx_plan* p, const FoldSite& fs);
 // contraction-tree planning (plan_tree.cpp)
 bool tree_cut_search(const std::vector<std::vector<int>>& site_legs, int n_edges,
                      std::vector<int64_t>& edim, std::vector<int>& cut_edges, uint64_t cap_elems,
-                     const std::vector<int64_t>& full, std::string* err);
+                     const std::vector<int64_t>& full, int* base_out, std::string* err);
 bool build_tree_nodes(const std::vector<std::vector<int>>& site_legs, const std::vector<int64_t>& edim,
-                      const std::vector<uint64_t>& site_off, uint64_t arena_base,
+                      int base, const std::vector<uint64_t>& site_off, uint64_t arena_base,
                       std::vector<TreeNode>& nodes, uint64_t* arena_bytes,
                       std::vector<int>* root_legs, int64_t* max_el, std::string* err);
 
