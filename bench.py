@@ -379,6 +379,10 @@ def run_qfx(args):
         line["permute"] = measure_permute(qfx, torch, steps=sub_steps, warmup=sub_warm)
         line["batch"] = measure_batch(qfx, torch, BATCH_MIX_SUBSET, 8, steps=1, warmup=1,
                                       tc=True, autotune=not args.no_autotune)
+        line["region"] = {"workload": "7x7x(1+40+1) RQC seed 0, contraction-tree plan at an 8 GiB cap, "
+                                      "|x2| = 6, BF16x3, seeded slices of one x1 batch",
+                          **region_entry(qfx, torch, qfx.Circuit(ri.rqc(7, 7, 40, seed=0)), "bf16x3",
+                                         steps=2, warmup=1, dev=dev)}
     if world == 1 and not args.no_cpu:
         cpu = cpu_full_route()
         rate, reps, dt = cpu_step_sample(seconds=4.0)
@@ -417,6 +421,10 @@ def summarize(line):
                              "per_item": _r(b["fp32_per_item"]["value"]),
                              "bf16x3_graph": _r(b["bf16x3_graph"]["value"]) if b.get("bf16x3_graph") else None,
                              "bf16x3_per_item": _r(b["bf16x3_per_item"]["value"]) if b.get("bf16x3_per_item") else None}
+    if "region" in line:
+        g = line["region"]
+        s["region_7x7x40_bf16x3"] = {"tflops": _r(g["value"]), "frac_probe": _r(g["roofline"]["tensor_probe"]["frac"]),
+                                     "amps_per_s_f0.006": _r(g["amplitudes_per_s_at_fidelity_0.006"])}
     if "cpu_baseline" in line:
         c = line["cpu_baseline"]
         s["cpu"] = {"tflops": _r(c["value"]), "cores": c["cores"],
@@ -979,6 +987,68 @@ def run_wide(args):
 
 
 # ----------------------------------------------------------------------------- region plans
+def region_entry(qfx, torch, circ, prec, steps, warmup, dev):
+    """One tree plan at an 8 GiB cap, |x2| = 6: `steps` seeded slices of one x1 batch timed
+    with CUDA events after `warmup` others, with the largest node's roofline, kernel shares
+    and the amplitude rates at the paper's fidelity (0.6%) and at full fidelity."""
+    n = circ.rows * circ.cols
+    x1 = torch.tensor(ri.random_bitstrings(n, 1, seed=2).view(np.int64), device=dev)
+    t0 = time.perf_counter()
+    plan = qfx.Plan(circ, n_open=6, max_intermediate_bytes=8 << 30, family="tree", precision=prec)
+    plan_s = time.perf_counter() - t0
+    sids = [int(v) for v in np.random.default_rng(1).integers(0, plan.n_slices, warmup + steps)]
+    ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
+    out = torch.empty((1, 64), dtype=torch.complex128, device=dev)
+    for s in sids[:warmup]:
+        qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    qfx.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in sids[warmup:]:
+        qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    qfx.profile_enable(False)
+    recs = qfx.profile_collect()
+    clk = clocks.stop()
+    qfx.sync()
+    el = e0.elapsed_time(e1) / 1e3
+    flops = plan.stats["flops_per_item"]
+    kt = {}
+    for r in recs:
+        k = {0: "contraction_step", 1: "fold", 4: "permute"}.get(r["kind"], str(r["kind"]))
+        kt[k] = kt.get(k, 0.0) + r["ms"]
+    tot = sum(kt.values()) or 1.0
+    big = plan.steps[plan.stats["largest_step"]]
+    dom = [r["ms"] for r in recs if r["kind"] == 0 and r["step"] == plan.stats["largest_step"]]
+    dom_tf = big["flops"] / (float(np.mean(dom)) / 1e3) / 1e12 if dom else float("nan")
+    if prec == "fp32":
+        peak, _ = fp32_peak(torch, dev, clk.get("sm_max_mhz") or 2070.0)
+        roof = {"bound": "alu", "achieved": dom_tf, "peak": peak, "unit": "TFLOP/s", "frac": dom_tf / peak}
+    else:
+        probe = qfx.tensor_peak("bf16x3", 1 << 16)
+        ach = dom_tf * TENSOR_FACTOR["bf16x3"]
+        roof = {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                "tensor_probe": {"tflops": probe, "frac": ach / probe}}
+    roof["kernel"] = f"largest node (P,K,N,Sd)=({big['P']},{big['K']},{big['N']},{big['Sd']})"
+    spl = el / steps
+    f_paper = 0.006          # the paper's fidelity for 7x7x(1+40+1) (Sec. V, Table I)
+    res = {
+        "value": flops * steps / el / 1e12, "unit": "TFLOP/s", "ms_per_slice": 1e3 * spl,
+        "amplitudes_per_s_at_fidelity_0.006": 64.0 / (max(1, round(f_paper * plan.n_slices)) * spl),
+        "amplitudes_per_s_full": 64.0 / (plan.n_slices * spl),
+        "slices": plan.n_slices, "flops_per_slice": flops, "flops_per_x1_batch": flops * plan.n_slices,
+        "max_intermediate_bytes": plan.stats["max_elements"] * 8, "workspace_bytes": plan.workspace_bytes(1),
+        "plan_s": plan_s, "cuts": len(plan.cuts), "kernel_share": {k: v / tot for k, v in kt.items()},
+        "roofline": roof, "clocks": clk}
+    del ws
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_region(args):
     """Region (contraction-tree) plans for the paper's 7x7x(1+40+1) shape and for
     8x8x(1+32+1), both at an 8 GiB cap on the largest intermediate, |x2| = 6: each timed
@@ -991,62 +1061,8 @@ def run_region(args):
     for rows, cols, depth in ((7, 7, 40), (8, 8, 32)):
         circ = qfx.Circuit(ri.rqc(rows, cols, depth, seed=0))
         line = qfx.Plan(circ, n_open=6, max_intermediate_bytes=8 << 30)
-        x1 = torch.tensor(ri.random_bitstrings(rows * cols, 1, seed=2).view(np.int64), device=dev)
-        entry = {}
-        for prec in ("fp32", "bf16x3"):
-            t0 = time.perf_counter()
-            plan = qfx.Plan(circ, n_open=6, max_intermediate_bytes=8 << 30, family="tree", precision=prec)
-            plan_s = time.perf_counter() - t0
-            sids = [int(v) for v in np.random.default_rng(1).integers(0, plan.n_slices, args.warmup + args.steps)]
-            ws = torch.empty(plan.workspace_bytes(1), dtype=torch.uint8, device=dev)
-            out = torch.empty((1, 64), dtype=torch.complex128, device=dev)
-            for s in sids[:args.warmup]:
-                qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
-            torch.cuda.synchronize(dev)
-            clocks = ClockSampler(0)
-            clocks.start()
-            qfx.profile_enable(True)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for s in sids[args.warmup:]:
-                qfx.amplitudes(plan, x1, slice_begin=s, slice_end=s + 1, workspace=ws, out=out)
-            e1.record()
-            torch.cuda.synchronize(dev)
-            qfx.profile_enable(False)
-            recs = qfx.profile_collect()
-            clk = clocks.stop()
-            qfx.sync()
-            el = e0.elapsed_time(e1) / 1e3
-            flops = plan.stats["flops_per_item"]
-            kt = {}
-            for r in recs:
-                k = {0: "contraction_step", 1: "fold", 4: "permute"}.get(r["kind"], str(r["kind"]))
-                kt[k] = kt.get(k, 0.0) + r["ms"]
-            tot = sum(kt.values()) or 1.0
-            big = plan.steps[plan.stats["largest_step"]]
-            dom = [r["ms"] for r in recs if r["kind"] == 0 and r["step"] == plan.stats["largest_step"]]
-            dom_tf = big["flops"] / (float(np.mean(dom)) / 1e3) / 1e12 if dom else float("nan")
-            if prec == "fp32":
-                peak, _ = fp32_peak(torch, dev, clk.get("sm_max_mhz") or 2070.0)
-                roof = {"bound": "alu", "achieved": dom_tf, "peak": peak, "unit": "TFLOP/s", "frac": dom_tf / peak}
-            else:
-                probe = qfx.tensor_peak("bf16x3", 1 << 16)
-                ach = dom_tf * TENSOR_FACTOR["bf16x3"]
-                roof = {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
-                        "tensor_probe": {"tflops": probe, "frac": ach / probe}}
-            roof["kernel"] = f"largest node (P,K,N,Sd)=({big['P']},{big['K']},{big['N']},{big['Sd']})"
-            spl = el / args.steps
-            f_paper = 0.006          # the paper's fidelity for this shape (Sec. V, Table I)
-            entry[prec] = {
-                "value": flops * args.steps / el / 1e12, "unit": "TFLOP/s", "ms_per_slice": 1e3 * spl,
-                "amplitudes_per_s_at_fidelity_0.006": 64.0 / (max(1, round(f_paper * plan.n_slices)) * spl),
-                "amplitudes_per_s_full": 64.0 / (plan.n_slices * spl),
-                "slices": plan.n_slices, "flops_per_slice": flops, "flops_per_x1_batch": flops * plan.n_slices,
-                "max_intermediate_bytes": plan.stats["max_elements"] * 8, "workspace_bytes": plan.workspace_bytes(1),
-                "plan_s": plan_s, "cuts": len(plan.cuts), "kernel_share": {k: v / tot for k, v in kt.items()},
-                "roofline": roof, "clocks": clk}
-            del ws
-            torch.cuda.empty_cache()
+        entry = {prec: region_entry(qfx, torch, circ, prec, args.steps, args.warmup, dev)
+                 for prec in ("fp32", "bf16x3")}
         entry["line_sweep_at_same_cap"] = {"slices": line.n_slices, "flops_per_slice": line.stats["flops_per_item"],
                                            "flops_per_x1_batch": line.stats["flops_per_item"] * line.n_slices}
         res[f"{rows}x{cols}x(1+{depth}+1)"] = entry

@@ -52,9 +52,11 @@ def test_summary_holds_every_part():
             "permute": {"cases": [{"frac": 0.75}, {"frac": 0.9}]},
             "batch": {"fp32_persistent": {"value": 41.6}, "fp32_per_item": {"value": 48.2},
                       "bf16x3_graph": {"value": 157.7}, "bf16x3_per_item": {"value": 153.6}},
+            "region": {"value": 280.0, "roofline": {"tensor_probe": {"frac": 0.76}},
+                       "amplitudes_per_s_at_fidelity_0.006": 6.7},
             "cpu_baseline": {"value": 0.01, "cores": 16, "step_sample": {"value": 0.1}}}
     s = bench.summarize(line)
-    assert set(s) == {"fp32", "bf16x3", "adjoint", "permute_frac", "batch_tflops", "cpu"}
+    assert set(s) == {"fp32", "bf16x3", "adjoint", "permute_frac", "batch_tflops", "region_7x7x40_bf16x3", "cpu"}
     assert s["batch_tflops"]["persistent"] == 41.6 and s["fp32"]["frac"] == 0.7
     assert len(json.dumps(s)) < 1000
     assert np.isclose(s["bf16x3"]["err_vs_fp32"], 4e-6)
