@@ -98,6 +98,9 @@ int simt_prepare_attributes() {
 #define QFX_ATTR(V, BM, BJ, TM, TJ, KM, ST) \
   if (int e = ensure_attr<BM, BJ, TM, TJ, KM, ST>()) return e;
   QFX_SIMT_VARIANTS(QFX_ATTR)
+#undef QFX_ATTR
+#define QFX_ATTR(V, BM, BJ, TM, TJ, KM, ST, NT) \
+  if (int e = ensure_attr<BM, BJ, TM, TJ, KM, ST, NT>()) return e;
   QFX_SIMT_FILL_VARIANTS(QFX_ATTR)
 #undef QFX_ATTR
   return 0;
@@ -135,8 +138,8 @@ int fill_variant(int variant, int64_t N, int64_t J, int batch) {
 }
 
 bool simt_variant_valid(int variant, int64_t Sd) {
-  const bool jmode = (variant >= 0 && variant < 5) || (variant >= 20 && variant < 25);
-  const bool kmode = (variant >= 5 && variant < 10) || (variant >= 25 && variant < 30 && variant != 29);
+  const bool jmode = (variant >= 0 && variant < 5) || (variant >= 20 && variant < 24);
+  const bool kmode = (variant >= 5 && variant < 10) || (variant >= 25 && variant < 29);
   return (jmode && Sd % 2 == 0) || kmode;
 }
 
@@ -153,6 +156,9 @@ int launch_step(const void* S, int64_t s_stride, const void* B, int64_t b_stride
 #define QFX_CASE(V, BM, BJ, TM, TJ, KM, ST) \
   case V: return launch_cfg<BM, BJ, TM, TJ, KM, ST>(a, batch, st);
     QFX_SIMT_VARIANTS(QFX_CASE)
+#undef QFX_CASE
+#define QFX_CASE(V, BM, BJ, TM, TJ, KM, ST, NT) \
+  case V: return launch_cfg<BM, BJ, TM, TJ, KM, ST, NT>(a, batch, st);
     QFX_SIMT_FILL_VARIANTS(QFX_CASE)
 #undef QFX_CASE
     default: return (int)cudaErrorInvalidValue;

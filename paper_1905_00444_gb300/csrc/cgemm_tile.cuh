@@ -225,16 +225,17 @@ __device__ __forceinline__ void cgemm_tile(const StepArgs& a, int64_t tile, int6
 // Fill variants: the same tiles with a quarter (or half) of the outputs per CTA, 4 x 4 (or
 // 4 x 2) per thread, for grids that the tiles above would leave with fewer CTAs than two
 // per SM (fill_variant picks them at launch time; the batch scheduler keeps 0..9).
-// Variant 20 + v serves 0..4 (21 for 1 and 2 ...), 25 + v the KMODE ones.
+// Variants 0, 1, 2, 3, 4 map to 20, 20, 21, 22, 23 and 5..9 to 25, 25, 26, 27, 28; the last
+// argument is the CTA's thread count.
 #define QFX_SIMT_FILL_VARIANTS(X)          \
-  X(20, 64, 64, 4, 4, false, 3)            \
-  X(21, 32, 128, 4, 4, false, 3)           \
-  X(22, 16, 256, 4, 4, false, 3)           \
-  X(23, 8, 256, 4, 2, false, 3)            \
-  X(25, 64, 64, 4, 4, true, 3)             \
-  X(26, 32, 128, 4, 4, true, 3)            \
-  X(27, 16, 256, 4, 4, true, 3)            \
-  X(28, 8, 256, 4, 2, true, 3)
+  X(20, 64, 64, 4, 4, false, 3, 256)       \
+  X(21, 32, 128, 4, 4, false, 3, 256)      \
+  X(22, 16, 256, 4, 4, false, 3, 256)      \
+  X(23, 8, 256, 4, 2, false, 3, 256)       \
+  X(25, 64, 64, 4, 4, true, 3, 256)        \
+  X(26, 32, 128, 4, 4, true, 3, 256)       \
+  X(27, 16, 256, 4, 4, true, 3, 256)       \
+  X(28, 8, 256, 4, 2, true, 3, 256)
 
 }  // namespace simt
 }  // namespace qfx
