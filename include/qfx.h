@@ -256,14 +256,16 @@ qfx_status qfx_amplitudes_static(const qfx_plan* p, const uint64_t* x1, int64_t 
 /* Batched execution (Sec. III.A: slices are independent paths; Sec. III.B: x1 batches).
  * Many work items -- every (slice, x1) of every listed item, of any mix of plans and
  * shapes -- run together:
- * - items of FP32 plans whose largest step has fewer than 512 output tiles: in ONE
- *   persistent kernel, a device task queue of fold chunks, scale chunks, contraction-step
- *   tiles (each step's plan-chosen variant) and FP64 accumulations, with per-segment
- *   completion counters as dependencies and bounded waits;
- * - larger FP32 items, and every item of a batch with any split-precision plan: as ONE
- *   CUDA graph built at prepare time, every item's launch sequence on one of up to 16
- *   parallel lanes, each lane with its own workspace slot (`slots` = lanes); the
- *   persistent launch of the small items, if any, is a node of the same graph.
+ * - items whose steps all run FP32 tiles (FP32 plans, and split-precision plans whose
+ *   step shapes the tensor-core tile does not take) and whose largest step has fewer
+ *   than 512 output tiles: in ONE persistent kernel, a device task queue of fold chunks,
+ *   scale chunks, contraction-step tiles (each step's plan-chosen variant) and FP64
+ *   accumulations, with per-segment completion counters as dependencies and bounded
+ *   waits;
+ * - items with tensor-core steps, larger items and contraction trees: as ONE CUDA graph
+ *   built at prepare time, every item's launch sequence on one of up to 16 parallel
+ *   lanes, each lane with its own workspace slot (`slots` = lanes); the persistent
+ *   launch of the small items, if any, is a node of the same graph.
  * Each batch item's `out` rows get the same values qfx_amplitudes would produce. */
 typedef struct {
   const qfx_plan* plan;

@@ -246,15 +246,6 @@ constexpr int64_t kGraphLanes = 16;
 
 }  // namespace
 
-// Whether any item's plan runs steps on the tensor cores (those batches use the graph
-// executor: the persistent scheduler's tasks are FP32 tiles).
-bool batch_has_tc(const qfx_batch_item* items, int32_t n_items) {
-  for (int i = 0; i < n_items; ++i)
-    for (const auto& sp : items[i].plan->steps)
-      if (sp.variant >= kVariantTcBf16) return true;
-  return false;
-}
-
 // Workspace of one graph lane: the header and block of one work item of the largest plan.
 uint64_t graph_lane_bytes(const qfx_batch_item* items, int32_t n_items) {
   uint64_t lane = 0;
@@ -309,7 +300,7 @@ struct qfx_batch {
   int grid = 0;
   size_t smem = 0;
   int64_t n_work = 0, slots = 0;
-  // batches with split-precision plans: one CUDA graph of per-item launch sequences
+  // batches with tensor-core or large items: one CUDA graph of per-item launch sequences
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t graph_kernels = 0;
@@ -339,6 +330,19 @@ bool item_is_big(const qfx_plan* p) {
   return most >= kBigTiles;
 }
 
+// Whether a work item runs as its own launch sequence in a batch's graph rather than inside
+// the persistent kernel: its plan has a step on the tensor cores (that tile has its own
+// warp roles, TMEM and barrier rings, and is itself persistent over a step's tiles), or it
+// is big (above).  Split-precision plans whose steps all resolve to FP32 tiles (step
+// shapes the tensor-core tile does not take: K or N below 16, fewer than 128 columns, as
+// in 4x4x(1+16+1) with bond dimension 4) run in the persistent kernel like FP32 plans: the
+// FP32 tile ignores the plan's precision.
+bool item_runs_launches(const qfx_plan* p) {
+  for (const auto& sp : p->steps)
+    if (sp.variant >= kVariantTcBf16) return true;
+  return item_is_big(p);
+}
+
 static qfx_status prepare_persistent(const qfx_batch_item* items, int32_t n_items,
                                      const std::map<const qfx_plan*, const DeviceTables*>& tabmap,
                                      void* workspace, size_t ws_bytes, qfx_batch** out, void* stream);
@@ -355,9 +359,9 @@ static uint64_t sub_bytes(const std::vector<qfx_batch_item>& small) {
 // steps, accumulation; one work item in flight) is recorded on one of `lanes` streams
 // forked from a capture stream, each lane with its own workspace slot, and the lanes join
 // again: one CUDA graph, replayed by qfx_batch_run.  Items on different lanes overlap; an
-// item's own launches keep their order.  Batches with split-precision plans run all
-// their items this way; FP32 batches run their large items this way and their small items
-// (`small`) in one persistent launch recorded on a lane of its own.
+// item's own launches keep their order.  Items with tensor-core steps and large items run
+// this way; the small FP32-tile items (`small`) run in one persistent launch recorded on a
+// lane of its own.
 static qfx_status prepare_graph(const qfx_batch_item* items, int32_t n_items,
                                 const std::vector<qfx_batch_item>& small,
                                 const std::map<const qfx_plan*, const DeviceTables*>& tabmap,
@@ -665,9 +669,8 @@ extern "C" uint64_t qfx_batch_workspace_bytes(const qfx_batch_item* items, int32
     if (!items[i].plan) return 0;
     if (distinct.insert(items[i].plan).second) tab += qfx::table_bytes(items[i].plan);
   }
-  if (qfx::batch_has_tc(items, n_items)) return tab + (uint64_t)slots * qfx::graph_lane_bytes(items, n_items);
   std::vector<qfx_batch_item> big, small;
-  for (int i = 0; i < n_items; ++i) (item_is_big(items[i].plan) ? big : small).push_back(items[i]);
+  for (int i = 0; i < n_items; ++i) (item_runs_launches(items[i].plan) ? big : small).push_back(items[i]);
   if (!big.empty())
     return tab + sub_bytes(small) + (uint64_t)slots * qfx::graph_lane_bytes(big.data(), (int32_t)big.size());
   return tab + qfx_batch_workspace_bytes_nt(items, n_items, slots);
@@ -711,14 +714,13 @@ extern "C" qfx_status qfx_batch_prepare(const qfx_batch_item* items, int32_t n_i
     }
     std::map<const qfx_plan*, const DeviceTables*> tabmap;
     for (size_t k = 0; k < plans.size(); ++k) tabmap[plans[k]] = tabs[k];
-    if (batch_has_tc(items, n_items))
-      return prepare_graph(items, n_items, {}, tabmap, workspace, ws_bytes, out, stream);
-    // FP32 plans: items whose steps fill the GPU many times over run as their own launch
-    // sequences inside one graph (their tiles run faster in the standalone kernels than
-    // inside the persistent one, and launch overhead is negligible at their size); the
-    // others run in one persistent launch, itself a node of that graph
+    // Items with tensor-core steps, and items whose steps fill the GPU many times over, run
+    // as their own launch sequences inside one graph (the tensor-core tile cannot run as a
+    // task of the persistent kernel, large FP32 tiles run faster in the standalone kernels
+    // than inside it, and launch overhead is negligible at their size); the others run in
+    // one persistent launch, itself a node of that graph
     std::vector<qfx_batch_item> big, small;
-    for (int i = 0; i < n_items; ++i) (item_is_big(items[i].plan) ? big : small).push_back(items[i]);
+    for (int i = 0; i < n_items; ++i) (item_runs_launches(items[i].plan) ? big : small).push_back(items[i]);
     if (!big.empty())
       return prepare_graph(big.data(), (int32_t)big.size(), small, tabmap, workspace, ws_bytes, out, stream);
     return prepare_persistent(items, n_items, tabmap, workspace, ws_bytes, out, stream);

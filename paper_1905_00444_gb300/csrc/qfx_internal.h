@@ -228,7 +228,6 @@ int tc_probe(int precision, int64_t iters, double* tflops, void* stream);
 int tc_prepare_attributes();     // shared-memory opt-ins of every tensor-core kernel
 int simt_prepare_attributes();   // and of every FP32 tile kernel
 int batch_take_status();  // reads and clears the batch scheduler's timeout flag
-bool batch_has_tc(const qfx_batch_item* items, int32_t n_items);
 uint64_t graph_lane_bytes(const qfx_batch_item* items, int32_t n_items);
 int perm_take_status();   // reads and clears the permute kernel's timeout flag
 int launch_permute(const void* in, void* out, int rank, const int64_t* shape,

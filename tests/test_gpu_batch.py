@@ -126,14 +126,16 @@ def mixed_tc_items(qfx):
 
 @pytest.mark.parametrize("slots", [1, 3, 16])
 def test_split_precision_batch_graph_matches_per_item(qfx, slots):
-    """Batches with tensor-core plans run as one CUDA graph of per-item launch sequences
-    over parallel lanes: outputs equal per-item qfx_amplitudes bit for bit (one work item
-    in flight either way), whatever the number of lanes."""
+    """Items with tensor-core steps run as per-item launch sequences over parallel lanes of
+    one CUDA graph, the split-precision items whose steps all take FP32 tiles (4x4x16,
+    3x5x16) in the persistent kernel recorded in the same graph: outputs equal per-item
+    qfx_amplitudes bit for bit, whatever the number of lanes."""
     items, circuits = mixed_tc_items(qfx)
-    assert sum(any(s["variant"] >= 10 for s in p.steps) for p, _, _, _ in items) >= 2
+    n_tc = sum(any(s["variant"] >= 10 for s in p.steps) for p, _, _, _ in items)
+    assert n_tc == 2
     want = per_item(qfx, items)
     b = qfx.Batch(items, slots=slots)
-    assert b.slots == min(slots, len(items))
+    assert b.slots == min(slots, n_tc)
     outs = b.run()
     qfx.sync()
     for o, w in zip(outs, want):
@@ -165,9 +167,31 @@ def test_split_precision_batch_replays_inside_a_cuda_graph(qfx):
             np.testing.assert_array_equal(o.cpu().numpy(), w)
 
 
+def test_small_split_precision_items_in_one_persistent_launch(qfx):
+    """Split-precision plans whose step shapes the tensor-core tile does not take (bond
+    dimension 4) are FP32-tile items: a batch of them is ONE persistent kernel launch,
+    bit-identical to per-item launches of the same plans."""
+    items = []
+    for rows, cols, seed, no, nx in [(4, 4, 20, 5, 3), (3, 5, 21, 6, 2), (4, 4, 22, 3, 4)]:
+        c = ri.rqc(rows, cols, 16, seed=seed)
+        plan = qfx.Plan(qfx.Circuit(c), n_open=no, precision="bf16x3")
+        assert all(st["variant"] < 10 for st in plan.steps)
+        x1 = torch.tensor(ri.random_bitstrings(rows * cols, nx, seed=seed).view(np.int64),
+                          device="cuda")
+        items.append((plan, x1, 0, None))
+    want = per_item(qfx, items)
+    b = qfx.Batch(items, slots=4)
+    before = qfx.launch_count()
+    outs = b.run()
+    assert qfx.launch_count() - before == 1
+    qfx.sync()
+    for o, w in zip(outs, want):
+        np.testing.assert_array_equal(o.cpu().numpy(), w)
+
+
 def test_fp32_items_in_a_split_precision_batch(qfx):
-    """An FP32 plan mixed with tensor-core plans goes through the graph executor too and
-    keeps its FP32 result."""
+    """An FP32 plan mixed with tensor-core plans (it joins the persistent launch beside
+    the lanes) keeps its FP32 result."""
     items, _ = mixed_tc_items(qfx)
     c = ri.rqc(4, 5, 16, seed=9)
     plan = qfx.Plan(qfx.Circuit(c), n_open=4)

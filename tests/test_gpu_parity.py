@@ -218,6 +218,21 @@ def test_7x7x32_slicing_invariance(qfx):
     assert np.all(np.abs(sliced - full) <= REL * np.maximum(np.abs(full), floor))
 
 
+def test_7x7x32_one_full_bond_cut_16_slices(qfx):
+    """The benchmarked circuit with one horizontal bond of the middle grid column,
+    (3,3)-(3,4), cut to single values: 16 slices whose FP64 sum equals the uncut
+    contraction (Sec. III.A), every slice the full-size FP32 path."""
+    c = ri.rqc(7, 7, 32, seed=0)
+    x1 = int(ri.random_bitstrings(49, 1, seed=1)[0])
+    _, full = run(qfx, c, [x1], n_open=6)
+    plan, sliced = run(qfx, c, [x1], n_open=6, cuts=[(24, 25, 1)])
+    assert plan.n_slices == 16
+    nrm = np.linalg.norm(full)
+    assert np.linalg.norm(sliced - full) / nrm <= REL
+    floor = 2.0 ** (-49 / 2)
+    assert np.all(np.abs(sliced - full) <= REL * np.maximum(np.abs(full), floor))
+
+
 # --- single operations: contraction step and permute --------------------------------
 
 FILL = {0: 20, 1: 20, 2: 21, 3: 22, 4: 23, 5: 25, 6: 25, 7: 26, 8: 27, 9: 28}
