@@ -50,10 +50,10 @@ WORKLOADS = {
 }
 # DRAM bytes (read + write) per launch of the dominant kernel: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the same kernel on the kernel case
-# (K = N = 256, 2^18 columns: 1.0291e9 B), scaled by the columns of a full launch
+# (K = N = 256, 2^18 columns: 1.0290e9 B), scaled by the columns of a full launch
 # (2^24 / 2^18 = 64); the traffic grows in proportion to the columns (B read once, C
 # written once).
-TRAFFIC = {"full": 1.0291e9 * 64, "small": None}
+TRAFFIC = {"full": 1.0290e9 * 64, "small": None}
 
 
 def workload_desc(w):
