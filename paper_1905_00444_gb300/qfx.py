@@ -368,8 +368,9 @@ def frugal_sample(plan: Plan, x1, u, scan_mask, M: float = 10.0, *, slice_begin:
 
 
 class Batch:
-    """Many (plan, x1 batch, slice range) items in one persistent launch (FP32 plans) or
-    one CUDA graph of per-item launches over parallel lanes (any split-precision plan).
+    """Many (plan, x1 batch, slice range) items in one CUDA graph: small items whose steps
+    all take FP32 tiles in one persistent launch, items with tensor-core steps, large items
+    and tree plans as per-item launch sequences over parallel lanes (`slots` of them).
 
     items: list of (plan, x1 tensor, slice_begin, slice_end); outputs are allocated here
     (complex128 [n_batch, 2^n_open] each) and refreshed by every run()."""
