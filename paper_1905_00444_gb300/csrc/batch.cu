@@ -3,7 +3,7 @@
 //
 // The host expands a list of qfx_batch_item into work items and cuts each one's work
 // into segments of independent tasks:
-//   FOLD  (chunks of site elements: FP64 time fold, per-site max)      depends on the
+//   FOLD  (chunks of site elements: float-float time fold, per-site max) depends on the
 //         previous occupant of the work item's workspace slot (its ACCUM);
 //   SCALE (same chunks: power-of-two scale)                            on FOLD;
 //   STEP i (output tiles of contraction step i, FP32 SIMT tile body)   on STEP i-1 / SCALE;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kT, 1) batch_kernel(const BatchArgs a) {
       if (sg.phase == PH_FOLD) {
         float mx = 0.f;
         for (int64_t i = start + tid; i < end; i += kT) {
-          const float2 v = foldk::fold_element(st, pl.t.events, pl.t.mats, pl.t.cuts, pl.n_cuts,
+          const float2 v = foldk::fold_element(st, pl.t.events, pl.t.matsf, pl.t.cuts, pl.n_cuts,
                                                w.x1, w.sid, i);
           T[i] = v;
           mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));

@@ -6,11 +6,12 @@
 // D(b0, b1) = sum_k delta(b0, k) D(k, b1), so q0 applies the projector |k><k| and q1
 // applies diag(D(k,0), D(k,1)), with k one bit (leg) of the bond between them.  The
 // tensor element T[up][left][x][right][down] is <x| ... |0> for the leg bits that its
-// bond values carry.  Each element is evolved in FP64 and rounded once to complex64.  A
+// bond values carry.  Each element is evolved in float-float arithmetic (FP32 pairs,
+// about 48 significant bits; see fold_element.cuh) and rounded once to complex64.  A
 // thread takes kGroup consecutive elements: they differ only in the low bits of the
 // innermost bond (its latest gates), so up to the first event that reads one of those bits
-// they share one 2-vector, computed once with the same FP64 operations as each element's
-// own fold (the results are those of foldk::fold_element bit for bit); from there on each
+// they share one 2-vector, computed once with the same operations as each element's own
+// fold (the results are those of foldk::fold_element bit for bit); from there on each
 // element has its own.
 //
 // Normalisation (Sec. III.E: inputs normalised, outputs renormalised, to keep FP32
@@ -30,15 +31,15 @@ constexpr int kGroup = 4;   // consecutive elements per thread
 
 template <int G>
 __device__ __forceinline__ void fold_group(const FoldSite& st, const FoldEvent* __restrict__ events,
-                                           const double* __restrict__ mats, const CutDev* __restrict__ cuts,
+                                           const float* __restrict__ matsf, const CutDev* __restrict__ cuts,
                                            int n_cuts, const uint64_t* __restrict__ x1w, int64_t sid,
                                            int64_t i0, float2 out[G]) {
   foldk::FoldCoord fc[G];
 #pragma unroll
   for (int q = 0; q < G; ++q) fc[q] = foldk::fold_coord(st, cuts, n_cuts, x1w, sid, i0 + q);
-  double2 v0[G], v1[G];
-  v0[0] = make_double2(1.0, 0.0);
-  v1[0] = make_double2(0.0, 0.0);
+  foldk::cff v0[G], v1[G];
+  v0[0] = foldk::cff_one();
+  v1[0] = foldk::cff_zero();
   bool split = false;
   for (int e = st.ev_begin; e < st.ev_end; ++e) {
     const FoldEvent ev = events[e];
@@ -50,7 +51,7 @@ __device__ __forceinline__ void fold_group(const FoldSite& st, const FoldEvent* 
 #pragma unroll
       for (int q = 1; q < G; ++q) same = same && k[q] == k[0];
       if (same) {
-        foldk::apply_event(ev, mats, k[0], v0[0], v1[0]);
+        foldk::apply_event(ev, matsf, k[0], v0[0], v1[0]);
         continue;
       }
 #pragma unroll
@@ -58,7 +59,7 @@ __device__ __forceinline__ void fold_group(const FoldSite& st, const FoldEvent* 
       split = true;
     }
 #pragma unroll
-    for (int q = 0; q < G; ++q) foldk::apply_event(ev, mats, k[q], v0[q], v1[q]);
+    for (int q = 0; q < G; ++q) foldk::apply_event(ev, matsf, k[q], v0[q], v1[q]);
   }
   if (!split) {
 #pragma unroll
@@ -66,14 +67,14 @@ __device__ __forceinline__ void fold_group(const FoldSite& st, const FoldEvent* 
   }
 #pragma unroll
   for (int q = 0; q < G; ++q) {
-    const double2 res = fc[q].xv ? v1[q] : v0[q];
-    out[q] = make_float2((float)res.x, (float)res.y);
+    const foldk::cff res = fc[q].xv ? v1[q] : v0[q];
+    out[q] = make_float2(foldk::ff_round(res.re), foldk::ff_round(res.im));
   }
 }
 
 __global__ void __launch_bounds__(kThreads) fold_kernel(
     const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events,
-    const double* __restrict__ mats, const CutDev* __restrict__ cuts, int n_cuts,
+    const float* __restrict__ matsf, const CutDev* __restrict__ cuts, int n_cuts,
     const uint64_t* __restrict__ x1, int x1_words, int64_t n_batch, int64_t slice_begin,
     int64_t item0, char* hdr, uint64_t hdr_stride, char* items, uint64_t item_bytes,
     uint64_t sites_off, int n_sites) {
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) fold_kernel(
     const int64_t b = item % n_batch;
     const int64_t sid = slice_begin + item / n_batch;
     float2 out[kGroup];
-    fold_group<kGroup>(st, events, mats, cuts, n_cuts, x1 + b * x1_words, sid, i0, out);
+    fold_group<kGroup>(st, events, matsf, cuts, n_cuts, x1 + b * x1_words, sid, i0, out);
     float2* T = reinterpret_cast<float2*>(items + (uint64_t)g * item_bytes + sites_off) + st.offset;
 #pragma unroll
     for (int q = 0; q < kGroup; ++q)
@@ -165,7 +166,7 @@ int launch_fold(const DeviceTables& t, int n_sites, int64_t max_site_size, int n
   const int64_t per_block = (int64_t)kThreads * kGroup;
   dim3 grid((unsigned)((max_site_size + per_block - 1) / per_block), n_sites, items);
   fold_kernel<<<grid, kThreads, 0, (cudaStream_t)stream>>>(
-      t.sites, t.events, t.mats, t.cuts, n_cuts, x1, x1_words, n_batch, slice_begin, item0, hdr,
+      t.sites, t.events, t.matsf, t.cuts, n_cuts, x1, x1_words, n_batch, slice_begin, item0, hdr,
       hdr_stride, itemsp, item_bytes, sites_off, n_sites);
   count_launch();
   return (int)cudaGetLastError();

@@ -133,6 +133,7 @@ struct DeviceTables {
   const int32_t* open_perm = nullptr;  // output bit i -> bit of the final tensor index
   const int32_t* gate_ev = nullptr;    // per caller gate: its (up to 2) fold events, -1 if none
   const int64_t* partoff = nullptr;    // per site: first fold-adjoint partial of the site
+  const float* matsf = nullptr;        // [n_mats][16]: mats' entries as float-float pairs (hi, lo)
 };
 
 }  // namespace qfx
@@ -173,7 +174,7 @@ struct qfx_plan {
   char* timg = nullptr;
   uint64_t timg_bytes = 0;        // image size, multiple of 256 (the workspace region)
   uint64_t timg_alloc = 0;        // allocation size, multiple of the page size
-  size_t toffs[7] = {0};          // region offsets (qfx::kTableRegions)
+  size_t toffs[8] = {0};          // region offsets (qfx::kTableRegions)
   mutable std::mutex mu;
   mutable bool timg_pinned = false;
   mutable bool timg_tried = false;
@@ -236,11 +237,11 @@ int launch_permute(const void* in, void* out, int rank, const int64_t* shape,
 void apply_autotune_cache(qfx_plan* p, const char* path);
 int tc_variant_of(int precision);   // plan-step variant marking a tensor-core step
 
-// A plan's tables: regions sites, events, mats, cuts, open_perm, gate_ev, partoff of one
-// image.  build_table_image packs the host image at plan creation; stage_tables copies it
+// A plan's tables: regions sites, events, mats, cuts, open_perm, gate_ev, partoff, matsf
+// of one image.  build_table_image packs the host image at plan creation; stage_tables copies it
 // (asynchronously on `stream`) to `dst`, a 256-byte aligned region of table_bytes(p) bytes
 // of the caller's workspace, and returns the kernels' view of it.
-constexpr int kTableRegions = 7;
+constexpr int kTableRegions = 8;
 void build_table_image(qfx_plan* p);
 void free_table_image(qfx_plan* p);
 inline uint64_t table_bytes(const qfx_plan* p) { return p->timg_bytes; }

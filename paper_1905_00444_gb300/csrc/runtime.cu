@@ -101,13 +101,22 @@ void build_table_image(qfx_plan* p) {
     partoff[q] = o;
     o += adjoint_site_partials(p, p->sites[q]);
   }
+  // the fold's float-float copy of the gate matrices: each FP64 entry d as hi = fl32(d)
+  // and lo = fl32(d - hi) (d - hi is exact in FP64), so hi + lo holds d to ~48 bits
+  std::vector<float> matsf(2 * p->mats.size());
+  for (size_t j = 0; j < p->mats.size(); ++j) {
+    const double d = p->mats[j];
+    const float hi = static_cast<float>(d);
+    matsf[2 * j] = hi;
+    matsf[2 * j + 1] = static_cast<float>(d - static_cast<double>(hi));
+  }
   const void* src[kTableRegions] = {p->sites.data(), p->events.data(), p->mats.data(),
                                     p->cut_dev.data(), p->open_perm.data(), p->gate_ev.data(),
-                                    partoff.data()};
+                                    partoff.data(), matsf.data()};
   const size_t len[kTableRegions] = {p->sites.size() * sizeof(FoldSite), p->events.size() * sizeof(FoldEvent),
                                      p->mats.size() * sizeof(double), p->cut_dev.size() * sizeof(CutDev),
                                      p->open_perm.size() * sizeof(int32_t), p->gate_ev.size() * sizeof(int32_t),
-                                     partoff.size() * sizeof(int64_t)};
+                                     partoff.size() * sizeof(int64_t), matsf.size() * sizeof(float)};
   size_t total = 0;
   for (int r = 0; r < kTableRegions; ++r) {
     p->toffs[r] = total;
@@ -168,6 +177,7 @@ DeviceTables tables_at(void* base, const size_t offs[kTableRegions]) {
   t.open_perm = (const int32_t*)(b + offs[4]);
   t.gate_ev = (const int32_t*)(b + offs[5]);
   t.partoff = (const int64_t*)(b + offs[6]);
+  t.matsf = (const float*)(b + offs[7]);
   return t;
 }
 
