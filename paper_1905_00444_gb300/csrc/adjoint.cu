@@ -365,8 +365,11 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmulcf(float2 a, float2 b) {   // a * conj(b)
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
-__device__ __forceinline__ float2 mat_entry(const double* m, int i) {
-  return make_float2((float)m[2 * i], (float)m[2 * i + 1]);
+// complex entry i of a gate matrix in the fold's float-float table (16 floats per matrix,
+// a (hi, lo) pair per FP64 real): its FP32 value is the hi parts, the round-to-nearest of
+// the FP64 entries, read without a conversion from FP64
+__device__ __forceinline__ float2 mat_entry(const float* m, int i) {
+  return make_float2(m[4 * i], m[4 * i + 2]);
 }
 
 // Sums v[0..7] over the warp by halving: after the exchanges at distance 16, 8 and 4 each
@@ -403,7 +406,7 @@ __device__ __forceinline__ float warp_sum8(float v[8], int lane) {
 __host__ __device__ __forceinline__ int ev_slots(int kind) { return kind == EV_BLOCK ? 4 : 1; }
 
 __global__ void __launch_bounds__(kT) fold_backward_kernel(
-    const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events, const double* __restrict__ mats,
+    const FoldSite* __restrict__ sites, const FoldEvent* __restrict__ events, const float* __restrict__ matsf,
     const CutDev* __restrict__ cuts, int n_cuts, const uint64_t* __restrict__ x1w, int64_t sid,
     const float2* __restrict__ sgrad, double* __restrict__ bpart, const int64_t* __restrict__ part_off) {
   __shared__ double wpart[kT / 32][kMaxEvents][8];
@@ -443,10 +446,10 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
   for (int j = 0; j < nev; ++j) {
     const FoldEvent ev = events[st.ev_begin + j];
     n_slots += ev_slots(ev.kind);
-    const double* m = mats + 8 * (int64_t)ev.mat;
+    const float* m = matsf + 16 * (int64_t)ev.mat;
     float2 a = u0[j], c = u1[j];
     if (ev.kind == EV_GATE || ev.kind == EV_BLOCK) {
-      const double* g = ev.kind == EV_GATE ? m : m + 8 * leg(ev, 3);
+      const float* g = ev.kind == EV_GATE ? m : m + 16 * leg(ev, 3);
       const float2 g00 = mat_entry(g, 0), g01 = mat_entry(g, 1), g10 = mat_entry(g, 2), g11 = mat_entry(g, 3);
       const float2 p0 = cmulf(g00, a), q0 = cmulf(g01, c), p1 = cmulf(g10, a), q1 = cmulf(g11, c);
       a = make_float2(p0.x + q0.x, p0.y + q0.y);
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
   int sl = n_slots;
   for (int j = nev - 1; j >= 0; --j) {
     const FoldEvent ev = events[st.ev_begin + j];
-    const double* m = mats + 8 * (int64_t)ev.mat;
+    const float* m = matsf + 16 * (int64_t)ev.mat;
     const float2 a = u0[j], c = u1[j];
     sl -= ev_slots(ev.kind);
     const int k = ev.kind == EV_GATE ? 0 : leg(ev, (ev.kind == EV_ELEM || ev.kind == EV_BLOCK) ? 3 : 1);
@@ -504,7 +507,7 @@ __global__ void __launch_bounds__(kT) fold_backward_kernel(
     }
     // w <- w O_j
     if (ev.kind == EV_GATE || ev.kind == EV_BLOCK) {
-      const double* gm = ev.kind == EV_GATE ? m : m + 8 * k;
+      const float* gm = ev.kind == EV_GATE ? m : m + 16 * k;
       const float2 g00 = mat_entry(gm, 0), g01 = mat_entry(gm, 1), g10 = mat_entry(gm, 2), g11 = mat_entry(gm, 3);
       const float2 p0 = cmulf(w0, g00), q0 = cmulf(w1, g10), p1 = cmulf(w0, g01), q1 = cmulf(w1, g11);
       w0 = make_float2(p0.x + q0.x, p0.y + q0.y);
@@ -825,7 +828,7 @@ qfx_status backward(const qfx_plan* p, const uint64_t* x1, int64_t n_batch, int6
     }
     // back through every site's time fold
     dim3 fg((unsigned)((max_site + kT - 1) / kT), n);
-    fold_backward_kernel<<<fg, kT, 0, st>>>(t.sites, t.events, t.mats, t.cuts, (int)p->cut_dev.size(),
+    fold_backward_kernel<<<fg, kT, 0, st>>>(t.sites, t.events, t.matsf, t.cuts, (int)p->cut_dev.size(),
                                             x1 + b * p->x1_words, sid, sgrad, (double*)(ws + Lw.bpart),
                                             t.partoff);
     const int nev = (int)p->events.size();
