@@ -465,3 +465,26 @@ def test_tree_plan_forced_cuts_keep_the_slice_numbering():
     line = qfx.Plan(qfx.Circuit(g), n_open=6, cuts=cuts)
     assert tree.cuts == line.cuts == cuts and tree.n_slices == line.n_slices == 16 ** 12
     assert tree.stats["flops_per_item"] < line.stats["flops_per_item"] / 10
+
+
+def test_batch_workspace_follows_the_persistent_and_lane_split():
+    """Host only: qfx_batch_workspace_bytes reads only the plans and ranges.  Split-precision
+    items whose steps all take FP32 tiles (bond dimension 4) size a persistent batch, like
+    their FP32 twins (same tables and blocks); an item with tensor-core steps (5x5x24,
+    K = N = 64) adds one graph lane per slot."""
+    def ws(plans, slots):
+        arr = (q.BatchItem * len(plans))(*[q.BatchItem(p._h.value, None, 1, 0, p.n_slices, None)
+                                            for p in plans])
+        return int(q.lib.qfx_batch_workspace_bytes(arr, len(plans), slots))
+
+    small = [ri.rqc(4, 4, 16, seed=s) for s in (20, 22)]
+    fp32 = [qfx.Plan(qfx.Circuit(c), n_open=3) for c in small]
+    bf16 = [qfx.Plan(qfx.Circuit(c), n_open=3, precision="bf16x3") for c in small]
+    assert all(st["variant"] < 10 for p in bf16 for st in p.steps)
+    assert ws(bf16, 4) == ws(fp32, 4) > 0
+    big = qfx.Plan(qfx.Circuit(ri.rqc(5, 5, 24, seed=1)), n_open=4, precision="bf16x3")
+    assert any(st["variant"] >= 10 for st in big.steps)
+    one, two = ws(bf16 + [big], 1), ws(bf16 + [big], 2)
+    lane = two - one
+    assert big.stats["item_bytes"] <= lane <= big.workspace_bytes(1)
+    assert ws(bf16 + [big], 3) - two == lane
