@@ -76,7 +76,10 @@ typedef enum {
  * The entries a kind does not use are ignored.  q0 and q1 must be grid neighbours.
  * Gates of one layer must act on disjoint qubits; layers run in increasing order.  A bond
  * holds at most 40 bits; its index reads the earliest gate's leg as the most significant
- * bits. */
+ * bits.  Entries must be finite.  The time fold computes in float-float arithmetic (FP32
+ * pairs, about 48 significant bits, the FP32 exponent range), so the partial products of a
+ * site's time line must stay within about 1e-30 .. 1e38 in magnitude; unitary gates and
+ * the diagonal and projector pieces of two-qubit gates keep them at most 1. */
 typedef struct {
   int32_t layer;
   int32_t q0;
