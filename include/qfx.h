@@ -132,10 +132,12 @@ typedef struct {
   const int32_t* open_sites;       /* x2 qubits (Sec. III.B), or NULL to let the planner take
                                       the last n_open sites of its contraction order */
   int32_t n_open;                  /* number of x2 qubits (<= 24); output index bit i = open site i */
-  const qfx_cut* forced_cuts;      /* cuts always applied (before any the cap needs) */
+  const qfx_cut* forced_cuts;      /* cuts always applied, first and in this order; cuts the
+                                      cap needs come after them, and may narrow a forced
+                                      one further (qfx_plan_cut reports the final sizes) */
   int32_t n_forced_cuts;
   int32_t precision;               /* qfx_precision */
-  int32_t plan_family;             /* 0 = line sweep, 1 = contraction tree (FP32; see below) */
+  int32_t plan_family;             /* 0 = line sweep, 1 = contraction tree (see qfx_plan_create) */
   int32_t tc_flags;                /* tensor-core options, QFX_TC_* bits; 0 = default */
   const char* autotune_cache;      /* JSON file written by qfx_autotune, or NULL */
   uint64_t adjoint_store_bytes;    /* qfx_amplitudes_backward keeps the output of every step
@@ -177,7 +179,8 @@ void qfx_plan_destroy(qfx_plan* p);
 
 typedef struct {
   int64_t n_slices;            /* product of the cut radices */
-  int32_t n_steps;             /* sites absorbed, = number of qubits (step 0 is free) */
+  int32_t n_steps;             /* line sweep: sites absorbed, = number of qubits (step 0 is
+                                  free); contraction tree: its n - 1 pairwise contractions */
   int32_t n_open;
   int32_t n_cuts;
   int32_t n_sites;

@@ -488,3 +488,58 @@ def test_batch_workspace_follows_the_persistent_and_lane_split():
     lane = two - one
     assert big.stats["item_bytes"] <= lane <= big.workspace_bytes(1)
     assert ws(bf16 + [big], 3) - two == lane
+
+
+def test_tree_planner_invariants_on_random_circuits():
+    """Plan family 1 on seeded random grids, depths, gate kinds, open sites, forced cuts and
+    caps: n - 1 pairwise contractions, Eq. 1 per node, a root of 2^|x2| outputs, long
+    contractions in 1024-long chunks (in place, P = 1) or split-K parts, the forced cuts
+    first and in order (as given without a cap; a cap may narrow them further), as many
+    slices as the cuts' radices multiply to, and the cap met."""
+    rng = np.random.default_rng(77)
+    for case in range(60):
+        rows, cols = int(rng.integers(2, 6)), int(rng.integers(2, 6))
+        depth = int(rng.choice([4, 8, 16, 24]))
+        kind = "fsim" if rng.random() < 0.3 else "cz"
+        c = ri.rqc(rows, cols, depth, seed=500 + case, two_qubit=kind)
+        n = rows * cols
+        n_open = int(rng.integers(0, min(6, n) + 1))
+        bits = {}
+        for g in c.gates:
+            if g.q1 >= 0:
+                e = (min(g.q0, g.q1), max(g.q0, g.q1))
+                bits[e] = bits.get(e, 0) + (2 if g.kind == ri.U4 else 1)
+        cuts = []
+        for e in rng.permutation(sorted(bits))[:int(rng.integers(0, 3))]:
+            m = bits[tuple(e)]
+            cuts.append((int(e[0]), int(e[1]), 1 << int(rng.integers(0, m + 1))))
+        base = qfx.Plan(qfx.Circuit(c), n_open=n_open, cuts=cuts, family="tree")
+        cap = 0
+        if rng.random() < 0.4 and base.stats["max_elements"] > 64:
+            cap = max(base.stats["max_elements"] * 8 // 4, 8 << n_open)
+        p = qfx.Plan(qfx.Circuit(c), n_open=n_open, cuts=cuts, max_intermediate_bytes=cap,
+                     family="tree")
+        st = p.steps
+        assert p.stats["n_steps"] == len(st) == n - 1, case
+        total = 0.0
+        for s in st:
+            assert min(s["P"], s["K"], s["N"], s["Sd"]) >= 1, case
+            assert s["flops"] == 8.0 * s["P"] * s["K"] * s["N"] * s["Sd"], case
+            if s["parts"]:
+                assert s["K"] == 1024 * s["parts"] and s["variant"] < 10, case
+            elif s["K"] > 1024:
+                assert s["P"] == 1 and s["K"] % 1024 == 0, case
+            total += s["flops"]
+        root = st[-1]
+        assert root["P"] * root["N"] * root["Sd"] == 1 << n_open, case
+        assert p.stats["flops_per_item"] == pytest.approx(total, rel=1e-12), case
+        for (qa, qb, size), got in zip(cuts, p.cuts):
+            assert got[:2] == (qa, qb) and got[2] <= size and size % got[2] == 0, case
+        if not cap:
+            assert p.cuts == cuts, case
+        want_slices = 1
+        for (a, b, size) in p.cuts:
+            want_slices *= (1 << bits[(min(a, b), max(a, b))]) // size
+        assert p.n_slices == want_slices, case
+        if cap:
+            assert p.stats["max_elements"] * 8 <= cap, case
