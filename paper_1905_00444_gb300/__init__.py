@@ -13,5 +13,5 @@ from .qfx import (  # noqa: E402,F401
     autotune, frugal_sample, frugal_select, permute, profile_collect, profile_enable, sync,
     tensor_peak, version, debug_permute_withhold,
 )
-from .sharding import partition_slices, reduce_partials  # noqa: E402,F401
+from .sharding import item_costs, partition_items, partition_slices, reduce_partials  # noqa: E402,F401
 from .autograd import CircuitAmplitudes, circuit_amplitudes  # noqa: E402,F401
