@@ -200,7 +200,9 @@ qfx_status qfx_plan_info(const qfx_plan* p, qfx_plan_stats* out);
 uint64_t qfx_workspace_bytes(const qfx_plan* p, int64_t n_concurrent);
 
 typedef struct {
-  int32_t site;       /* qubit absorbed by this step */
+  int32_t site;       /* line sweep: qubit absorbed by this step; contraction tree: id of
+                         the node's result (the sites are tensors 0 .. n-1, node results
+                         n, n+1, ... in step order) */
   int32_t variant;    /* kernel tile variant chosen for it */
   int64_t P, K, N, NL, Sd;  /* shapes as in qfx_plan_create's formula; NH = N / NL */
   double flops;       /* 8*P*K*N*Sd = 8 sqrt(v0 v1 v2), Eq. 1 */

@@ -521,6 +521,7 @@ def test_tree_planner_invariants_on_random_circuits():
                      family="tree")
         st = p.steps
         assert p.stats["n_steps"] == len(st) == n - 1, case
+        assert [s["site"] for s in st] == list(range(n, 2 * n - 1)), case   # node result ids
         total = 0.0
         for s in st:
             assert min(s["P"], s["K"], s["N"], s["Sd"]) >= 1, case
